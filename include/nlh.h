@@ -1,0 +1,185 @@
+/*
+ * nlh.h -- C ABI of the GB300 (sm_103a) NFFT nonlocal-denoising library.
+ *
+ * The library solves the nonlocal system of arXiv 2407.06834
+ *     (lambda I + mu L) u = b,   L = diag(eta) - Gamma,   eta = Gamma 1
+ * (Eq. discretized-state, Sec. 4.2) matrix-free.  Gamma is the unnormalised
+ * extended Gaussian ANOVA kernel over per-pixel patch features
+ * (Eq. discrete_ANOVA, with the zero diagonal of Sec. 2.3), and every
+ * product with Gamma is an NFFT fast Gauss transform per feature window
+ * (Sec. 3).  Throughout, mu = 1 and alpha = lambda / mu, so the system is
+ * (alpha I + L) u = b; the denoising right-hand side is b = alpha f.
+ *
+ * Conventions for every entry point:
+ *   - Vectors and feature matrices are DEVICE pointers owned by the caller;
+ *     the library never frees or keeps them beyond the call.  All FP64.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; a call that returns host-visible
+ *     results (plan creation, solve info) synchronises that stream only.
+ *   - Errors come back as nlh_status codes, never as exceptions or aborts;
+ *     nlh_last_error() gives a message for the calling thread.
+ *   - The library owns everything inside a plan (grids, permutations,
+ *     tables, solver workspace); nlh_plan_destroy frees it.
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef NLH_H
+#define NLH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NLH_OK = 0,
+    NLH_ERR_NOT_CONVERGED = 1, /* warning: u holds the last iterate         */
+    NLH_ERR_ARG = -1,          /* invalid argument (message says which)     */
+    NLH_ERR_CUDA = -2,         /* a CUDA runtime call failed                */
+    NLH_ERR_OOM = -3,          /* device allocation failed                  */
+    NLH_ERR_BREAKDOWN = -4,    /* CG breakdown: p^T A p <= 0 or not finite  */
+    NLH_ERR_TIMEOUT = -5       /* a bounded device wait gave up             */
+} nlh_status;
+
+typedef struct nlh_plan_s *nlh_plan;
+
+/* NFFT arithmetic of a matvec. */
+enum { NLH_FP64 = 0, NLH_FP32 = 1 };
+
+/* Patch features, Sec. 5: for every pixel the closed square patch of radius
+ * `radius` of the image, zero padded (pad = 0, the paper's choice) or
+ * reflect padded (pad = 1: index -1 maps to 1, n to n-2).
+ *   image     device, n1 x n2 FP64, row-major (pixel i = r n2 + c)
+ *   features  device, (n1 n2) x D FP64 with D = (2 radius + 1)^2, row-major;
+ *             patch dim k = (dr + radius)(2 radius + 1) + (dc + radius).
+ * Errors: NLH_ERR_ARG for n1, n2 < 1, radius < 0 or NULL pointers. */
+nlh_status nlh_patch_features(const double *image, int n1, int n2, int radius,
+                              int pad, double *features, void *stream);
+
+/* Plan description.  Window l uses feature dims windows[3l .. 3l+2]
+ * (Eq. continuous_ANOVA; windows of at most three dims, Sec. 3); an entry -1
+ * is a zero-valued dim.  The Gaussian exp(-||x - y||^2 / sigma^2) of each
+ * window is summed by an NFFT with bandwidth M per dim (frequencies
+ * |k| < M/2), an oversampled grid of n_os points per dim and a Kaiser-Bessel
+ * window that touches 2m grid points per dim. */
+typedef struct {
+    int64_t N;              /* points (pixels), >= 2                         */
+    int D;                  /* feature dims per point, >= 1                  */
+    int L;                  /* windows, 1..64                                */
+    const int32_t *windows; /* HOST, L x 3 dim indices in [-1, D)            */
+    double sigma;           /* kernel width, > 0                             */
+    int M;                  /* even, 4 <= M <= n_os                          */
+    int n_os;               /* power of two, 32..256                         */
+    int m;                  /* 2..8, and 2m < n_os                           */
+    int precision;          /* bit 0: build FP64 path, bit 1: FP32 path      */
+    double torus_fill;      /* in (0, 1): fraction of the torus the points
+                               span per dim; 0 = choose automatically        */
+    int max_items_pts;      /* points per work item, 0 = default (256)       */
+} nlh_plan_desc;
+
+/* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
+ * the affine map onto the torus x~ = s (x - c_l) with c_l the per-window
+ * midrange and s = torus_fill / (largest per-dim range), the sort of the
+ * points by grid cell, the per-point window weights, the Fourier multiplier
+ * tables and the degrees d = Gamma_full 1 (one matvec per precision built).
+ *   features  device, N x D FP64 row-major (e.g. from nlh_patch_features).
+ * Synchronises `stream`.  Errors: NLH_ERR_ARG, NLH_ERR_OOM, NLH_ERR_CUDA. */
+nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc,
+                           const double *features, void *stream);
+
+/* Change sigma: recompute the multiplier tables and the degrees (Sec. 5.5
+ * learns over sigma through theta = sigma^-2).  The torus map is kept.
+ * Synchronises `stream`. */
+nlh_status nlh_plan_set_sigma(nlh_plan plan, double sigma, void *stream);
+
+typedef struct {
+    int64_t N;
+    int L, M, n_os, m, precision;
+    double sigma, torus_fill, scale; /* scale s of the torus map             */
+    double sigma_torus;              /* s * sigma                            */
+    double max_range;                /* R, largest per-dim coordinate range  */
+    int64_t n_items;                 /* work items over all windows          */
+    int64_t occupied_cells;          /* non-empty (window, cell) pairs       */
+    double est_trunc_err, est_alias_err; /* a-priori per-dim error estimates */
+    int64_t device_bytes;            /* device memory owned by the plan      */
+} nlh_plan_info;
+
+nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
+
+/* Matrix-free products (Sec. 3 and Eq. discretized-state), y and x device
+ * FP64 vectors of length N (y must not alias x):
+ *   op 0: y = Gamma_full x          (kernel sum over all j, diagonal kept)
+ *   op 1: y = L x = d o x - Gamma_full x   (d = Gamma_full 1; the diagonal
+ *                                           cancels, Sec. 2.3)
+ *   op 2: y = (alpha I + L) x
+ * precision: NLH_FP64 or NLH_FP32 (the NFFT stages; the output is FP64).
+ * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers). */
+nlh_status nlh_matvec(nlh_plan plan, int op, int precision, double alpha,
+                      const double *x, double *y, void *stream);
+
+/* Krylov methods (Sec. 4.3 and Sec. 5.3-5.4). */
+enum {
+    NLH_CG = 0,            /* CG in the original basis (Table 2)              */
+    NLH_PCG_JACOBI = 1,    /* CG with P_a = alpha I + diag(eta)               */
+    NLH_PCG_DEFLATED = 2,  /* decoupled CG with the projected P_{U,a}         */
+    NLH_CG_DEFLATED = 3    /* decoupled CG without preconditioner (I_U)       */
+};
+/* Arithmetic of a solve. */
+enum {
+    NLH_SOLVE_FP64 = 0,    /* every matvec FP64                               */
+    NLH_SOLVE_MIXED = 1    /* FP32-NFFT inner solves inside FP64 iterative
+                              refinement (FP64 residuals and dots)            */
+};
+
+typedef struct {
+    double tol;             /* stop at ||b - A u|| <= tol ||b||               */
+    int maxit;              /* CG iterations (per inner solve when mixed)     */
+    int method;             /* NLH_CG .. NLH_CG_DEFLATED                      */
+    int arith;              /* NLH_SOLVE_FP64 or NLH_SOLVE_MIXED              */
+    double inner_tol;       /* mixed: inner relative tolerance (0 = 1e-4)     */
+    int max_outer;          /* mixed: refinement steps (0 = 20)               */
+    const double *x0;       /* device N, initial guess, or NULL (zero)        */
+    const double *diag_scale; /* device N, positive factors c_i multiplying
+                               P_a (learned correction), or NULL             */
+    double *hist;           /* HOST, optional residual history ||r_k||/||b||  */
+    int hist_len;           /* capacity of hist                               */
+    int check_every;        /* iterations between host convergence checks
+                               (0 = default)                                  */
+} nlh_solve_opts;
+
+typedef struct {
+    int iters;              /* CG iterations (summed over inner solves)       */
+    int outer;              /* refinement steps (1 for FP64 solves)           */
+    int matvecs_fp64, matvecs_fp32;
+    double rel_res;         /* last recurrence residual ||r||/||b||           */
+    double rel_res_true;    /* ||b - A u||/||b|| from a final FP64 matvec     */
+    double seconds;         /* wall time of the call                          */
+    int used_fallback;      /* 1 if diag_scale was dropped after a failure    */
+    int status;             /* same as the return value                       */
+} nlh_solve_info;
+
+/* Solve (alpha I + L) u = b (Eq. discretized-state with mu = 1).
+ * NLH_PCG_DEFLATED: u = (mean(b)/alpha) 1 + w with w the CG iterate on the
+ * orthogonal complement of 1, preconditioned by Pi P^-1 Pi (Pi the mean
+ * removal); this is iterate-for-iterate the paper's CG on pi_2(U^T A U)
+ * with pi_2(U^T P_a^-1 U) (Sec. 4.3.2), because U = [1/sqrt(n), U_2] and
+ * U_2 U_2^T = Pi.  b, u device FP64 length N; u is overwritten.
+ * Synchronises `stream`.  Returns NLH_OK, NLH_ERR_NOT_CONVERGED (u = last
+ * iterate), NLH_ERR_BREAKDOWN, or an error. */
+nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, double *u,
+                     const nlh_solve_opts *opts, nlh_solve_info *info,
+                     void *stream);
+
+/* Free a plan and everything it owns.  NULL is accepted. */
+nlh_status nlh_plan_destroy(nlh_plan plan);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *nlh_last_error(void);
+
+/* Library version string. */
+const char *nlh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLH_H */

@@ -1,0 +1,165 @@
+// common.cuh -- internals shared by the translation units of libnlh.
+//
+// Device data layout of a plan (all device arrays are owned by the plan):
+//   perm     [L*N]   int32   sorted position s (window l = s / N) -> pixel
+//   items    [n_items] int4  {window, cell (z*n+y)*n+x, first sorted
+//                             position, point count}; the points of one item
+//                             share one grid cell, hence one stencil
+//   wts64/32 [L*N][3][2m]    Kaiser-Bessel weights of each sorted point per
+//                             dim for the grid points cell-m+1 .. cell+m
+//   grid64/32 [L][n][n][n]   oversampled grids, x fastest; zero between
+//                             matvecs (the epilogue clears them)
+//   tab64/32 [n]             per-dim Fourier multiplier in bit-reversed order
+//   tw64/32  [n/2]           FFT twiddles exp(-2 pi i j / n)
+//   Y        [L][N]          per-window interpolated values, pixel order
+//   d64/d32  [N]             degrees d = Gamma_full 1 of each NFFT precision
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/nlh.h"
+
+namespace nlh {
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+struct Failure {
+    nlh_status st;
+};
+
+#define NLH_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            ::nlh::set_error("%s failed: %s (%s:%d)", #call,                   \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);      \
+            throw ::nlh::Failure{e_ == cudaErrorMemoryAllocation ? NLH_ERR_OOM \
+                                                                 : NLH_ERR_CUDA}; \
+        }                                                                      \
+    } while (0)
+
+#define NLH_CHECK_LAUNCH() NLH_CUDA(cudaGetLastError())
+
+#define NLH_REQUIRE(cond, ...)                                                 \
+    do {                                                                       \
+        if (!(cond)) {                                                         \
+            ::nlh::set_error(__VA_ARGS__);                                     \
+            throw ::nlh::Failure{NLH_ERR_ARG};                                 \
+        }                                                                      \
+    } while (0)
+
+// Device-side scalars of one Krylov solve.  Written only by block 0 of the
+// kernel that owns each field (see solve.cu); read by every kernel.
+struct SolveState {
+    int done;        // 1 once converged, broken down or out of iterations
+    int status;      // 0 running/converged, -4 breakdown
+    int k;           // completed iterations
+    int maxit;
+    double tol;
+    double bnorm;    // ||rhs||
+    double bmean;    // mean(rhs) (deflated methods)
+    double rz;       // r^T z of the current iterate
+    double rz_old;   // copy made by the update kernel
+    double rr;       // ||r||^2 of the current iterate
+};
+
+constexpr int kMaxHist = 4096;
+
+struct Plan {
+    int64_t N = 0;
+    int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 256;
+    double sigma = 0, fill = 0, scale = 0, R = 0, kb_beta = 0;
+    int64_t n_items = 0, occupied = 0;
+    std::vector<int32_t> windows;
+    // device arrays
+    int32_t *perm = nullptr;
+    int4 *items = nullptr;
+    double *wts64 = nullptr;
+    float *wts32 = nullptr;
+    double *tab64 = nullptr;
+    float *tab32 = nullptr;
+    double2 *tw64 = nullptr;
+    float2 *tw32 = nullptr;
+    double *grid64 = nullptr;
+    float *grid32 = nullptr;
+    double *Y = nullptr;
+    double *d64 = nullptr, *d32 = nullptr;
+    // solver workspace
+    double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
+           *t = nullptr, *rhs = nullptr, *pinv = nullptr;
+    double *partials = nullptr;   // kRedBlocks * 12 doubles
+    SolveState *st = nullptr;     // device
+    SolveState *st_host = nullptr; // pinned mirror
+    double *hist = nullptr;       // device, kMaxHist
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+
+    template <typename T> T *alloc(size_t count) {
+        void *ptr = nullptr;
+        if (count == 0) count = 1;
+        NLH_CUDA(cudaMalloc(&ptr, count * sizeof(T)));
+        allocs.push_back(ptr);
+        bytes += (int64_t)(count * sizeof(T));
+        return static_cast<T *>(ptr);
+    }
+    ~Plan();
+};
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs; grid-stride loops beyond
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; result valid in thread 0.  blockDim.x <= 1024.
+__device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        s = (lane < nw) ? sh[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// Every thread of the block gets sum_{j < nparts} parts[j * stride + off].
+// Deterministic: fixed order per thread, fixed tree.
+__device__ __forceinline__ double reduce_partials(const double *parts, int nparts,
+                                                  int stride, int off,
+                                                  double *sh) {
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nparts; j += blockDim.x) v += parts[j * stride + off];
+    v = block_sum(v, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) sh[32] = v;
+    __syncthreads();
+    double out = sh[32];
+    __syncthreads();
+    return out;
+}
+
+// ---------------------------------------------------------------- host API (internal)
+void plan_tables(Plan &P, cudaStream_t s);
+void plan_degrees(Plan &P, cudaStream_t s);
+void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
+            double *partials, const int *done, cudaStream_t s);
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace nlh
+
+// The opaque handle of the C ABI is the plan itself.
+struct nlh_plan_s : public nlh::Plan {};

@@ -1,0 +1,665 @@
+// plan.cu -- plan construction: features, torus map, sort by grid cell,
+// work items, window weights and Fourier multiplier tables.
+//
+// Paper: arXiv 2407.06834.  Patches and windows: Sec. 5.  Fast summation
+// per window (adjoint NFFT, multiply by the Gaussian's Fourier coefficients,
+// NFFT): Sec. 3, Eq. NFFT and Eq. DGT.  Degrees eta = Gamma 1: Sec. 2.3.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <new>
+
+namespace nlh {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+Plan::~Plan() {
+    for (void *ptr : allocs) cudaFree(ptr);
+    if (st_host) cudaFreeHost(st_host);
+}
+
+// ------------------------------------------------------------------ features
+__device__ __forceinline__ int reflect_index(int i, int n) {
+    if (n == 1) return 0;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * (n - 1) - i;
+    }
+    return i;
+}
+
+// Patch features (Sec. 5): one thread per (pixel, patch dim).
+__global__ void k_patch_features(const double *__restrict__ img, int n1, int n2,
+                                 int rho, int pad, double *__restrict__ feat) {
+    const int P = 2 * rho + 1, D = P * P;
+    const int64_t total = (int64_t)n1 * n2 * D;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pix = idx / D;
+        int k = (int)(idx - pix * D);
+        int r = (int)(pix / n2), c = (int)(pix - (int64_t)r * n2);
+        int rr = r + k / P - rho, cc = c + k % P - rho;
+        double val;
+        if (pad == 0) {
+            val = (rr < 0 || rr >= n1 || cc < 0 || cc >= n2) ? 0.0 : img[(int64_t)rr * n2 + cc];
+        } else {
+            val = img[(int64_t)reflect_index(rr, n1) * n2 + reflect_index(cc, n2)];
+        }
+        feat[idx] = val;
+    }
+}
+
+__device__ __forceinline__ double window_coord(const double *__restrict__ feat, int D,
+                                               const int *__restrict__ win, int l,
+                                               int64_t i, int t) {
+    int d = win[3 * l + t];
+    return d < 0 ? 0.0 : feat[i * D + d];
+}
+
+// ------------------------------------------------------------------ min/max
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// blockIdx.y = coordinate (window l, dim t); partial min / max per block.
+__global__ void k_minmax_partial(const double *__restrict__ feat, int64_t N, int D,
+                                 const int *__restrict__ win, double *__restrict__ part) {
+    __shared__ double smin[32], smax[32];
+    int coord = blockIdx.y, l = coord / 3, t = coord % 3;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = window_coord(feat, D, win, l, i, t);
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { smin[wid] = lo; smax[wid] = hi; }
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        lo = lane < nw ? smin[lane] : INFINITY;
+        hi = lane < nw ? smax[lane] : -INFINITY;
+        lo = warp_min(lo);
+        hi = warp_max(hi);
+        if (lane == 0) {
+            part[((int64_t)coord * gridDim.x + blockIdx.x) * 2 + 0] = lo;
+            part[((int64_t)coord * gridDim.x + blockIdx.x) * 2 + 1] = hi;
+        }
+    }
+}
+
+__global__ void k_minmax_final(const double *__restrict__ part, int nb, double *__restrict__ mm) {
+    int coord = blockIdx.x;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int j = threadIdx.x; j < nb; j += 32) {
+        lo = fmin(lo, part[((int64_t)coord * nb + j) * 2 + 0]);
+        hi = fmax(hi, part[((int64_t)coord * nb + j) * 2 + 1]);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if (threadIdx.x == 0) { mm[2 * coord] = lo; mm[2 * coord + 1] = hi; }
+}
+
+// ------------------------------------------------------------------ sort by cell
+// Grid coordinate u = (s (x - c) + 1/2) n taken modulo n, so that the torus
+// [-1/2, 1/2) maps to the grid points 0..n-1.  Cell = floor(u).
+__global__ void k_cell_keys(const double *__restrict__ feat, int64_t N, int D, int L,
+                            const int *__restrict__ win, const double *__restrict__ center,
+                            double s, int n, double *__restrict__ u, int *__restrict__ keys,
+                            int *__restrict__ hist) {
+    const int64_t total = (int64_t)L * N;
+    const int64_t n3 = (int64_t)n * n * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int l = (int)(idx / N);
+        int64_t i = idx - (int64_t)l * N;
+        int cell[3];
+        for (int t = 0; t < 3; ++t) {
+            double x = window_coord(feat, D, win, l, i, t);
+            double ut = (s * (x - center[3 * l + t]) + 0.5) * n;
+            ut -= n * floor(ut / n);
+            if (ut >= n) ut -= n;
+            if (ut < 0.0) ut = 0.0;
+            int c = (int)floor(ut);
+            if (c > n - 1) c = n - 1;
+            u[idx * 3 + t] = ut;
+            cell[t] = c;
+        }
+        int key = (cell[2] * n + cell[1]) * n + cell[0];
+        keys[idx] = key;
+        atomicAdd(&hist[(int64_t)l * n3 + key], 1);
+    }
+}
+
+__global__ void k_scatter(const int *__restrict__ keys, int64_t N, int L, int64_t n3,
+                          int *__restrict__ cursor, int *__restrict__ perm) {
+    const int64_t total = (int64_t)L * N;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int l = (int)(idx / N);
+        int64_t i = idx - (int64_t)l * N;
+        int pos = atomicAdd(&cursor[(int64_t)l * n3 + keys[idx]], 1);
+        perm[pos] = (int)i;
+    }
+}
+
+// ------------------------------------------------------------------ exclusive scan (int32)
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_incl_scan(int v, int *sh /* 32 */) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = sh[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) v += sh[wid - 1];
+    __syncthreads();
+    return v;
+}
+
+__global__ void k_scan_tiles(const int *__restrict__ in, int64_t n, int *__restrict__ sums) {
+    __shared__ int sh[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int v = 0;
+    for (int j = 0; j < kScanPer; ++j)
+        if (base + j < n) v += in[base + j];
+    v = block_incl_scan(v, sh);
+    if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = v;
+}
+
+__global__ void k_scan_sums(int *__restrict__ sums, int nt, int *__restrict__ total) {
+    __shared__ int sh[32];
+    __shared__ int last;
+    int carry = 0;
+    for (int base = 0; base < nt; base += kScanThreads) {
+        int i = base + threadIdx.x;
+        int v = i < nt ? sums[i] : 0;
+        int inc = block_incl_scan(v, sh);
+        if (i < nt) sums[i] = carry + inc - v;
+        if (threadIdx.x == kScanThreads - 1) last = inc;
+        __syncthreads();
+        carry += last;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, int64_t n, const int *__restrict__ sums,
+                             int *__restrict__ out) {
+    __shared__ int sh[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int vals[kScanPer];
+    int v = 0;
+    for (int j = 0; j < kScanPer; ++j) {
+        vals[j] = (base + j < n) ? in[base + j] : 0;
+        v += vals[j];
+    }
+    int inc = block_incl_scan(v, sh);
+    int run = sums[blockIdx.x] + inc - v;
+    for (int j = 0; j < kScanPer; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += vals[j];
+    }
+}
+
+// out = exclusive scan of in; returns the total (synchronises s).
+static int64_t exclusive_scan(Plan &P, const int *in, int *out, int64_t n, cudaStream_t s,
+                              int *tmp_sums, int *d_total) {
+    int nt = div_up(n, kScanTile);
+    k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, n, tmp_sums);
+    NLH_CHECK_LAUNCH();
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp_sums, nt, d_total);
+    NLH_CHECK_LAUNCH();
+    k_scan_apply<<<nt, kScanThreads, 0, s>>>(in, n, tmp_sums, out);
+    NLH_CHECK_LAUNCH();
+    int total = 0;
+    NLH_CUDA(cudaMemcpyAsync(&total, d_total, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    return total;
+}
+
+// ------------------------------------------------------------------ work items
+__global__ void k_item_counts(const int *__restrict__ hist, int64_t ncells, int kmax,
+                              int *__restrict__ cnt, int *__restrict__ occupied) {
+    int occ = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int h = hist[c];
+        cnt[c] = (h + kmax - 1) / kmax;
+        occ += h > 0;
+    }
+    occ = __reduce_add_sync(0xffffffffu, occ);
+    if ((threadIdx.x & 31) == 0 && occ) atomicAdd(occupied, occ);
+}
+
+__global__ void k_emit_items(const int *__restrict__ hist, const int *__restrict__ start,
+                             const int *__restrict__ item_off, int64_t ncells, int64_t n3,
+                             int kmax, int4 *__restrict__ items) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int h = hist[c];
+        if (h == 0) continue;
+        int l = (int)(c / n3);
+        int cell = (int)(c - (int64_t)l * n3);
+        int o = item_off[c];
+        for (int t = 0; t * kmax < h; ++t)
+            items[o + t] = make_int4(l, cell, start[c] + t * kmax, min(kmax, h - t * kmax));
+    }
+}
+
+// ------------------------------------------------------------------ window weights
+// Kaiser-Bessel window (Kaiser 1974; its use for gridding: Jackson et al.
+// 1991): phi(x) = I0(beta sqrt(1 - (n x / m)^2)) / I0(beta) for |n x| <= m.
+// A point at grid coordinate u = c + f (c integer, 0 <= f < 1) touches the
+// 2m grid points g = c - m + 1 + t, t = 0..2m-1, at offsets g - u in (-m, m].
+__device__ __forceinline__ double kb_window(double off_over_m, double beta, double inv_i0b) {
+    double z = 1.0 - off_over_m * off_over_m;
+    if (z < 0.0) return 0.0;
+    return cyl_bessel_i0(beta * sqrt(z)) * inv_i0b;
+}
+
+__global__ void k_weights(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
+                          int L, int m, double beta, double inv_i0b,
+                          double *__restrict__ w64, float *__restrict__ w32) {
+    const int64_t total = (int64_t)L * N;
+    const int W2 = 2 * m;
+    for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < total;
+         sidx += (int64_t)gridDim.x * blockDim.x) {
+        int l = (int)(sidx / N);
+        int64_t i = perm[sidx];
+        const double *up = u + ((int64_t)l * N + i) * 3;
+        for (int t = 0; t < 3; ++t) {
+            double ut = up[t];
+            double f = ut - floor(ut);
+            for (int j = 0; j < W2; ++j) {
+                double off = (double)(j - m + 1) - f;
+                double w = kb_window(off / m, beta, inv_i0b);
+                int64_t o = (sidx * 3 + t) * W2 + j;
+                if (w64) w64[o] = w;
+                if (w32) w32[o] = (float)w;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ multiplier tables
+// Per dim, the adjoint NFFT, the multiply by the Gaussian's Fourier
+// coefficients and the NFFT (Sec. 3) collapse into one circular convolution
+// of the oversampled grid with the real, even multiplier
+//   w(k) = 1_{|k| < M/2} ghat(k) / (n chat(k))^2,
+//   ghat(k) = sqrt(pi) sigma_s exp(-pi^2 sigma_s^2 k^2)  (Gaussian transform),
+//   chat(k) = (2m/n) sinh(z)/z / I0(beta), z = sqrt(beta^2 - (2 pi m k/n)^2)
+// (transform of the Kaiser-Bessel window above).  The table is stored in
+// bit-reversed order for the FFT of nfft.cu.
+__global__ void k_tables(int n, int logn, int M, int m, double beta, double inv_i0b,
+                         double sigma_s, double *__restrict__ tab64, float *__restrict__ tab32,
+                         double2 *__restrict__ tw64, float2 *__restrict__ tw32) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int kk = (int)(__brev((unsigned)j) >> (32 - logn));
+    int f = kk < n / 2 ? kk : kk - n;
+    double w = 0.0;
+    if (2 * abs(f) < M) {
+        const double pi = 3.141592653589793238462643;
+        double om = 2.0 * pi * m * f / n;
+        double z2 = beta * beta - om * om;
+        double shz;
+        if (z2 > 1e-24) {
+            double z = sqrt(z2);
+            shz = sinh(z) / z;
+        } else {
+            shz = 1.0;
+        }
+        double chat = (2.0 * m / n) * shz * inv_i0b;
+        double ghat = sqrt(pi) * sigma_s * exp(-pi * pi * sigma_s * sigma_s * (double)f * f);
+        double nc = n * chat;
+        w = ghat / (nc * nc);
+    }
+    if (tab64) tab64[j] = w;
+    if (tab32) tab32[j] = (float)w;
+    if (j < n / 2) {
+        double sn, cs;
+        sincospi(2.0 * j / n, &sn, &cs);
+        if (tw64) tw64[j] = make_double2(cs, -sn);
+        if (tw32) tw32[j] = make_float2((float)cs, (float)-sn);
+    }
+}
+
+__global__ void k_fill(double *__restrict__ x, int64_t n, double v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+static int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// A-priori per-dim error estimates used to pick the torus fill: the Gaussian
+// coefficients dropped by the truncation |k| < M/2 sum to at most
+// erfc(pi sigma_s (M/2 - 1)); the nearest periodic image of the Gaussian
+// sits at distance 1 - fill, giving about 2 exp(-((1 - fill)/sigma_s)^2).
+static void error_estimates(double sigma, double R, double fill, int M, double *trunc,
+                            double *alias) {
+    double ss = sigma * fill / R;
+    *trunc = std::erfc(M_PI * ss * (M / 2.0 - 1.0));
+    double a = (1.0 - fill) / ss;
+    *alias = 2.0 * std::exp(-a * a);
+}
+
+static double choose_fill(double sigma, double R, int M) {
+    double best = 0.5, best_err = INFINITY;
+    for (int k = 5; k <= 95; ++k) {
+        double fill = k / 100.0, tr, al;
+        error_estimates(sigma, R, fill, M, &tr, &al);
+        double e = std::max(tr, al);
+        if (e < best_err) { best_err = e; best = fill; }
+    }
+    return best;
+}
+
+void plan_tables(Plan &P, cudaStream_t s) {
+    double sigma_s = P.sigma * P.scale;
+    double inv_i0b = 1.0 / std::cyl_bessel_i(0.0, P.kb_beta);
+    k_tables<<<div_up(P.n, 256), 256, 0, s>>>(P.n, ilog2(P.n), P.M, P.m, P.kb_beta, inv_i0b,
+                                              sigma_s, P.tab64, P.tab32, P.tw64, P.tw32);
+    NLH_CHECK_LAUNCH();
+}
+
+void plan_degrees(Plan &P, cudaStream_t s) {
+    k_fill<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N, 1.0);
+    NLH_CHECK_LAUNCH();
+    if (P.precision & 1) matvec(P, 0, NLH_FP64, 0.0, P.t, P.d64, nullptr, nullptr, s);
+    if (P.precision & 2) matvec(P, 0, NLH_FP32, 0.0, P.t, P.d32, nullptr, nullptr, s);
+}
+
+static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *features,
+                       cudaStream_t s) {
+    P.N = desc.N;
+    P.D = desc.D;
+    P.L = desc.L;
+    P.M = desc.M;
+    P.n = desc.n_os;
+    P.m = desc.m;
+    P.W2 = 2 * desc.m;
+    P.precision = desc.precision;
+    P.sigma = desc.sigma;
+    P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 256;
+    P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
+    const int64_t N = P.N;
+    const int L = P.L, n = P.n;
+    const int64_t n3 = (int64_t)n * n * n;
+
+    int *d_win = P.alloc<int>(3 * L);
+    NLH_CUDA(cudaMemcpyAsync(d_win, P.windows.data(), sizeof(int) * 3 * L,
+                             cudaMemcpyHostToDevice, s));
+
+    // per-window, per-dim ranges -> torus map
+    const int nb = 152;
+    double *part = P.alloc<double>((size_t)3 * L * nb * 2);
+    double *mm = P.alloc<double>((size_t)3 * L * 2);
+    k_minmax_partial<<<dim3(nb, 3 * L), 256, 0, s>>>(features, N, P.D, d_win, part);
+    NLH_CHECK_LAUNCH();
+    k_minmax_final<<<3 * L, 32, 0, s>>>(part, nb, mm);
+    NLH_CHECK_LAUNCH();
+    std::vector<double> hmm(6 * L), center(3 * L);
+    NLH_CUDA(cudaMemcpyAsync(hmm.data(), mm, sizeof(double) * 6 * L, cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    double R = 0.0;
+    for (int c = 0; c < 3 * L; ++c) {
+        NLH_REQUIRE(std::isfinite(hmm[2 * c]) && std::isfinite(hmm[2 * c + 1]),
+                    "features contain non-finite values");
+        center[c] = 0.5 * (hmm[2 * c] + hmm[2 * c + 1]);
+        R = std::max(R, hmm[2 * c + 1] - hmm[2 * c]);
+    }
+    if (!(R > 0.0)) R = 1.0;
+    P.R = R;
+    P.fill = desc.torus_fill > 0.0 ? desc.torus_fill : choose_fill(P.sigma, R, P.M);
+    P.scale = P.fill / R;
+    P.kb_beta = M_PI * P.m * (2.0 - (double)P.M / P.n);
+    double *d_center = P.alloc<double>(3 * L);
+    NLH_CUDA(cudaMemcpyAsync(d_center, center.data(), sizeof(double) * 3 * L,
+                             cudaMemcpyHostToDevice, s));
+
+    // grid coordinates, cell keys and per-cell counts
+    const int64_t LN = (int64_t)L * N;
+    double *u = nullptr;
+    int *keys = nullptr, *hist = nullptr, *start = nullptr, *cnt = nullptr, *ioff = nullptr,
+        *sums = nullptr, *scal = nullptr;
+    NLH_CUDA(cudaMalloc(&u, sizeof(double) * LN * 3));
+    std::vector<void *> tmp{u};
+    auto tmp_alloc = [&](int **ptr, size_t count) {
+        NLH_CUDA(cudaMalloc((void **)ptr, sizeof(int) * std::max<size_t>(count, 1)));
+        tmp.push_back(*ptr);
+    };
+    try {
+        const int64_t ncells = (int64_t)L * n3;
+        tmp_alloc(&keys, LN);
+        tmp_alloc(&hist, ncells);
+        tmp_alloc(&start, ncells);
+        tmp_alloc(&cnt, ncells);
+        tmp_alloc(&ioff, ncells);
+        tmp_alloc(&sums, div_up(ncells, kScanTile) + 1);
+        tmp_alloc(&scal, 2);
+        NLH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * ncells, s));
+        NLH_CUDA(cudaMemsetAsync(scal, 0, sizeof(int) * 2, s));
+        const int gb = 152 * 8;
+        k_cell_keys<<<gb, 256, 0, s>>>(features, N, P.D, L, d_win, d_center, P.scale, n, u, keys,
+                                       hist);
+        NLH_CHECK_LAUNCH();
+        int64_t tot = exclusive_scan(P, hist, start, ncells, s, sums, scal);
+        NLH_REQUIRE(tot == LN, "internal: cell histogram total %lld != L*N", (long long)tot);
+        P.perm = P.alloc<int32_t>(LN);
+        NLH_CUDA(cudaMemcpyAsync(cnt, start, sizeof(int) * ncells, cudaMemcpyDeviceToDevice, s));
+        k_scatter<<<gb, 256, 0, s>>>(keys, N, L, n3, cnt, P.perm);
+        NLH_CHECK_LAUNCH();
+        k_item_counts<<<gb, 256, 0, s>>>(hist, ncells, P.kmax, cnt, scal + 1);
+        NLH_CHECK_LAUNCH();
+        P.n_items = exclusive_scan(P, cnt, ioff, ncells, s, sums, scal);
+        int occ = 0;
+        NLH_CUDA(cudaMemcpyAsync(&occ, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        P.items = P.alloc<int4>(P.n_items);
+        k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n3, P.kmax, P.items);
+        NLH_CHECK_LAUNCH();
+        // weights in sorted order
+        double inv_i0b = 1.0 / std::cyl_bessel_i(0.0, P.kb_beta);
+        const size_t nw = (size_t)LN * 3 * P.W2;
+        if (P.precision & 1) P.wts64 = P.alloc<double>(nw);
+        if (P.precision & 2) P.wts32 = P.alloc<float>(nw);
+        k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, P.kb_beta, inv_i0b, P.wts64, P.wts32);
+        NLH_CHECK_LAUNCH();
+        NLH_CUDA(cudaStreamSynchronize(s));
+        P.occupied = occ;
+    } catch (...) {
+        for (void *ptr : tmp) cudaFree(ptr);
+        throw;
+    }
+    for (void *ptr : tmp) cudaFree(ptr);
+
+    // tables, grids, outputs, solver workspace
+    if (P.precision & 1) {
+        P.tab64 = P.alloc<double>(n);
+        P.tw64 = P.alloc<double2>(n / 2);
+        P.grid64 = P.alloc<double>((size_t)L * n3);
+        NLH_CUDA(cudaMemsetAsync(P.grid64, 0, sizeof(double) * L * n3, s));
+        P.d64 = P.alloc<double>(N);
+    }
+    if (P.precision & 2) {
+        P.tab32 = P.alloc<float>(n);
+        P.tw32 = P.alloc<float2>(n / 2);
+        P.grid32 = P.alloc<float>((size_t)L * n3);
+        NLH_CUDA(cudaMemsetAsync(P.grid32, 0, sizeof(float) * L * n3, s));
+        P.d32 = P.alloc<double>(N);
+    }
+    P.Y = P.alloc<double>(LN);
+    P.w = P.alloc<double>(N);
+    P.r = P.alloc<double>(N);
+    P.p = P.alloc<double>(N);
+    P.q = P.alloc<double>(N);
+    P.t = P.alloc<double>(N);
+    P.rhs = P.alloc<double>(N);
+    P.pinv = P.alloc<double>(N);
+    P.partials = P.alloc<double>((size_t)kRedBlocks * 12);
+    P.st = P.alloc<SolveState>(1);
+    P.hist = P.alloc<double>(kMaxHist);
+    NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
+    plan_tables(P, s);
+    plan_degrees(P, s);
+    NLH_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace nlh
+
+using namespace nlh;
+
+extern "C" {
+
+const char *nlh_last_error(void) { return g_err.c_str(); }
+
+const char *nlh_version(void) { return "nlh 0.1 (sm_103a)"; }
+
+nlh_status nlh_patch_features(const double *image, int n1, int n2, int radius, int pad,
+                              double *features, void *stream) {
+    clear_error();
+    try {
+        NLH_REQUIRE(image && features, "nlh_patch_features: NULL pointer");
+        NLH_REQUIRE(n1 >= 1 && n2 >= 1 && radius >= 0 && radius <= 16,
+                    "nlh_patch_features: bad sizes n1=%d n2=%d radius=%d", n1, n2, radius);
+        NLH_REQUIRE(pad == 0 || pad == 1, "nlh_patch_features: pad must be 0 or 1");
+        cudaStream_t s = (cudaStream_t)stream;
+        int64_t total = (int64_t)n1 * n2 * (2 * radius + 1) * (2 * radius + 1);
+        int blocks = (int)std::min<int64_t>(div_up(total, 256), 152 * 16);
+        k_patch_features<<<blocks, 256, 0, s>>>(image, n1, n2, radius, pad, features);
+        NLH_CHECK_LAUNCH();
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const double *features,
+                           void *stream) {
+    clear_error();
+    nlh_plan_s *P = nullptr;
+    try {
+        NLH_REQUIRE(out && desc && features && desc->windows, "nlh_plan_create: NULL pointer");
+        *out = nullptr;
+        const nlh_plan_desc &d = *desc;
+        NLH_REQUIRE(d.N >= 2 && d.N <= (int64_t)1 << 30, "nlh_plan_create: N=%lld out of range",
+                    (long long)d.N);
+        NLH_REQUIRE(d.D >= 1 && d.L >= 1 && d.L <= 64, "nlh_plan_create: D=%d L=%d", d.D, d.L);
+        NLH_REQUIRE(d.n_os >= 32 && d.n_os <= 256 && (d.n_os & (d.n_os - 1)) == 0,
+                    "nlh_plan_create: n_os=%d must be a power of two in [32, 256]", d.n_os);
+        NLH_REQUIRE(d.M >= 4 && d.M <= d.n_os && d.M % 2 == 0,
+                    "nlh_plan_create: M=%d must be even, 4 <= M <= n_os", d.M);
+        NLH_REQUIRE(d.m >= 2 && d.m <= 8 && 2 * d.m < d.n_os, "nlh_plan_create: m=%d", d.m);
+        NLH_REQUIRE(d.sigma > 0.0 && std::isfinite(d.sigma), "nlh_plan_create: sigma=%g",
+                    d.sigma);
+        NLH_REQUIRE(d.precision >= 1 && d.precision <= 3, "nlh_plan_create: precision=%d",
+                    d.precision);
+        NLH_REQUIRE(d.torus_fill >= 0.0 && d.torus_fill < 1.0, "nlh_plan_create: torus_fill=%g",
+                    d.torus_fill);
+        NLH_REQUIRE((int64_t)d.L * d.N < ((int64_t)1 << 31), "nlh_plan_create: L*N too large");
+        for (int i = 0; i < 3 * d.L; ++i)
+            NLH_REQUIRE(d.windows[i] >= -1 && d.windows[i] < d.D,
+                        "nlh_plan_create: windows[%d]=%d out of range", i, d.windows[i]);
+        P = new nlh_plan_s();
+        build_plan(*P, d, features, (cudaStream_t)stream);
+        *out = P;
+        return NLH_OK;
+    } catch (Failure &f) {
+        delete P;
+        return f.st;
+    } catch (std::bad_alloc &) {
+        delete P;
+        set_error("nlh_plan_create: host allocation failed");
+        return NLH_ERR_OOM;
+    }
+}
+
+nlh_status nlh_plan_set_sigma(nlh_plan plan, double sigma, void *stream) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan, "nlh_plan_set_sigma: NULL plan");
+        NLH_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "nlh_plan_set_sigma: sigma=%g", sigma);
+        cudaStream_t s = (cudaStream_t)stream;
+        plan->sigma = sigma;
+        plan_tables(*plan, s);
+        plan_degrees(*plan, s);
+        NLH_CUDA(cudaStreamSynchronize(s));
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan && info, "nlh_plan_get_info: NULL pointer");
+        info->N = plan->N;
+        info->L = plan->L;
+        info->M = plan->M;
+        info->n_os = plan->n;
+        info->m = plan->m;
+        info->precision = plan->precision;
+        info->sigma = plan->sigma;
+        info->torus_fill = plan->fill;
+        info->scale = plan->scale;
+        info->sigma_torus = plan->sigma * plan->scale;
+        info->max_range = plan->R;
+        info->n_items = plan->n_items;
+        info->occupied_cells = plan->occupied;
+        error_estimates(plan->sigma, plan->R, plan->fill, plan->M, &info->est_trunc_err,
+                        &info->est_alias_err);
+        info->device_bytes = plan->bytes;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_destroy(nlh_plan plan) {
+    clear_error();
+    delete plan;
+    return NLH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+"""Python binding of libnlh (include/nlh.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this
+module converts torch CUDA tensors to device pointers and the current torch
+stream to a cudaStream_t.  It raises if the native library cannot be loaded:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libnlh.so")
+_lock = threading.Lock()
+_lib = None
+
+NLH_OK, NLH_ERR_NOT_CONVERGED = 0, 1
+NLH_FP64, NLH_FP32 = 0, 1
+CG, PCG_JACOBI, PCG_DEFLATED, CG_DEFLATED = 0, 1, 2, 3
+SOLVE_FP64, SOLVE_MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
+                -4: "ERR_BREAKDOWN", -5: "ERR_TIMEOUT"}
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("N", C.c_int64), ("D", C.c_int), ("L", C.c_int),
+                ("windows", C.POINTER(C.c_int32)), ("sigma", C.c_double), ("M", C.c_int),
+                ("n_os", C.c_int), ("m", C.c_int), ("precision", C.c_int),
+                ("torus_fill", C.c_double), ("max_items_pts", C.c_int)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("N", C.c_int64), ("L", C.c_int), ("M", C.c_int), ("n_os", C.c_int),
+                ("m", C.c_int), ("precision", C.c_int), ("sigma", C.c_double),
+                ("torus_fill", C.c_double), ("scale", C.c_double), ("sigma_torus", C.c_double),
+                ("max_range", C.c_double), ("n_items", C.c_int64),
+                ("occupied_cells", C.c_int64), ("est_trunc_err", C.c_double),
+                ("est_alias_err", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("method", C.c_int),
+                ("arith", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
+                ("x0", C.c_void_p), ("diag_scale", C.c_void_p), ("hist", C.c_void_p),
+                ("hist_len", C.c_int), ("check_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("matvecs_fp64", C.c_int),
+                ("matvecs_fp32", C.c_int), ("rel_res", C.c_double),
+                ("rel_res_true", C.c_double), ("seconds", C.c_double),
+                ("used_fallback", C.c_int), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every entry point of include/nlh.h with its ctypes signature.
+SIGNATURES = {
+    "nlh_patch_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_void_p, C.c_void_p]),
+    "nlh_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(PlanDesc), C.c_void_p,
+                                  C.c_void_p]),
+    "nlh_plan_set_sigma": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
+    "nlh_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
+    "nlh_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                             C.c_void_p, C.c_void_p]),
+    "nlh_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                            C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
+    "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
+    "nlh_last_error": (C.c_char_p, []),
+    "nlh_version": (C.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libnlh.so (building it in-tree first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH) and build_if_missing:
+            from . import build_native
+            build_native.build()
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libnlh.so not found at %s; run __graft_entry__.build()" % _LIB_PATH)
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class NLHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+def _check(status: int, allow_not_converged: bool = False) -> int:
+    if status == NLH_OK or (allow_not_converged and status == NLH_ERR_NOT_CONVERGED):
+        return status
+    raise NLHError(status, load().nlh_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(st.cuda_stream)
+
+
+def _dptr(t, n: Optional[int] = None) -> int:
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return int(t.data_ptr())
+
+
+def patch_features(image, radius: int, pad: str = "reflect", stream=None):
+    """(n1 n2, (2 radius + 1)^2) patch features of a CUDA float64 image."""
+    torch = _torch()
+    n1, n2 = image.shape
+    D = (2 * radius + 1) ** 2
+    out = torch.empty((n1 * n2, D), dtype=torch.float64, device=image.device)
+    _check(load().nlh_patch_features(_dptr(image), n1, n2, radius, 1 if pad == "reflect" else 0,
+                                     _dptr(out), _stream_ptr(stream)))
+    return out
+
+
+@dataclass
+class SolveResult:
+    u: object
+    info: dict
+    hist: np.ndarray
+
+
+class Plan:
+    """An NFFT plan for one feature matrix (see nlh_plan_create)."""
+
+    def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
+                 precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
+                 stream=None):
+        lib = load()
+        N, D = features.shape
+        win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
+        self._win = win
+        desc = PlanDesc(N=N, D=D, L=win.shape[0],
+                        windows=win.ctypes.data_as(C.POINTER(C.c_int32)), sigma=float(sigma),
+                        M=M, n_os=n_os, m=m, precision=precision,
+                        torus_fill=float(torus_fill), max_items_pts=max_items_pts)
+        h = C.c_void_p()
+        _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
+                                   _stream_ptr(stream)))
+        self._h = h
+        self.N = N
+        self.L = win.shape[0]
+
+    @classmethod
+    def from_image(cls, image, radius: int, windows, sigma: float, pad: str = "reflect",
+                   **kw):
+        feats = patch_features(image, radius, pad, kw.get("stream"))
+        return cls(feats, windows, sigma, **kw)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().nlh_plan_get_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def set_sigma(self, sigma: float, stream=None):
+        _check(load().nlh_plan_set_sigma(self._h, float(sigma), _stream_ptr(stream)))
+
+    def matvec(self, x, op: int = 0, precision: int = NLH_FP64, alpha: float = 0.0, out=None,
+               stream=None):
+        torch = _torch()
+        y = out if out is not None else torch.empty_like(x)
+        _check(load().nlh_matvec(self._h, op, precision, float(alpha), _dptr(x, self.N),
+                                 _dptr(y, self.N), _stream_ptr(stream)))
+        return y
+
+    def solve(self, alpha: float, b, tol: float = 1e-6, maxit: int = 200,
+              method: int = PCG_DEFLATED, arith: int = SOLVE_FP64, inner_tol: float = 0.0,
+              max_outer: int = 0, x0=None, diag_scale=None, u=None, check_every: int = 0,
+              hist_len: int = 256, stream=None) -> SolveResult:
+        torch = _torch()
+        u = u if u is not None else torch.empty_like(b)
+        hist = np.zeros(hist_len)
+        opts = SolveOpts(tol=tol, maxit=maxit, method=method, arith=arith, inner_tol=inner_tol,
+                         max_outer=max_outer,
+                         x0=None if x0 is None else _dptr(x0, self.N),
+                         diag_scale=None if diag_scale is None else _dptr(diag_scale, self.N),
+                         hist=hist.ctypes.data, hist_len=hist_len, check_every=check_every)
+        info = SolveInfo()
+        st = load().nlh_solve(self._h, float(alpha), _dptr(b, self.N), _dptr(u, self.N),
+                              C.byref(opts), C.byref(info), _stream_ptr(stream))
+        _check(st, allow_not_converged=True)
+        d = info.as_dict()
+        n = (d["iters"] + 1) if arith == SOLVE_FP64 else d["outer"]
+        return SolveResult(u, d, hist[:max(0, min(n, hist_len))].copy())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().nlh_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,182 @@
+"""GPU parity of the NFFT matvec against the CPU oracle (through the C ABI).
+
+Tolerances (relative, max-norm over the output vector):
+  * FP64 path at tight NFFT parameters (M = 64, n_os = 128, m = 8, fill 0.5)
+    vs the oracle's direct Gaussian sum: 1e-10.  At these parameters the
+    truncation term erfc(pi sigma_s (M/2 - 1)) ~ 1e-17, the alias term
+    exp(-((1 - fill)/sigma_s)^2) ~ 1e-28 and the Kaiser-Bessel window error
+    ~ 1e-15, so 1e-10 leaves room for the O(N) rounding of the sums.
+  * FP64 path at the configured parameters (M = 32, n_os = 64, m = 4) vs the
+    oracle's truncated-Fourier kernel sum at the same torus map: 1e-6
+    (only the window error of the NFFT remains), and vs the direct Gaussian
+    sum: within 10 x the a-priori estimate.
+  * FP32 path vs the FP64 path at the same parameters: 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2407_06834_gb300.inputs import random_vector, raster_windows
+from gpu_helpers import cuda, host, image, make_plan, relmax, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2407_06834_gb300 import nlh  # noqa: E402
+
+SIGMA = 0.2
+
+
+@pytest.mark.parametrize("shape,radius,pad", [((17, 23), 1, "reflect"), ((8, 5), 2, "zero"),
+                                              ((64, 64), 1, "reflect"), ((1, 1), 1, "reflect")])
+def test_patch_features_bit_exact(shape, radius, pad):
+    img = image(*shape)
+    got = host(nlh.patch_features(cuda(img), radius, pad))
+    np.testing.assert_array_equal(got, orc.patch_features(img, radius, pad))
+
+
+@pytest.fixture(scope="module")
+def img64():
+    img = image(64)
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    return img, coords
+
+
+def test_fp64_tight_parameters_match_direct_sum(img64):
+    img, coords = img64
+    P = make_plan(img, M=64, n_os=128, m=8, fill=0.5, precision=1)
+    for seed in (1, 2):
+        v = random_vector(img.size, seed)
+        y = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+        ref = orc.gamma_full_matvec(coords, SIGMA, v)
+        assert relmax(y, ref) < 1e-10, relmax(y, ref)
+
+
+def test_fp64_ragged_image_tight(img64):
+    img = image(37, 53, seed=3)
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    P = make_plan(img, M=64, n_os=128, m=8, fill=0.5, precision=1, kmax=7)
+    v = random_vector(img.size, 4)
+    y = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+    assert relmax(y, orc.gamma_full_matvec(coords, SIGMA, v)) < 1e-10
+
+
+def test_configured_parameters_window_error_only(img64):
+    img, coords = img64
+    P = make_plan(img, precision=3)
+    info = P.info()
+    fill, s = info["torus_fill"], info["scale"]
+    tc, s_orc = orc.torus_map(coords, fill)
+    assert s == pytest.approx(s_orc, rel=1e-14)
+    v = random_vector(img.size, 5)
+    y64 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+    trig = orc.trig_full_matvec(tc, s * SIGMA, 32, v)
+    assert relmax(y64, trig) < 1e-6, relmax(y64, trig)
+    ref = orc.gamma_full_matvec(coords, SIGMA, v)
+    est = max(info["est_trunc_err"], info["est_alias_err"])
+    scale = np.abs(v).sum() / np.max(np.abs(ref))
+    assert relmax(y64, ref) < 10 * est * scale + 1e-6
+    y32 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP32))
+    assert relmax(y32, y64) < 1e-5, relmax(y32, y64)
+
+
+def test_error_falls_with_cutoff_m(img64):
+    img, coords = img64
+    fill = 0.55
+    tc, s = orc.torus_map(coords, fill)
+    v = np.abs(random_vector(img.size, 6))
+    trig = orc.trig_full_matvec(tc, s * SIGMA, 32, v)
+    errs = []
+    for m in (2, 3, 4, 5, 6):
+        P = make_plan(img, m=m, fill=fill, precision=1)
+        errs.append(relmax(host(P.matvec(cuda(v), precision=nlh.NLH_FP64)), trig))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-9
+
+
+def test_error_falls_with_bandwidth_M(img64):
+    img, coords = img64
+    v = np.abs(random_vector(img.size, 7))
+    ref = orc.gamma_full_matvec(coords, SIGMA, v)
+    errs = []
+    for M, n in ((8, 32), (16, 32), (24, 64), (32, 64), (48, 128)):
+        P = make_plan(img, M=M, n_os=n, m=8 if n > 32 else 6, fill=0.5, precision=1)
+        errs.append(relmax(host(P.matvec(cuda(v), precision=nlh.NLH_FP64)), ref))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+
+
+def test_laplacian_ops_invariants(img64):
+    img, coords = img64
+    P = make_plan(img, precision=3)
+    N = img.size
+    one = cuda(np.ones(N))
+    for prec, tol in ((nlh.NLH_FP64, 1e-12), (nlh.NLH_FP32, 1e-5)):
+        d = host(P.matvec(one, op=0, precision=prec))
+        L1 = host(P.matvec(one, op=1, precision=prec))
+        assert np.max(np.abs(L1)) < tol * np.max(d)
+        A1 = host(P.matvec(one, op=2, precision=prec, alpha=0.5))
+        assert np.max(np.abs(A1 - 0.5)) < tol * np.max(d)
+    v, w = random_vector(N, 8), random_vector(N, 9)
+    Lv = host(P.matvec(cuda(v), op=1))
+    Lw = host(P.matvec(cuda(w), op=1))
+    assert w @ Lv == pytest.approx(v @ Lw, rel=1e-12)
+    # degrees against the oracle's eta = Gamma 1 (diagonal removed)
+    eta = orc.degrees(coords, SIGMA)
+    d = host(P.matvec(one, op=0))
+    assert relmax(d - 1.0, eta) < 1e-5
+
+
+def test_constant_image_complete_graph():
+    """Identical features: Gamma_full = 1 1^T up to the NFFT error."""
+    img = np.full((16, 16), 0.4)
+    P = make_plan(img, precision=3)
+    v = random_vector(256, 10)
+    y = host(P.matvec(cuda(v), precision=nlh.NLH_FP64))
+    assert relmax(y, np.full(256, v.sum())) < 1e-6
+    Lv = host(P.matvec(cuda(v), op=1, precision=nlh.NLH_FP64))
+    np.testing.assert_allclose(Lv, 256 * v - v.sum() * np.ones(256), atol=1e-5 * 256 * np.abs(v).max())
+
+
+def test_full_size_512_sampled_rows():
+    """The timed workload (512 x 512, 3 windows, M = 32, n_os = 64, m = 4):
+    sampled rows against direct sums, and FP32 against FP64 everywhere."""
+    img = image(512)
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    P = make_plan(img, precision=3)
+    info = P.info()
+    v = random_vector(img.size, 11)
+    y64 = host(P.matvec(cuda(v), precision=nlh.NLH_FP64))
+    y32 = host(P.matvec(cuda(v), precision=nlh.NLH_FP32))
+    assert rel(y32, y64) < 1e-5
+    rng = np.random.Generator(np.random.PCG64(12))
+    rows = np.sort(rng.choice(img.size, 48, replace=False))
+    ref = orc.gamma_full_rows(coords, SIGMA, v, rows)
+    est = max(info["est_trunc_err"], info["est_alias_err"])
+    err = np.max(np.abs(y64[rows] - ref)) / np.max(np.abs(ref))
+    assert err < 10 * est * np.abs(v).sum() / np.max(np.abs(ref)) + 1e-6, err
+
+
+def test_set_sigma_matches_fresh_plan(img64):
+    img, coords = img64
+    P = make_plan(img, M=64, n_os=128, m=8, fill=0.5, precision=1)
+    P.set_sigma(0.3)
+    v = random_vector(img.size, 13)
+    y = host(P.matvec(cuda(v), precision=nlh.NLH_FP64))
+    assert relmax(y, orc.gamma_full_matvec(coords, 0.3, v)) < 1e-10
+
+
+def test_argument_errors():
+    img = image(8)
+    P = make_plan(img, precision=1)
+    x = cuda(np.ones(64))
+    with pytest.raises(nlh.NLHError):
+        P.matvec(x, precision=nlh.NLH_FP32)        # FP32 path not built
+    with pytest.raises(nlh.NLHError):
+        P.matvec(x, op=7)
+    with pytest.raises(nlh.NLHError):
+        make_plan(img, n_os=48)                    # not a power of two
+    with pytest.raises(nlh.NLHError):
+        make_plan(img, M=5)
