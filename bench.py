@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the NFFT nonlocal-denoising hot path (one JSON line).
+
+A step is one pass of the whole path over one synthetic image: patch
+features, the plan (torus map, sort by cell, weights, tables, degrees), and
+a deflated Jacobi-PCG solve of (alpha I + L) u = alpha f to relative
+residual 1e-6 in the mixed form (FP32-NFFT inner solves, FP64 refinement
+residuals).  The metric is NFFT matvec throughput in Gpts/s: point-windows
+(N * L per matvec) pushed through the NFFT per second, over the whole step;
+the seconds-to-solve of the FP64 and mixed forms are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun): the
+path has no exchange step, so there is no data collective; the ranks only
+meet at the timing barriers and the max-over-ranks of the step time.
+--impl reference times the CPU FP64 oracle (direct O(N^2) sums) on the host
+cores on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2407_06834_gb300.inputs import WORKLOADS  # noqa: E402
+
+METRIC = "NFFT kernel matvec Gpts/s (whole features+plan+solve step, mixed form)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Non-tensor ALU peaks derived from unit counts and the 2070 MHz max clock:
+# FP32: 152 SMs x 128 FMA lanes x 2 flop; FP64: GB300 nominal 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="img512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=0, help="oracle row sample (0 = auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_rows_baseline(wl, rows: int, seed: int = 99):
+    """Direct O(N^2) oracle sums on a row sample; Gpts/s = rows * L / t."""
+    from oracle import oracle as orc
+    img = wl.image()
+    coords = orc.image_coords(img, wl.radius, wl.windows, wl.pad)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal(wl.N)
+    r = np.sort(rng.choice(wl.N, rows, replace=False))
+    t0 = time.perf_counter()
+    orc.gamma_full_rows(coords, wl.sigma, v, r)
+    dt = time.perf_counter() - t0
+    return {"value": rows * wl.L / dt / 1e9, "unit": "Gpts/s", "cores": orc.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": "%d random rows of the direct FP64 sum Gamma_full v on %s (N=%d, L=%d)"
+                      % (rows, wl.name, wl.N, wl.L)}
+
+
+def auto_rows(wl, target_s=12.0):
+    from oracle import oracle as orc
+    probe = oracle_rows_baseline(wl, 64)
+    per_row = probe["seconds"] / 64
+    return int(max(64, min(wl.N, target_s / max(per_row, 1e-9)))), orc.num_threads()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    rows = args.cpu_rows or max(64, auto_rows(wl, target_s=8.0)[0] // max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rows_baseline(wl, max(16, rows // 8))
+    times, vals = [], []
+    for k in range(args.steps):
+        b = oracle_rows_baseline(wl, rows, seed=100 + k)
+        times.append(b["seconds"])
+        vals.append(b["value"])
+    total = sum(times)
+    value = rows * wl.L * args.steps / total / 1e9
+    cpu = {"value": value, "unit": "Gpts/s", "cores": b["cores"], "kind": "oracle",
+           "sample": b["sample"] + " per step"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: %dx%d synthetic image, 3x3 reflect patches, L=%d, "
+                                   "sigma=%g" % (wl.name, wl.n1, wl.n2, wl.L, wl.sigma),
+                       "sample_rows": rows},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_06834_gb300 import nlh
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib = nlh.load()
+    wl = WORKLOADS[args.workload]
+    img_np = wl.image()
+    img = torch.as_tensor(img_np, device=dev)
+    N, L = wl.N, wl.L
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(image, u):
+        P = nlh.Plan.from_image(image, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                                n_os=wl.n_os, m=wl.m, precision=3)
+        b = image.reshape(-1) * wl.alpha
+        res = P.solve(wl.alpha, b, tol=wl.tol, arith=nlh.SOLVE_MIXED, inner_tol=1e-3, u=u)
+        P.close()
+        return res
+
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(step(img, u).info)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    lib.nlh_profile_reset()
+    launches0 = lib.nlh_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        lib.nlh_profile_enable(1)
+        step_infos = []
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step_infos.append(step(img, u).info)
+            ev[k][1].record(stream)
+        lib.nlh_profile_enable(0)
+        barrier()
+    launches = lib.nlh_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    # 2 degree matvecs per plan (FP64 and FP32) + the solve's matvecs
+    mv = [i["matvecs_fp64"] + i["matvecs_fp32"] + 2 for i in step_infos]
+    pts = float(N * L * sum(mv))
+    t_all = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    p_all = torch.tensor([pts], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p_all, op=dist.ReduceOp.SUM)
+    value = float(p_all.item()) / (float(t_all.item()) * 1e-3) / 1e9
+
+    # per-kernel-class device time inside the timed region
+    prof = {}
+    names = ["spread64", "spread32", "conv64", "conv32", "interp64", "interp32", "epilogue",
+             "krylov", "plan"]
+    import ctypes as C
+    for c, nm in enumerate(names):
+        cl, cm = C.c_int64(0), C.c_double(0)
+        lib.nlh_profile_read(c, C.byref(cl), C.byref(cm))
+        if cl.value:
+            prof[nm] = {"launches": cl.value, "ms": cm.value}
+    lib.nlh_profile_reset()
+    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+    W2 = 2 * wl.m
+    flop_per_launch = 2.0 * N * L * W2 ** 3   # (2m)^3 FMAs per point-window
+    roof = None
+    if dom and dom.startswith(("spread", "interp")):
+        avg_s = prof[dom]["ms"] / prof[dom]["launches"] * 1e-3
+        peak = FP64_PEAK_TFLOPS if dom.endswith("64") else FP32_PEAK_TFLOPS
+        ach = flop_per_launch / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: %s" % ("GB300 nominal FP64 1.25 TFLOP/s"
+                                                if dom.endswith("64") else
+                                                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")}
+    elif dom:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": None, "unit": "GB/s",
+                "frac": None, "traffic": None}
+
+    # ---- end to end through the public API with host buffers
+    img_h = torch.empty((wl.n1, wl.n2), dtype=torch.float64, pin_memory=True)
+    img_h.copy_(torch.as_tensor(img_np))
+    u_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    img_d = torch.empty_like(img)
+    e2e_ms = []
+    barrier()
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        img_d.copy_(img_h, non_blocking=True)
+        info = step(img_d, u).info
+        u_h.copy_(u, non_blocking=True)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b_))
+        mv_e = info["matvecs_fp64"] + info["matvecs_fp32"] + 2
+    e2e_val = N * L * mv_e / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+
+    # ---- seconds to 1e-6, FP64 form vs mixed form (plan prebuilt)
+    P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                            n_os=wl.n_os, m=wl.m, precision=3)
+    bvec = img.reshape(-1) * wl.alpha
+    solve_s = {}
+    t0 = time.perf_counter()
+    for _ in range(3):
+        Q = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                                n_os=wl.n_os, m=wl.m, precision=3)
+        Q.close()
+    torch.cuda.synchronize()
+    solve_s["plan_seconds"] = (time.perf_counter() - t0) / 3
+    for nm, ar in (("fp64", nlh.SOLVE_FP64), ("mixed", nlh.SOLVE_MIXED)):
+        P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
+        r = P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
+        solve_s[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
+                       "rel_res_fp64": r.info["rel_res_true"]}
+    # kernel-only matvec throughput
+    x = torch.randn(N, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    mv_gpts = {}
+    for nm, prec in (("fp64", nlh.NLH_FP64), ("fp32", nlh.NLH_FP32)):
+        for _ in range(3):
+            P.matvec(x, op=2, precision=prec, alpha=wl.alpha, out=y)
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            P.matvec(x, op=2, precision=prec, alpha=wl.alpha, out=y)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        mv_gpts[nm] = N * L / (a.elapsed_time(b_) / 10 * 1e-3) / 1e9
+    pinfo = P.info()
+    P.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rows = args.cpu_rows or auto_rows(wl)[0]
+        cpu = oracle_rows_baseline(wl, rows)
+        cpu.pop("seconds", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (FP32 NFFT, FP64 Krylov and refinement)",
+        "data": "synthetic (seeded piecewise-constant image + N(0,0.1^2) noise)",
+        "config": {"workload": "%s: %dx%d image (N=%d), 3x3 reflect patches -> L=%d windows "
+                               "of 3 dims, sigma=%g, alpha=%g, M=%d, n_os=%d, m=%d, "
+                               "tol=%g" % (wl.name, wl.n1, wl.n2, N, L, wl.sigma, wl.alpha,
+                                            wl.M, wl.n_os, wl.m, wl.tol),
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "torus_fill": pinfo["torus_fill"], "work_items": pinfo["n_items"]},
+        "solve_seconds": solve_s,
+        "matvec_gpts_kernel_only": mv_gpts,
+        "iters_per_step": statistics.mean(i["iters"] for i in step_infos),
+        "matvecs_per_step": statistics.mean(mv),
+        "e2e": {"value": e2e_val, "unit": "Gpts/s", "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "roofline": roof,
+        "kernel_ms": prof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

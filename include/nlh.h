@@ -113,7 +113,9 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
  *                                           cancels, Sec. 2.3)
  *   op 2: y = (alpha I + L) x
  * precision: NLH_FP64 or NLH_FP32 (the NFFT stages; the output is FP64).
- * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers). */
+ * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers).  The
+ * call does not synchronise: a device-side failure (NLH_ERR_TIMEOUT) is
+ * reported by the next synchronising call on the plan. */
 nlh_status nlh_matvec(nlh_plan plan, int op, int precision, double alpha,
                       const double *x, double *y, void *stream);
 
@@ -178,6 +180,23 @@ const char *nlh_last_error(void);
 
 /* Library version string. */
 const char *nlh_version(void);
+
+/* ---- Instrumentation (not part of the paper's method) ------------------
+ * nlh_kernel_launches: number of CUDA kernels the library has launched in
+ * this process.  nlh_profile_enable(1) makes the library bracket each launch
+ * of the classes below with CUDA events on the launch's own stream;
+ * nlh_profile_read synchronises those events and returns the launch count
+ * and summed device time of one class; nlh_profile_reset drops the records.
+ * Profiling is process-wide and off by default. */
+enum {
+    NLH_K_SPREAD64 = 0, NLH_K_SPREAD32, NLH_K_CONV64, NLH_K_CONV32,
+    NLH_K_INTERP64, NLH_K_INTERP32, NLH_K_EPILOGUE, NLH_K_KRYLOV, NLH_K_PLAN,
+    NLH_K_NCLASSES
+};
+int64_t nlh_kernel_launches(void);
+nlh_status nlh_profile_enable(int enable);
+nlh_status nlh_profile_reset(void);
+nlh_status nlh_profile_read(int kernel_class, int64_t *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

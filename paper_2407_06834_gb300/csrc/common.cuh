@@ -2,11 +2,17 @@
 //
 // Device data layout of a plan (all device arrays are owned by the plan):
 //   perm     [L*N]   int32   sorted position s (window l = s / N) -> pixel
-//   items    [n_items] int4  {window, cell (z*n+y)*n+x, first sorted
-//                             position, point count}; the points of one item
-//                             share one grid cell, hence one stencil
-//   wts64/32 [L*N][3][2m]    Kaiser-Bessel weights of each sorted point per
-//                             dim for the grid points cell-m+1 .. cell+m
+//   items    [n_items] int4  {window << 16 | lz << 6 | ly << 3 | lx, tile,
+//                             first sorted position, point count}: (lx, ly,
+//                             lz) is the cell inside its kTile^3 tile; the
+//                             points of one item share one grid cell, hence
+//                             one stencil.  Items are ordered tile-major.
+//   units    [n_units] int4  {window, tile (z*nt+y)*nt+x, first item, item
+//                             count}: a run of items inside one tile with at
+//                             most ~kUnitPoints points; one CTA per unit
+//   wts64/32 [L*N][PWP]      Kaiser-Bessel weights of each sorted point:
+//                             3 dims x 2m grid points cell-m+1 .. cell+m,
+//                             the record padded to PWP values (16 bytes)
 //   grid64/32 [L][n][n][n]   oversampled grids, x fastest; zero between
 //                             matvecs (the epilogue clears them)
 //   tab64/32 [n]             per-dim Fourier multiplier in bit-reversed order
@@ -42,7 +48,27 @@ struct Failure {
         }                                                                      \
     } while (0)
 
-#define NLH_CHECK_LAUNCH() NLH_CUDA(cudaGetLastError())
+void count_launch();
+
+#define NLH_CHECK_LAUNCH()                                                     \
+    do {                                                                       \
+        ::nlh::count_launch();                                                 \
+        NLH_CUDA(cudaGetLastError());                                          \
+    } while (0)
+
+// Brackets the launches issued in its scope with CUDA events on stream s
+// when profiling is enabled (profile.cu).
+class ProfRange {
+  public:
+    ProfRange(int cls, cudaStream_t s);
+    ~ProfRange();
+    ProfRange(const ProfRange &) = delete;
+    ProfRange &operator=(const ProfRange &) = delete;
+
+  private:
+    int idx_;
+    cudaStream_t s_;
+};
 
 #define NLH_REQUIRE(cond, ...)                                                 \
     do {                                                                       \
@@ -68,6 +94,9 @@ struct SolveState {
 };
 
 constexpr int kMaxHist = 4096;
+constexpr int kTile = 8;          // tile edge in grid cells (spread/interp units)
+constexpr int kUnitPoints = 1024; // points per work unit before a tile is split
+constexpr int kUnitItems = 256;   // items per work unit (staged in shared memory)
 
 struct Plan {
     int64_t N = 0;
@@ -78,6 +107,8 @@ struct Plan {
     // device arrays
     int32_t *perm = nullptr;
     int4 *items = nullptr;
+    int4 *units = nullptr;
+    int64_t n_units = 0;
     double *wts64 = nullptr;
     float *wts32 = nullptr;
     double *tab64 = nullptr;
@@ -87,21 +118,26 @@ struct Plan {
     double *grid64 = nullptr;
     float *grid32 = nullptr;
     double *Y = nullptr;
+    double *xs = nullptr;         // [L*N] matvec input in sorted order (T)
     double *d64 = nullptr, *d32 = nullptr;
     // solver workspace
     double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
            *t = nullptr, *rhs = nullptr, *pinv = nullptr;
     double *partials = nullptr;   // kRedBlocks * 12 doubles
     SolveState *st = nullptr;     // device
+    int *err = nullptr;           // device error word (bounded waits that gave up)
     SolveState *st_host = nullptr; // pinned mirror
     double *hist = nullptr;       // device, kMaxHist
     std::vector<void *> allocs;
     int64_t bytes = 0;
+    // Device memory comes from the stream-ordered pool allocator on the
+    // stream of the current call; it is released on the last such stream.
+    cudaStream_t stream = nullptr;
 
     template <typename T> T *alloc(size_t count) {
         void *ptr = nullptr;
         if (count == 0) count = 1;
-        NLH_CUDA(cudaMalloc(&ptr, count * sizeof(T)));
+        NLH_CUDA(cudaMallocAsync(&ptr, count * sizeof(T), stream));
         allocs.push_back(ptr);
         bytes += (int64_t)(count * sizeof(T));
         return static_cast<T *>(ptr);
@@ -153,11 +189,21 @@ __device__ __forceinline__ double reduce_partials(const double *parts, int npart
 
 // ---------------------------------------------------------------- host API (internal)
 void plan_tables(Plan &P, cudaStream_t s);
+// Keep freed pool memory in the process (set once).
+void retain_pool_memory();
+// Throws Failure{NLH_ERR_TIMEOUT} if a kernel recorded a bounded wait that
+// gave up (synchronises s).
+void check_device_error(Plan &P, cudaStream_t s);
 void plan_degrees(Plan &P, cudaStream_t s);
 void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
             double *partials, const int *done, cudaStream_t s);
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Values per padded weight record (a multiple of 16 bytes).
+inline int record_len(int W2, int elem_bytes) {
+    return ((3 * W2 * elem_bytes + 15) / 16) * 16 / elem_bytes;
+}
 
 }  // namespace nlh
 

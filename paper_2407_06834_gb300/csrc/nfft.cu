@@ -15,6 +15,7 @@
 // point.  Spreading flushes each item's accumulators with one atomic add per
 // stencil cell.
 #include "common.cuh"
+#include "async_copy.cuh"
 
 namespace nlh {
 
@@ -36,19 +37,265 @@ template <typename C> __device__ __forceinline__ C cshfl(C a, int o) {
 
 constexpr int kChunk = 32;  // points staged in shared memory at a time
 
-// ------------------------------------------------------------------ spreading
+// A team is NW warps; a CTA holds TPB teams.  Teams synchronise among
+// themselves only (a warp sync, or a named barrier for two-warp teams).
+template <int NW>
+__device__ __forceinline__ void team_sync(int team) {
+    if (NW == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(32 * NW) : "memory");
+    }
+}
+
+// Weight record of one point: 3 x 2m values padded to a multiple of 16
+// bytes so that a chunk of records is one bulk copy.
+template <typename T, int W2>
+constexpr int padded_record() {
+    return ((3 * W2 * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
+}
+
+constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Shared memory of one unit: the tile region (kTile + 2m - 1)^3, per team
+// two staging buffers of kChunk weight records, two mbarriers, a status word
+// and kChunk reduction slots.
+template <typename T, int W2, int TPB>
+struct UnitSmem {
+    static constexpr int E = kTile + W2 - 1, E3 = E * E * E, PWP = padded_record<T, W2>();
+    static constexpr size_t tile = align16(sizeof(T) * E3);
+    static constexpr size_t stage = align16(sizeof(T) * kChunk * PWP);
+    static constexpr size_t team = 2 * stage + 2 * sizeof(uint64_t) + 16 + align16(sizeof(T) * kChunk);
+};
+
+__device__ __forceinline__ void tile_origin(int tile, int n, int &tx0, int &ty0, int &tz0) {
+    const int nt = n / kTile;
+    tx0 = (tile % nt) * kTile;
+    ty0 = ((tile / nt) % nt) * kTile;
+    tz0 = (tile / (nt * nt)) * kTile;
+}
+
+// Item record (see common.cuh): x = window << 16 | lz << 6 | ly << 3 | lx
+// (cell offsets inside the tile), y = tile, z = first sorted position,
+// w = point count.
+__device__ __forceinline__ void item_local(int packed, int &lx, int &ly, int &lz) {
+    lx = packed & 7;
+    ly = (packed >> 3) & 7;
+    lz = (packed >> 6) & 7;
+}
+
+// The (item, chunk) work list of one team inside a unit.  Items are taken
+// dynamically from a CTA-wide counter in shared memory, so teams that draw
+// small items take more of them.
+struct ChunkCursor {
+    int ii, c0, start, cnt, local;
+    __device__ bool valid() const { return ii >= 0; }
+};
+
+template <int NW>
+__device__ __forceinline__ int fetch_item(int *s_next, int *s_slot, int team, int tid) {
+    int idx = 0;
+    if (NW == 1) {
+        if (tid == 0) idx = atomicAdd(s_next, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+    } else {
+        if (tid == 0) *s_slot = atomicAdd(s_next, 1);
+        team_sync<NW>(team);
+        idx = *s_slot;
+        team_sync<NW>(team);
+    }
+    return idx;
+}
+
+__device__ __forceinline__ ChunkCursor make_cursor(const int4 *s_items, int ii, int nit) {
+    if (ii >= nit) return ChunkCursor{-1, 0, 0, 0, 0};
+    int4 it = s_items[ii];
+    return ChunkCursor{ii, 0, it.z, it.w, it.x};
+}
+
+template <int NW>
+__device__ __forceinline__ ChunkCursor next_chunk(const ChunkCursor &c, const int4 *s_items,
+                                                  int nit, int *s_next, int *s_slot, int team,
+                                                  int tid) {
+    ChunkCursor d = c;
+    d.c0 += kChunk;
+    if (d.c0 < d.cnt) return d;
+    return make_cursor(s_items, fetch_item<NW>(s_next, s_slot, team, tid), nit);
+}
+
+// Per-team staging pipeline: thread 0 of the team issues the bulk copy of
+// a chunk's weight records and waits for it (bounded); the team then reads.
 template <typename T, int W2, int NW>
-__global__ void __launch_bounds__(32 * NW)
-k_spread(const int4 *__restrict__ items, const int *__restrict__ perm,
-         const T *__restrict__ wts, const double *__restrict__ v, T *__restrict__ grid, int n,
-         int m, const int *__restrict__ done) {
-    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PW = 3 * W2;
-    __shared__ T sw[kChunk * PW];
-    __shared__ T sv[kChunk];
+struct Stager {
+    static constexpr int PWP = padded_record<T, W2>();
+    T *buf[2];
+    uint64_t *bar;
+    volatile int *flag;
+    uint32_t phase[2];
+    bool pending[2];
+    int team, tid;
+
+    __device__ void issue(int b, const T *wts, const ChunkCursor &c) {
+        if (tid == 0) {
+            const int cn = min(kChunk, c.cnt - c.c0);
+            const uint32_t bytes = (uint32_t)(cn * PWP * sizeof(T));
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[b], bytes);
+            bulk_copy_g2s(buf[b], wts + (int64_t)(c.start + c.c0) * PWP, bytes, &bar[b]);
+        }
+        pending[b] = true;
+    }
+
+    // Returns false if the copy timed out (the team then stops).
+    __device__ bool wait(int b, int *err) {
+        if (tid == 0) *flag = mbar_wait_bounded(&bar[b], phase[b], err) ? 1 : 0;
+        team_sync<NW>(team);
+        bool ok = *flag != 0;
+        if (ok) ok = mbar_try_wait(&bar[b], phase[b]);  // acquire for every reader
+        phase[b] ^= 1u;
+        pending[b] = false;
+        return ok;
+    }
+
+    // On an early exit: wait (bounded) for copies still in flight.
+    __device__ void drain(int *err) {
+        for (int b = 0; b < 2; ++b)
+            if (pending[b] && tid == 0) mbar_wait_bounded(&bar[b], phase[b], err);
+    }
+};
+
+// Team area: two staging buffers, two mbarriers, a status word, a
+// broadcast slot, kChunk reduction values.
+template <typename T, int W2, int NW, int TPB>
+__device__ __forceinline__ Stager<T, W2, NW> make_stager(unsigned char *team_base, int team,
+                                                         int tid) {
+    using SM = UnitSmem<T, W2, TPB>;
+    Stager<T, W2, NW> st;
+    st.buf[0] = reinterpret_cast<T *>(team_base);
+    st.buf[1] = reinterpret_cast<T *>(team_base + SM::stage);
+    st.bar = reinterpret_cast<uint64_t *>(team_base + 2 * SM::stage);
+    st.flag = reinterpret_cast<volatile int *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t));
+    st.phase[0] = st.phase[1] = 0u;
+    st.pending[0] = st.pending[1] = false;
+    st.team = team;
+    st.tid = tid;
+    return st;
+}
+
+// acc[a] += s * w[a] for a = 0..W2-1 (packed FP32 pairs on the FP32 path).
+template <typename T, int W2>
+__device__ __forceinline__ void axpy_line(T (&acc)[W2], T s, const T (&w)[W2]) {
+#pragma unroll
+    for (int a = 0; a < W2; ++a) acc[a] = fma(s, w[a], acc[a]);
+}
+template <int W2>
+__device__ __forceinline__ void axpy_line(float (&acc)[W2], float s, const float (&w)[W2]) {
+    static_assert(W2 % 2 == 0, "even stencil");
+    const unsigned long long ss =
+        ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)__float_as_uint(s);
+#pragma unroll
+    for (int a = 0; a < W2; a += 2) {
+        unsigned long long wv = ((unsigned long long)__float_as_uint(w[a + 1]) << 32) |
+                                (unsigned long long)__float_as_uint(w[a]);
+        unsigned long long av = ((unsigned long long)__float_as_uint(acc[a + 1]) << 32) |
+                                (unsigned long long)__float_as_uint(acc[a]);
+        unsigned long long d;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ss), "l"(wv), "l"(av));
+        acc[a] = __uint_as_float((unsigned)(d & 0xffffffffull));
+        acc[a + 1] = __uint_as_float((unsigned)(d >> 32));
+    }
+}
+
+// sum_a w[a] h[a]
+template <typename T, int W2>
+__device__ __forceinline__ T dot_line(const T (&w)[W2], const T (&h)[W2]) {
+    T in = T(0);
+#pragma unroll
+    for (int a = 0; a < W2; ++a) in = fma(w[a], h[a], in);
+    return in;
+}
+template <int W2>
+__device__ __forceinline__ float dot_line(const float (&w)[W2], const float (&h)[W2]) {
+    unsigned long long acc = 0ull;
+#pragma unroll
+    for (int a = 0; a < W2; a += 2) {
+        unsigned long long wv = ((unsigned long long)__float_as_uint(w[a + 1]) << 32) |
+                                (unsigned long long)__float_as_uint(w[a]);
+        unsigned long long hv = ((unsigned long long)__float_as_uint(h[a + 1]) << 32) |
+                                (unsigned long long)__float_as_uint(h[a]);
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(wv), "l"(hv));
+    }
+    return __uint_as_float((unsigned)(acc & 0xffffffffull)) +
+           __uint_as_float((unsigned)(acc >> 32));
+}
+
+// Load W2 consecutive values from 16-byte aligned shared memory.
+template <typename T, int W2>
+__device__ __forceinline__ void load_line(T (&dst)[W2], const T *src) {
+    constexpr int PER = 16 / sizeof(T);
+    if (W2 % PER == 0) {
+#pragma unroll
+        for (int a = 0; a < W2; a += PER) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(src + a);
+            const T *qv = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int e = 0; e < PER; ++e) dst[a + e] = qv[e];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < W2; ++a) dst[a] = src[a];
+    }
+}
+
+// Shared carve-up common to both kernels: tile region, item records, the
+// CTA's item counter, then TPB team areas.
+template <typename T, int W2, int TPB>
+struct UnitLayout {
+    using SM = UnitSmem<T, W2, TPB>;
+    static constexpr size_t items_off = SM::tile;
+    static constexpr size_t next_off = items_off + sizeof(int4) * kUnitItems;
+    static constexpr size_t teams_off = next_off + 16;
+    static constexpr size_t bytes = teams_off + TPB * SM::team;
+};
+
+// ------------------------------------------------------------------ spreading
+// One CTA per unit.  Each team takes items of the unit; a thread owns PPT
+// (y, z) stencil pairs with their full x line of 2m accumulators, summed in
+// registers over the item's points (all points of an item share the
+// stencil).  Items are then added into the shared tile, and the tile is
+// added into the global grid once (non-zero entries only).  xs holds the
+// input vector in sorted order.
+template <typename T, int W2, int NW, int TPB>
+__global__ void __launch_bounds__(32 * NW * TPB)
+k_spread(const int4 *__restrict__ units, const int4 *__restrict__ items,
+         const T *__restrict__ wts, const T *__restrict__ xs, T *__restrict__ grid, int n,
+         int m, const int *__restrict__ done, int *__restrict__ err) {
+    using SM = UnitSmem<T, W2, TPB>;
+    using LY = UnitLayout<T, W2, TPB>;
+    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PWP = SM::PWP;
+    constexpr int E = SM::E, E3 = SM::E3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
+    int *s_next = reinterpret_cast<int *>(smem_raw + LY::next_off);
     if (done && *done) return;
-    const int4 it = items[blockIdx.x];
-    const int l = it.x, cell = it.y, start = it.z, cnt = it.w;
-    const int tid = threadIdx.x;
+    const int4 un = units[blockIdx.x];
+    const int l = un.x, it0 = un.z, nit = un.w;
+    int tx0, ty0, tz0;
+    tile_origin(un.y, n, tx0, ty0, tz0);
+    const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31;
+    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
+    auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
+    int *s_slot = const_cast<int *>(st.flag) + 1;
+    for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = T(0);
+    for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+    if (threadIdx.x == 0) *s_next = TPB;
+    if (tid == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
     int bb[PPT], cc[PPT];
     bool ok[PPT];
 #pragma unroll
@@ -64,97 +311,182 @@ k_spread(const int4 *__restrict__ items, const int *__restrict__ perm,
 #pragma unroll
         for (int a = 0; a < W2; ++a) acc[k][a] = T(0);
 
-    for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-        const int cn = min(kChunk, cnt - c0);
-        const T *src = wts + (int64_t)(start + c0) * PW;
-        for (int e = tid; e < cn * PW; e += NT) sw[e] = src[e];
-        for (int e = tid; e < cn; e += NT) sv[e] = (T)v[perm[start + c0 + e]];
-        __syncthreads();
+    ChunkCursor cur = make_cursor(s_items, team, nit);
+    T vcur = T(0);
+    if (cur.valid()) {
+        st.issue(0, wts, cur);
+        if (lane < cur.cnt) vcur = xs[cur.start + lane];
+    }
+    int b = 0;
+    while (cur.valid()) {
+        const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_next, s_slot, team, tid);
+        T vnxt = T(0);
+        if (nxt.valid()) {
+            st.issue(b ^ 1, wts, nxt);
+            if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
+        }
+        if (!st.wait(b, err)) {
+            st.drain(err);
+            break;
+        }
+        const T *sw = st.buf[b];
+        const int cn = min(kChunk, cur.cnt - cur.c0);
         for (int j = 0; j < cn; ++j) {
-            const T *wp = sw + j * PW;
+            const T *wp = sw + j * PWP;
             T wx[W2];
+            load_line<T, W2>(wx, wp);
+            const T vj = __shfl_sync(0xffffffffu, vcur, j);
 #pragma unroll
-            for (int a = 0; a < W2; ++a) wx[a] = wp[a];
-            const T vj = sv[j];
+            for (int k = 0; k < PPT; ++k)
+                if (ok[k]) axpy_line(acc[k], vj * wp[W2 + bb[k]] * wp[2 * W2 + cc[k]], wx);
+        }
+        if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
+            int lx0, ly0, lz0;
+            item_local(cur.local, lx0, ly0, lz0);
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (ok[k]) {
-                    T s = vj * wp[W2 + bb[k]] * wp[2 * W2 + cc[k]];
+                    T *row = S + ((lz0 + cc[k]) * E + (ly0 + bb[k])) * E + lx0;
 #pragma unroll
-                    for (int a = 0; a < W2; ++a) acc[k][a] = fma(s, wx[a], acc[k][a]);
+                    for (int a = 0; a < W2; ++a) atomicAdd(&row[a], acc[k][a]);
                 }
+#pragma unroll
+                for (int a = 0; a < W2; ++a) acc[k][a] = T(0);
             }
         }
-        __syncthreads();
+        team_sync<NW>(team);  // every read of buffer b is done before it is refilled
+        cur = nxt;
+        vcur = vnxt;
+        b ^= 1;
     }
+    __syncthreads();
     const int msk = n - 1;
-    const int x0 = cell % n, y0 = (cell / n) % n, z0 = cell / (n * n);
     T *g = grid + (int64_t)l * n * n * n;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (!ok[k]) continue;
-        int y = (y0 - m + 1 + bb[k]) & msk, z = (z0 - m + 1 + cc[k]) & msk;
-        T *row = g + ((int64_t)z * n + y) * n;
-#pragma unroll
-        for (int a = 0; a < W2; ++a) atomicAdd(&row[(x0 - m + 1 + a) & msk], acc[k][a]);
+    for (int e = threadIdx.x; e < E3; e += blockDim.x) {
+        T val = S[e];
+        if (val != T(0)) {
+            int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+            int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                gz = (tz0 - m + 1 + ez) & msk;
+            atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], val);
+        }
     }
 }
 
 // ------------------------------------------------------------------ interpolation
-template <typename T, int W2, int NW>
-__global__ void __launch_bounds__(32 * NW)
-k_interp(const int4 *__restrict__ items, const int *__restrict__ perm,
-         const T *__restrict__ wts, const T *__restrict__ grid, double *__restrict__ Y, int n,
-         int m, int64_t N, const int *__restrict__ done) {
-    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PW = 3 * W2;
-    __shared__ T sw[kChunk * PW];
-    __shared__ T sred[kChunk];
+// One CTA per unit: the tile region of the convolved grid is staged in
+// shared memory; each team holds an item's stencil in registers and sums
+// every point's 2m^3 products.  The per-thread partial sums of a chunk of 32
+// points are reduce-scattered over the warp so that lane j ends with point
+// j's value.
+template <typename T, int W2, int NW, int TPB>
+__global__ void __launch_bounds__(32 * NW * TPB)
+k_interp(const int4 *__restrict__ units, const int4 *__restrict__ items,
+         const int *__restrict__ perm, const T *__restrict__ wts, const T *__restrict__ grid,
+         double *__restrict__ Y, int n, int m, int64_t N, const int *__restrict__ done,
+         int *__restrict__ err) {
+    using SM = UnitSmem<T, W2, TPB>;
+    using LY = UnitLayout<T, W2, TPB>;
+    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PWP = SM::PWP;
+    constexpr int E = SM::E, E3 = SM::E3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
+    int *s_next = reinterpret_cast<int *>(smem_raw + LY::next_off);
     if (done && *done) return;
-    const int4 it = items[blockIdx.x];
-    const int l = it.x, cell = it.y, start = it.z, cnt = it.w;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int4 un = units[blockIdx.x];
+    const int l = un.x, it0 = un.z, nit = un.w;
+    int tx0, ty0, tz0;
+    tile_origin(un.y, n, tx0, ty0, tz0);
+    const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31, warp = tid >> 5;
+    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
+    auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
+    int *s_slot = const_cast<int *>(st.flag) + 1;
+    T *sred = reinterpret_cast<T *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t) + 16);
+    if (tid == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        mbar_fence_init();
+    }
+    for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+    if (threadIdx.x == 0) *s_next = TPB;
     const int msk = n - 1;
-    const int x0 = cell % n, y0 = (cell / n) % n, z0 = cell / (n * n);
     const T *g = grid + (int64_t)l * n * n * n;
+    {
+        constexpr int UNR = 8;
+        for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
+            T vals[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                int e = base + u * blockDim.x;
+                vals[u] = T(0);
+                if (e < E3) {
+                    int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+                    int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                        gz = (tz0 - m + 1 + ez) & msk;
+                    vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                int e = base + u * blockDim.x;
+                if (e < E3) S[e] = vals[u];
+            }
+        }
+    }
+    __syncthreads();
+    ChunkCursor cur = make_cursor(s_items, team, nit);
+    if (cur.valid()) st.issue(0, wts, cur);
+    int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
     int bb[PPT], cc[PPT];
     bool ok[PPT];
-    T H[PPT][W2];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         int p = tid + NT * k;
         ok[k] = p < NP;
         bb[k] = ok[k] ? p % W2 : 0;
         cc[k] = ok[k] ? p / W2 : 0;
-        int y = (y0 - m + 1 + bb[k]) & msk, z = (z0 - m + 1 + cc[k]) & msk;
-        const T *row = g + ((int64_t)z * n + y) * n;
-#pragma unroll
-        for (int a = 0; a < W2; ++a) H[k][a] = ok[k] ? row[(x0 - m + 1 + a) & msk] : T(0);
     }
-    for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-        const int cn = min(kChunk, cnt - c0);
-        const T *src = wts + (int64_t)(start + c0) * PW;
-        for (int e = tid; e < cn * PW; e += NT) sw[e] = src[e];
-        __syncthreads();
+    T H[PPT][W2];
+    int b = 0;
+    while (cur.valid()) {
+        if (cur.c0 == 0) {  // first chunk of an item: its stencil from the tile
+            int lx0, ly0, lz0;
+            item_local(cur.local, lx0, ly0, lz0);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const T *row = S + ((lz0 + cc[k]) * E + (ly0 + bb[k])) * E + lx0;
+#pragma unroll
+                for (int a = 0; a < W2; ++a) H[k][a] = ok[k] ? row[a] : T(0);
+            }
+        }
+        const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_next, s_slot, team, tid);
+        int pnxt = 0;
+        if (nxt.valid()) {
+            st.issue(b ^ 1, wts, nxt);
+            if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
+        }
+        if (!st.wait(b, err)) {
+            st.drain(err);
+            break;
+        }
+        const T *sw = st.buf[b];
+        const int cn = min(kChunk, cur.cnt - cur.c0);
         T part[kChunk];
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
             T sum = T(0);
             if (j < cn) {
-                const T *wp = sw + j * PW;
+                const T *wp = sw + j * PWP;
+                T wx[W2];
+                load_line<T, W2>(wx, wp);
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (ok[k]) {
-                        T in = T(0);
-#pragma unroll
-                        for (int a = 0; a < W2; ++a) in = fma(wp[a], H[k][a], in);
-                        sum = fma(wp[W2 + bb[k]] * wp[2 * W2 + cc[k]], in, sum);
-                    }
-                }
+                for (int k = 0; k < PPT; ++k)
+                    if (ok[k])
+                        sum = fma(wp[W2 + bb[k]] * wp[2 * W2 + cc[k]], dot_line(wx, H[k]), sum);
             }
             part[j] = sum;
         }
-        // reduce-scatter over the warp: afterwards lane j holds the warp's sum
-        // for point j of the chunk
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             const bool upper = lane & o;
@@ -168,17 +500,30 @@ k_interp(const int4 *__restrict__ items, const int *__restrict__ perm,
         T tot = part[0];
         if (NW > 1) {
             if (warp == 0) sred[lane] = tot;
-            __syncthreads();
+            team_sync<NW>(team);
 #pragma unroll
             for (int w = 1; w < NW; ++w) {
                 if (warp == w) sred[lane] += tot;
-                __syncthreads();
+                team_sync<NW>(team);
             }
             tot = sred[lane];
         }
-        if (warp == 0 && lane < cn) Y[(int64_t)l * N + perm[start + c0 + lane]] = (double)tot;
-        __syncthreads();
+        if (warp == 0 && lane < cn) Y[(int64_t)l * N + pcur] = (double)tot;
+        team_sync<NW>(team);  // every read of buffer b (and sred) is done
+        cur = nxt;
+        pcur = pnxt;
+        b ^= 1;
     }
+}
+
+// xs[s] = x[perm[s]] for every sorted position s (input in sorted order).
+template <typename T>
+__global__ void k_gather(const double *__restrict__ x, const int *__restrict__ perm, int64_t LN,
+                         T *__restrict__ xs, const int *__restrict__ done) {
+    if (done && *done) return;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < LN;
+         s += (int64_t)gridDim.x * blockDim.x)
+        xs[s] = (T)x[perm[s]];
 }
 
 // ------------------------------------------------------------------ grid convolution
@@ -342,20 +687,32 @@ k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restr
 // ------------------------------------------------------------------ dispatch
 template <typename T, int W2>
 static void launch_spread_interp(Plan &P, bool spread, const T *wts, T *grid,
-                                 const double *v, const int *done, cudaStream_t s) {
-    constexpr int NW = W2 <= 8 ? 1 : 2;
-    if (P.n_items == 0) return;
+                                 const T *xs, const int *done, cudaStream_t s) {
+    constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2;
+    constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
+    if (P.n_units == 0) return;
+    static bool configured = false;  // per template instance
+    if (!configured) {
+        NLH_CUDA(cudaFuncSetAttribute(k_spread<T, W2, NW, TPB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NLH_CUDA(cudaFuncSetAttribute(k_interp<T, W2, NW, TPB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const int cls = spread ? (sizeof(T) == 8 ? NLH_K_SPREAD64 : NLH_K_SPREAD32)
+                           : (sizeof(T) == 8 ? NLH_K_INTERP64 : NLH_K_INTERP32);
+    ProfRange pr(cls, s);
     if (spread)
-        k_spread<T, W2, NW><<<(unsigned)P.n_items, 32 * NW, 0, s>>>(P.items, P.perm, wts, v,
-                                                                    grid, P.n, P.m, done);
+        k_spread<T, W2, NW, TPB><<<(unsigned)P.n_units, 32 * NW * TPB, smem, s>>>(
+            P.units, P.items, wts, xs, grid, P.n, P.m, done, P.err);
     else
-        k_interp<T, W2, NW><<<(unsigned)P.n_items, 32 * NW, 0, s>>>(P.items, P.perm, wts, grid,
-                                                                    P.Y, P.n, P.m, P.N, done);
+        k_interp<T, W2, NW, TPB><<<(unsigned)P.n_units, 32 * NW * TPB, smem, s>>>(
+            P.units, P.items, P.perm, wts, grid, P.Y, P.n, P.m, P.N, done, P.err);
     NLH_CHECK_LAUNCH();
 }
 
 template <typename T>
-static void spread_interp(Plan &P, bool spread, const T *wts, T *grid, const double *v,
+static void spread_interp(Plan &P, bool spread, const T *wts, T *grid, const T *v,
                           const int *done, cudaStream_t s) {
     switch (P.W2) {
         case 4: launch_spread_interp<T, 4>(P, spread, wts, grid, v, done, s); break;
@@ -374,6 +731,7 @@ static void convolve(Plan &P, T *grid, const T *tab, const typename Vec2<T>::typ
                      const int *done, cudaStream_t s) {
     const int n = P.n;
     dim3 gdim((unsigned)(n * n / 16), (unsigned)P.L);
+    ProfRange pr(sizeof(T) == 8 ? NLH_K_CONV64 : NLH_K_CONV32, s);
     for (int axis = 0; axis < 3; ++axis) {
         switch (n) {
             case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
@@ -390,10 +748,17 @@ template <typename T>
 static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
                      double *partials, const int *done, const T *wts, T *grid, const T *tab,
                      const typename Vec2<T>::type *tw, const double *d, cudaStream_t s) {
-    spread_interp<T>(P, true, wts, grid, x, done, s);
+    T *xs = reinterpret_cast<T *>(P.xs);
+    {
+        ProfRange pr(NLH_K_EPILOGUE, s);
+        k_gather<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, P.perm, (int64_t)P.L * P.N, xs, done);
+        NLH_CHECK_LAUNCH();
+    }
+    spread_interp<T>(P, true, wts, grid, xs, done, s);
     convolve<T>(P, grid, tab, tw, done, s);
     spread_interp<T>(P, false, wts, grid, nullptr, done, s);
     const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
+    ProfRange pr(NLH_K_EPILOGUE, s);
     k_epilogue<T><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, op, y, partials,
                                                      grid, ge, done);
     NLH_CHECK_LAUNCH();
@@ -423,6 +788,7 @@ extern "C" nlh_status nlh_matvec(nlh_plan plan, int op, int precision, double al
         NLH_REQUIRE(op >= 0 && op <= 2, "nlh_matvec: op=%d", op);
         NLH_REQUIRE(precision == NLH_FP64 || precision == NLH_FP32, "nlh_matvec: precision=%d",
                     precision);
+        plan->stream = (cudaStream_t)stream;
         nlh::matvec(*plan, op, precision, alpha, x, y, nullptr, nullptr, (cudaStream_t)stream);
         return NLH_OK;
     } catch (nlh::Failure &f) {

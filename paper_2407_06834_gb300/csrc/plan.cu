@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <map>
+#include <mutex>
 #include <new>
 
 namespace nlh {
@@ -26,8 +28,23 @@ void set_error(const char *fmt, ...) {
 void clear_error() { g_err.clear(); }
 
 Plan::~Plan() {
-    for (void *ptr : allocs) cudaFree(ptr);
-    if (st_host) cudaFreeHost(st_host);
+    for (void *ptr : allocs) cudaFreeAsync(ptr, stream);
+    if (st_host) {
+        cudaStreamSynchronize(stream);
+        cudaFreeHost(st_host);
+    }
+}
+
+void retain_pool_memory() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
 }
 
 // ------------------------------------------------------------------ features
@@ -123,6 +140,17 @@ __global__ void k_minmax_final(const double *__restrict__ part, int nb, double *
 }
 
 // ------------------------------------------------------------------ sort by cell
+// Cells are ordered tile-major: tiles of kTile^3 cells in (z, y, x) order,
+// then the cells inside a tile in (z, y, x) order.  The map is a bijection
+// of [0, n^3), so a counting sort over it groups the points of each cell and
+// keeps the cells of one tile contiguous.
+__device__ __forceinline__ int tile_major_key(int x, int y, int z, int n) {
+    const int nt = n / kTile;
+    int tile = ((z / kTile) * nt + y / kTile) * nt + x / kTile;
+    int local = ((z % kTile) * kTile + y % kTile) * kTile + x % kTile;
+    return tile * (kTile * kTile * kTile) + local;
+}
+
 // Grid coordinate u = (s (x - c) + 1/2) n taken modulo n, so that the torus
 // [-1/2, 1/2) maps to the grid points 0..n-1.  Cell = floor(u).
 __global__ void k_cell_keys(const double *__restrict__ feat, int64_t N, int D, int L,
@@ -147,7 +175,7 @@ __global__ void k_cell_keys(const double *__restrict__ feat, int64_t N, int D, i
             u[idx * 3 + t] = ut;
             cell[t] = c;
         }
-        int key = (cell[2] * n + cell[1]) * n + cell[0];
+        int key = tile_major_key(cell[0], cell[1], cell[2], n);
         keys[idx] = key;
         atomicAdd(&hist[(int64_t)l * n3 + key], 1);
     }
@@ -268,17 +296,21 @@ __global__ void k_item_counts(const int *__restrict__ hist, int64_t ncells, int 
 }
 
 __global__ void k_emit_items(const int *__restrict__ hist, const int *__restrict__ start,
-                             const int *__restrict__ item_off, int64_t ncells, int64_t n3,
+                             const int *__restrict__ item_off, int64_t ncells, int n,
                              int kmax, int4 *__restrict__ items) {
+    const int64_t n3 = (int64_t)n * n * n;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
          c += (int64_t)gridDim.x * blockDim.x) {
         int h = hist[c];
         if (h == 0) continue;
         int l = (int)(c / n3);
-        int cell = (int)(c - (int64_t)l * n3);
+        const int key = (int)(c - (int64_t)l * n3), t3 = kTile * kTile * kTile;
+        const int tile = key / t3, local = key % t3;  // tile-major key
+        const int lx = local % kTile, ly = (local / kTile) % kTile, lz = local / (kTile * kTile);
+        const int packed = (l << 16) | (lz << 6) | (ly << 3) | lx;
         int o = item_off[c];
         for (int t = 0; t * kmax < h; ++t)
-            items[o + t] = make_int4(l, cell, start[c] + t * kmax, min(kmax, h - t * kmax));
+            items[o + t] = make_int4(packed, tile, start[c] + t * kmax, min(kmax, h - t * kmax));
     }
 }
 
@@ -286,18 +318,93 @@ __global__ void k_emit_items(const int *__restrict__ hist, const int *__restrict
 // Kaiser-Bessel window (Kaiser 1974; its use for gridding: Jackson et al.
 // 1991): phi(x) = I0(beta sqrt(1 - (n x / m)^2)) / I0(beta) for |n x| <= m.
 // A point at grid coordinate u = c + f (c integer, 0 <= f < 1) touches the
-// 2m grid points g = c - m + 1 + t, t = 0..2m-1, at offsets g - u in (-m, m].
-__device__ __forceinline__ double kb_window(double off_over_m, double beta, double inv_i0b) {
-    double z = 1.0 - off_over_m * off_over_m;
+// 2m grid points g = c - m + 1 + j, j = 0..2m-1, at offsets g - u in
+// (-m, m], with weight P_j(f) = phi((j - m + 1 - f) / m).  Because
+// I0(beta sqrt(z)) is an entire function of z, each P_j is analytic on
+// [0, 1]; it is fitted once per plan by Chebyshev interpolation in
+// y = 2f - 1, converted to a polynomial in y (validated against direct
+// evaluation on the host) and evaluated by Horner's rule per point.
+constexpr int kMaxPolyCoef = 24;
+
+static double kb_host(double x, double beta) {
+    double z = 1.0 - x * x;
     if (z < 0.0) return 0.0;
-    return cyl_bessel_i0(beta * sqrt(z)) * inv_i0b;
+    return std::cyl_bessel_i(0.0, beta * std::sqrt(z)) / std::cyl_bessel_i(0.0, beta);
+}
+
+// Monomial coefficients (in y) of the degree-D Chebyshev interpolant of
+// P_j, for every j; returns D + 1 (coefficients per j), or throws.  Fits
+// are cached per (m, beta): they depend on nothing else.
+static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &coef);
+
+static int fit_weight_polys(int m, double beta, std::vector<double> &coef) {
+    static std::mutex mu;
+    static std::map<std::pair<int, double>, std::pair<int, std::vector<double>>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(m, beta);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        std::vector<double> c;
+        int K = fit_weight_polys_uncached(m, beta, c);
+        it = cache.emplace(key, std::make_pair(K, c)).first;
+    }
+    coef = it->second.second;
+    return it->second.first;
+}
+
+static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &coef) {
+    const int W2 = 2 * m;
+    for (int D = 8; D < kMaxPolyCoef; ++D) {
+        const int K = D + 1;
+        coef.assign((size_t)W2 * K, 0.0);
+        double worst = 0.0;
+        for (int j = 0; j < W2; ++j) {
+            auto Pj = [&](double y) { return kb_host((j - m + 1 - 0.5 * (y + 1.0)) / m, beta); };
+            std::vector<double> c(K, 0.0), g(K);
+            for (int i = 0; i < K; ++i) g[i] = Pj(std::cos(M_PI * (i + 0.5) / K));
+            for (int k = 0; k < K; ++k) {
+                double acc = 0.0;
+                for (int i = 0; i < K; ++i) acc += g[i] * std::cos(M_PI * k * (i + 0.5) / K);
+                c[k] = (k == 0 ? 1.0 : 2.0) * acc / K;
+            }
+            // Chebyshev -> monomial: T_{k+1} = 2 y T_k - T_{k-1}
+            std::vector<double> tkm1(K, 0.0), tk(K, 0.0), a(K, 0.0);
+            tkm1[0] = 1.0;
+            if (K > 1) tk[1] = 1.0;
+            for (int i = 0; i < K; ++i) a[i] += c[0] * tkm1[i];
+            if (K > 1)
+                for (int i = 0; i < K; ++i) a[i] += c[1] * tk[i];
+            for (int k = 2; k < K; ++k) {
+                std::vector<double> tn(K, 0.0);
+                for (int i = 0; i < K; ++i) {
+                    if (i > 0) tn[i] += 2.0 * tk[i - 1];
+                    tn[i] -= tkm1[i];
+                }
+                for (int i = 0; i < K; ++i) a[i] += c[k] * tn[i];
+                tkm1 = tk;
+                tk = tn;
+            }
+            for (int i = 0; i < K; ++i) coef[(size_t)j * K + i] = a[i];
+            for (int q = 0; q <= 100; ++q) {
+                double y = -1.0 + q / 50.0, h = 0.0;
+                for (int i = K - 1; i >= 0; --i) h = h * y + a[i];
+                worst = std::max(worst, std::fabs(h - Pj(y)));
+            }
+        }
+        if (worst < 2e-14) return K;
+    }
+    set_error("internal: window polynomial fit did not converge (m=%d)", m);
+    throw Failure{NLH_ERR_ARG};
 }
 
 __global__ void k_weights(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
-                          int L, int m, double beta, double inv_i0b,
-                          double *__restrict__ w64, float *__restrict__ w32) {
-    const int64_t total = (int64_t)L * N;
+                          int L, int m, int K, const double *__restrict__ coef, int rec64,
+                          int rec32, double *__restrict__ w64, float *__restrict__ w32) {
+    __shared__ double sc[16 * kMaxPolyCoef];
     const int W2 = 2 * m;
+    for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
+    __syncthreads();
+    const int64_t total = (int64_t)L * N;
     for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < total;
          sidx += (int64_t)gridDim.x * blockDim.x) {
         int l = (int)(sidx / N);
@@ -305,15 +412,19 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
         const double *up = u + ((int64_t)l * N + i) * 3;
         for (int t = 0; t < 3; ++t) {
             double ut = up[t];
-            double f = ut - floor(ut);
+            double y = 2.0 * (ut - floor(ut)) - 1.0;
             for (int j = 0; j < W2; ++j) {
-                double off = (double)(j - m + 1) - f;
-                double w = kb_window(off / m, beta, inv_i0b);
-                int64_t o = (sidx * 3 + t) * W2 + j;
-                if (w64) w64[o] = w;
-                if (w32) w32[o] = (float)w;
+                const double *a = sc + j * K;
+                double w = a[K - 1];
+                for (int q = K - 2; q >= 0; --q) w = fma(w, y, a[q]);
+                if (w64) w64[sidx * rec64 + t * W2 + j] = w;
+                if (w32) w32[sidx * rec32 + t * W2 + j] = (float)w;
             }
         }
+        if (w64)
+            for (int j = 3 * W2; j < rec64; ++j) w64[sidx * rec64 + j] = 0.0;
+        if (w32)
+            for (int j = 3 * W2; j < rec32; ++j) w32[sidx * rec32 + j] = 0.0f;
     }
 }
 
@@ -366,6 +477,45 @@ __global__ void k_fill(double *__restrict__ x, int64_t n, double v) {
         x[i] = v;
 }
 
+// Work units: consecutive items (tile-major order) of one window and one
+// tile, cut when the running point count would exceed kUnitPoints or the
+// item count kUnitItems.  Units are then ordered by decreasing point count
+// so that the largest start first.  Built on the host from the item list
+// (a plan-time pass over n_items records).
+static void build_units(Plan &P, cudaStream_t s) {
+    std::vector<int4> items(P.n_items);
+    if (P.n_items)
+        NLH_CUDA(cudaMemcpyAsync(items.data(), P.items, sizeof(int4) * P.n_items,
+                                 cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::pair<int, int4>> units;
+    int64_t i = 0;
+    while (i < P.n_items) {
+        const int l = items[i].x >> 16, tile = items[i].y;
+        int64_t j = i;
+        int pts = 0;
+        while (j < P.n_items && (items[j].x >> 16) == l && items[j].y == tile &&
+               j - i < kUnitItems && (j == i || pts + items[j].w <= kUnitPoints)) {
+            pts += items[j].w;
+            ++j;
+        }
+        units.push_back({pts, make_int4(l, tile, (int)i, (int)(j - i))});
+        i = j;
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const std::pair<int, int4> &a, const std::pair<int, int4> &b) {
+                         return a.first > b.first;
+                     });
+    std::vector<int4> u(units.size());
+    for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
+    P.n_units = (int64_t)u.size();
+    P.units = P.alloc<int4>(u.size());
+    if (!u.empty())
+        NLH_CUDA(cudaMemcpyAsync(P.units, u.data(), sizeof(int4) * u.size(),
+                                 cudaMemcpyHostToDevice, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+}
+
 static int ilog2(int n) {
     int l = 0;
     while ((1 << l) < n) ++l;
@@ -403,6 +553,17 @@ void plan_tables(Plan &P, cudaStream_t s) {
     NLH_CHECK_LAUNCH();
 }
 
+void check_device_error(Plan &P, cudaStream_t s) {
+    int e = 0;
+    NLH_CUDA(cudaMemcpyAsync(&e, P.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    if (e != 0) {
+        NLH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), s));
+        set_error("a bulk copy did not complete within its bounded wait (status %d)", e);
+        throw Failure{NLH_ERR_TIMEOUT};
+    }
+}
+
 void plan_degrees(Plan &P, cudaStream_t s) {
     k_fill<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N, 1.0);
     NLH_CHECK_LAUNCH();
@@ -421,7 +582,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.W2 = 2 * desc.m;
     P.precision = desc.precision;
     P.sigma = desc.sigma;
-    P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 256;
+    P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
     P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
     const int64_t N = P.N;
     const int L = P.L, n = P.n;
@@ -463,10 +624,10 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     double *u = nullptr;
     int *keys = nullptr, *hist = nullptr, *start = nullptr, *cnt = nullptr, *ioff = nullptr,
         *sums = nullptr, *scal = nullptr;
-    NLH_CUDA(cudaMalloc(&u, sizeof(double) * LN * 3));
+    NLH_CUDA(cudaMallocAsync(&u, sizeof(double) * LN * 3, s));
     std::vector<void *> tmp{u};
     auto tmp_alloc = [&](int **ptr, size_t count) {
-        NLH_CUDA(cudaMalloc((void **)ptr, sizeof(int) * std::max<size_t>(count, 1)));
+        NLH_CUDA(cudaMallocAsync((void **)ptr, sizeof(int) * std::max<size_t>(count, 1), s));
         tmp.push_back(*ptr);
     };
     try {
@@ -496,22 +657,30 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         int occ = 0;
         NLH_CUDA(cudaMemcpyAsync(&occ, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         P.items = P.alloc<int4>(P.n_items);
-        k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n3, P.kmax, P.items);
+        k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n, P.kmax, P.items);
         NLH_CHECK_LAUNCH();
+        build_units(P, s);
         // weights in sorted order
-        double inv_i0b = 1.0 / std::cyl_bessel_i(0.0, P.kb_beta);
-        const size_t nw = (size_t)LN * 3 * P.W2;
-        if (P.precision & 1) P.wts64 = P.alloc<double>(nw);
-        if (P.precision & 2) P.wts32 = P.alloc<float>(nw);
-        k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, P.kb_beta, inv_i0b, P.wts64, P.wts32);
+        std::vector<double> coef;
+        const int K = fit_weight_polys(P.m, P.kb_beta, coef);
+        double *d_coef = nullptr;
+        NLH_CUDA(cudaMallocAsync(&d_coef, sizeof(double) * coef.size(), s));
+        tmp.push_back(d_coef);
+        NLH_CUDA(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(),
+                                 cudaMemcpyHostToDevice, s));
+        const int rec64 = record_len(P.W2, 8), rec32 = record_len(P.W2, 4);
+        if (P.precision & 1) P.wts64 = P.alloc<double>((size_t)LN * rec64);
+        if (P.precision & 2) P.wts32 = P.alloc<float>((size_t)LN * rec32);
+        k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_coef, rec64, rec32, P.wts64,
+                                     P.wts32);
         NLH_CHECK_LAUNCH();
         NLH_CUDA(cudaStreamSynchronize(s));
         P.occupied = occ;
     } catch (...) {
-        for (void *ptr : tmp) cudaFree(ptr);
+        for (void *ptr : tmp) cudaFreeAsync(ptr, s);
         throw;
     }
-    for (void *ptr : tmp) cudaFree(ptr);
+    for (void *ptr : tmp) cudaFreeAsync(ptr, s);
 
     // tables, grids, outputs, solver workspace
     if (P.precision & 1) {
@@ -529,6 +698,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         P.d32 = P.alloc<double>(N);
     }
     P.Y = P.alloc<double>(LN);
+    P.xs = P.alloc<double>(LN);
     P.w = P.alloc<double>(N);
     P.r = P.alloc<double>(N);
     P.p = P.alloc<double>(N);
@@ -538,11 +708,13 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.pinv = P.alloc<double>(N);
     P.partials = P.alloc<double>((size_t)kRedBlocks * 12);
     P.st = P.alloc<SolveState>(1);
+    P.err = P.alloc<int>(1);
+    NLH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), s));
     P.hist = P.alloc<double>(kMaxHist);
     NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
     plan_tables(P, s);
     plan_degrees(P, s);
-    NLH_CUDA(cudaStreamSynchronize(s));
+    check_device_error(P, s);
 }
 
 }  // namespace nlh
@@ -600,7 +772,9 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
         for (int i = 0; i < 3 * d.L; ++i)
             NLH_REQUIRE(d.windows[i] >= -1 && d.windows[i] < d.D,
                         "nlh_plan_create: windows[%d]=%d out of range", i, d.windows[i]);
+        retain_pool_memory();
         P = new nlh_plan_s();
+        P->stream = (cudaStream_t)stream;
         build_plan(*P, d, features, (cudaStream_t)stream);
         *out = P;
         return NLH_OK;
@@ -620,10 +794,11 @@ nlh_status nlh_plan_set_sigma(nlh_plan plan, double sigma, void *stream) {
         NLH_REQUIRE(plan, "nlh_plan_set_sigma: NULL plan");
         NLH_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "nlh_plan_set_sigma: sigma=%g", sigma);
         cudaStream_t s = (cudaStream_t)stream;
+        plan->stream = s;
         plan->sigma = sigma;
         plan_tables(*plan, s);
         plan_degrees(*plan, s);
-        NLH_CUDA(cudaStreamSynchronize(s));
+        check_device_error(*plan, s);
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;

@@ -359,6 +359,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     "nlh_solve: arith=%d", opts->arith);
         Plan &P = *plan;
         cudaStream_t s = (cudaStream_t)stream;
+        P.stream = s;
         if (opts->arith == NLH_SOLVE_FP64)
             NLH_REQUIRE(P.precision & 1, "nlh_solve: FP64 solve needs a plan with the FP64 path");
         else
@@ -426,7 +427,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
             scale = nullptr;
             inf.used_fallback = 1;
         }
-        NLH_CUDA(cudaStreamSynchronize(s));
+        check_device_error(P, s);
     } catch (Failure &f) {
         ret = f.st;
     }
