@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default="img512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle row sample (0 = auto)")
+    ap.add_argument("--matvec-case", action="store_true",
+                    help="profiling case: one plan, then 2 matvecs per NFFT precision; no JSON")
     return ap.parse_args()
 
 
@@ -367,9 +369,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def matvec_case(args):
+    """Small profiling case: plan (both precisions) + 2 matvecs per precision."""
+    import torch
+
+    from paper_2407_06834_gb300 import nlh
+    wl = WORKLOADS[args.workload]
+    img = torch.as_tensor(wl.image(), device="cuda")
+    P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                            n_os=wl.n_os, m=wl.m, precision=3)
+    x = torch.randn(wl.N, dtype=torch.float64, device="cuda")
+    for prec in (nlh.NLH_FP64, nlh.NLH_FP32):
+        for _ in range(2):
+            P.matvec(x, op=2, precision=prec, alpha=wl.alpha)
+    torch.cuda.synchronize()
+    P.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.matvec_case:
+        matvec_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

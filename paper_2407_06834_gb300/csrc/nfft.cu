@@ -17,6 +17,8 @@
 #include "common.cuh"
 #include "async_copy.cuh"
 
+#include <algorithm>
+
 namespace nlh {
 
 template <typename T> struct Vec2;
@@ -89,7 +91,7 @@ __device__ __forceinline__ void item_local(int packed, int &lx, int &ly, int &lz
 // small items take more of them.
 struct ChunkCursor {
     int ii, c0, start, cnt, local;
-    __device__ bool valid() const { return ii >= 0; }
+    __device__ __forceinline__ bool valid() const { return ii >= 0; }
 };
 
 template <int NW>
@@ -128,39 +130,44 @@ __device__ __forceinline__ ChunkCursor next_chunk(const ChunkCursor &c, const in
 template <typename T, int W2, int NW>
 struct Stager {
     static constexpr int PWP = padded_record<T, W2>();
-    T *buf[2];
+    // two buffers, selected by b in {0, 1} without indexing an array (so the
+    // state stays in registers)
+    T *buf0, *buf1;
     uint64_t *bar;
     volatile int *flag;
-    uint32_t phase[2];
-    bool pending[2];
+    uint32_t phase0, phase1;
+    bool pending0, pending1;
     int team, tid;
 
-    __device__ void issue(int b, const T *wts, const ChunkCursor &c) {
+    __device__ __forceinline__ T *buf(int b) const { return b ? buf1 : buf0; }
+
+    __device__ __forceinline__ void issue(int b, const T *wts, const ChunkCursor &c) {
         if (tid == 0) {
             const int cn = min(kChunk, c.cnt - c.c0);
             const uint32_t bytes = (uint32_t)(cn * PWP * sizeof(T));
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[b], bytes);
-            bulk_copy_g2s(buf[b], wts + (int64_t)(c.start + c.c0) * PWP, bytes, &bar[b]);
+            bulk_copy_g2s(buf(b), wts + (int64_t)(c.start + c.c0) * PWP, bytes, &bar[b]);
         }
-        pending[b] = true;
+        if (b) pending1 = true; else pending0 = true;
     }
 
     // Returns false if the copy timed out (the team then stops).
-    __device__ bool wait(int b, int *err) {
-        if (tid == 0) *flag = mbar_wait_bounded(&bar[b], phase[b], err) ? 1 : 0;
+    __device__ __forceinline__ bool wait(int b, int *err) {
+        const uint32_t ph = b ? phase1 : phase0;
+        if (tid == 0) *flag = mbar_wait_bounded(&bar[b], ph, err) ? 1 : 0;
         team_sync<NW>(team);
         bool ok = *flag != 0;
-        if (ok) ok = mbar_try_wait(&bar[b], phase[b]);  // acquire for every reader
-        phase[b] ^= 1u;
-        pending[b] = false;
+        if (ok) ok = mbar_try_wait(&bar[b], ph);  // acquire for every reader
+        if (b) { phase1 ^= 1u; pending1 = false; } else { phase0 ^= 1u; pending0 = false; }
         return ok;
     }
 
     // On an early exit: wait (bounded) for copies still in flight.
-    __device__ void drain(int *err) {
-        for (int b = 0; b < 2; ++b)
-            if (pending[b] && tid == 0) mbar_wait_bounded(&bar[b], phase[b], err);
+    __device__ __forceinline__ void drain(int *err) {
+        if (tid != 0) return;
+        if (pending0) mbar_wait_bounded(&bar[0], phase0, err);
+        if (pending1) mbar_wait_bounded(&bar[1], phase1, err);
     }
 };
 
@@ -171,81 +178,106 @@ __device__ __forceinline__ Stager<T, W2, NW> make_stager(unsigned char *team_bas
                                                          int tid) {
     using SM = UnitSmem<T, W2, TPB>;
     Stager<T, W2, NW> st;
-    st.buf[0] = reinterpret_cast<T *>(team_base);
-    st.buf[1] = reinterpret_cast<T *>(team_base + SM::stage);
+    st.buf0 = reinterpret_cast<T *>(team_base);
+    st.buf1 = reinterpret_cast<T *>(team_base + SM::stage);
     st.bar = reinterpret_cast<uint64_t *>(team_base + 2 * SM::stage);
     st.flag = reinterpret_cast<volatile int *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t));
-    st.phase[0] = st.phase[1] = 0u;
-    st.pending[0] = st.pending[1] = false;
+    st.phase0 = st.phase1 = 0u;
+    st.pending0 = st.pending1 = false;
     st.team = team;
     st.tid = tid;
     return st;
 }
 
-// acc[a] += s * w[a] for a = 0..W2-1 (packed FP32 pairs on the FP32 path).
-template <typename T, int W2>
-__device__ __forceinline__ void axpy_line(T (&acc)[W2], T s, const T (&w)[W2]) {
+// Arithmetic on one x line of the stencil.  On the FP32 path a line of 2m
+// values is held as m 64-bit registers, each a pair of floats, and updated
+// with the packed fma.rn.f32x2 instruction; on the FP64 path it is scalar.
+template <typename T, int W2> struct Line {
+    T v[W2];
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int a = 0; a < W2; ++a) acc[a] = fma(s, w[a], acc[a]);
-}
-template <int W2>
-__device__ __forceinline__ void axpy_line(float (&acc)[W2], float s, const float (&w)[W2]) {
-    static_assert(W2 % 2 == 0, "even stencil");
-    const unsigned long long ss =
-        ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)__float_as_uint(s);
-#pragma unroll
-    for (int a = 0; a < W2; a += 2) {
-        unsigned long long wv = ((unsigned long long)__float_as_uint(w[a + 1]) << 32) |
-                                (unsigned long long)__float_as_uint(w[a]);
-        unsigned long long av = ((unsigned long long)__float_as_uint(acc[a + 1]) << 32) |
-                                (unsigned long long)__float_as_uint(acc[a]);
-        unsigned long long d;
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ss), "l"(wv), "l"(av));
-        acc[a] = __uint_as_float((unsigned)(d & 0xffffffffull));
-        acc[a + 1] = __uint_as_float((unsigned)(d >> 32));
+        for (int a = 0; a < W2; ++a) v[a] = T(0);
     }
-}
-
-// sum_a w[a] h[a]
-template <typename T, int W2>
-__device__ __forceinline__ T dot_line(const T (&w)[W2], const T (&h)[W2]) {
-    T in = T(0);
+    __device__ __forceinline__ void load(const T *src) {  // 16-byte aligned
 #pragma unroll
-    for (int a = 0; a < W2; ++a) in = fma(w[a], h[a], in);
-    return in;
-}
-template <int W2>
-__device__ __forceinline__ float dot_line(const float (&w)[W2], const float (&h)[W2]) {
-    unsigned long long acc = 0ull;
-#pragma unroll
-    for (int a = 0; a < W2; a += 2) {
-        unsigned long long wv = ((unsigned long long)__float_as_uint(w[a + 1]) << 32) |
-                                (unsigned long long)__float_as_uint(w[a]);
-        unsigned long long hv = ((unsigned long long)__float_as_uint(h[a + 1]) << 32) |
-                                (unsigned long long)__float_as_uint(h[a]);
-        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(wv), "l"(hv));
-    }
-    return __uint_as_float((unsigned)(acc & 0xffffffffull)) +
-           __uint_as_float((unsigned)(acc >> 32));
-}
-
-// Load W2 consecutive values from 16-byte aligned shared memory.
-template <typename T, int W2>
-__device__ __forceinline__ void load_line(T (&dst)[W2], const T *src) {
-    constexpr int PER = 16 / sizeof(T);
-    if (W2 % PER == 0) {
-#pragma unroll
-        for (int a = 0; a < W2; a += PER) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(src + a);
-            const T *qv = reinterpret_cast<const T *>(&q);
-#pragma unroll
-            for (int e = 0; e < PER; ++e) dst[a + e] = qv[e];
+        for (int a = 0; a < W2; a += 2) {
+            const double2 q = *reinterpret_cast<const double2 *>(src + a);
+            v[a] = q.x;
+            v[a + 1] = q.y;
         }
-    } else {
-#pragma unroll
-        for (int a = 0; a < W2; ++a) dst[a] = src[a];
     }
-}
+    __device__ __forceinline__ void axpy(T s, const Line &w) {  // v += s w
+#pragma unroll
+        for (int a = 0; a < W2; ++a) v[a] = fma(s, w.v[a], v[a]);
+    }
+    __device__ __forceinline__ T dot(const Line &h) const {
+        T in = T(0);
+#pragma unroll
+        for (int a = 0; a < W2; ++a) in = fma(v[a], h.v[a], in);
+        return in;
+    }
+    __device__ __forceinline__ T get(int a) const { return v[a]; }
+    __device__ __forceinline__ void set(int a, T x) { v[a] = x; }
+};
+
+template <int W2> struct Line<float, W2> {
+    static_assert(W2 % 2 == 0, "even stencil");
+    unsigned long long v[W2 / 2];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) v[a] = 0ull;
+    }
+    __device__ __forceinline__ void load(const float *src) {  // 8-byte aligned
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) v[a] = reinterpret_cast<const unsigned long long *>(src)[a];
+    }
+    __device__ __forceinline__ void axpy(float s, const Line &w) {
+        unsigned long long ss;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(ss) : "f"(s));
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a)
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(v[a]) : "l"(ss), "l"(w.v[a]));
+    }
+    __device__ __forceinline__ float dot(const Line &h) const {
+        unsigned long long acc = 0ull;
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a)
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(v[a]), "l"(h.v[a]));
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc));
+        return lo + hi;
+    }
+    __device__ __forceinline__ float get(int a) const {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v[a / 2]));
+        return (a & 1) ? hi : lo;
+    }
+    __device__ __forceinline__ void set(int a, float x) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v[a / 2]));
+        if (a & 1) hi = x; else lo = x;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(v[a / 2]) : "f"(lo), "f"(hi));
+    }
+};
+
+// (y, z) stencil pairs owned by one thread: pair p = tid + NT k.  When the
+// team size is a multiple of 2m every pair of a thread has the same y offset.
+template <int W2, int NT, int PPT>
+struct Pairs {
+    int b0, bb[PPT], cc[PPT];
+    bool ok[PPT];
+    static constexpr bool kSameB = (NT % W2) == 0;
+    __device__ __forceinline__ void init(int tid) {
+        b0 = tid % W2;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            int p = tid + NT * k;
+            ok[k] = p < W2 * W2;
+            bb[k] = kSameB ? b0 : (ok[k] ? p % W2 : 0);
+            cc[k] = ok[k] ? p / W2 : 0;
+        }
+    }
+};
 
 // Shared carve-up common to both kernels: tile region, item records, the
 // CTA's item counter, then TPB team areas.
@@ -253,13 +285,15 @@ template <typename T, int W2, int TPB>
 struct UnitLayout {
     using SM = UnitSmem<T, W2, TPB>;
     static constexpr size_t items_off = SM::tile;
-    static constexpr size_t next_off = items_off + sizeof(int4) * kUnitItems;
+    static constexpr size_t next_off = items_off + sizeof(int4) * kUnitItems;  // 4 ints:
+    // [0] item counter, [1] current unit, [2] abort flag
     static constexpr size_t teams_off = next_off + 16;
     static constexpr size_t bytes = teams_off + TPB * SM::team;
 };
 
 // ------------------------------------------------------------------ spreading
-// One CTA per unit.  Each team takes items of the unit; a thread owns PPT
+// Persistent CTAs take units from a global counter (units are stored in
+// decreasing size).  Per unit, each team takes items; a thread owns PPT
 // (y, z) stencil pairs with their full x line of 2m accumulators, summed in
 // registers over the item's points (all points of an item share the
 // stencil).  Items are then added into the shared tile, and the tile is
@@ -267,137 +301,140 @@ struct UnitLayout {
 // input vector in sorted order.
 template <typename T, int W2, int NW, int TPB>
 __global__ void __launch_bounds__(32 * NW * TPB)
-k_spread(const int4 *__restrict__ units, const int4 *__restrict__ items,
-         const T *__restrict__ wts, const T *__restrict__ xs, T *__restrict__ grid, int n,
-         int m, const int *__restrict__ done, int *__restrict__ err) {
+k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
+         const int4 *__restrict__ items, const T *__restrict__ wts, const T *__restrict__ xs,
+         T *__restrict__ grid, int n, int m, const int *__restrict__ done,
+         int *__restrict__ err) {
     using SM = UnitSmem<T, W2, TPB>;
     using LY = UnitLayout<T, W2, TPB>;
-    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PWP = SM::PWP;
+    constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
     constexpr int E = SM::E, E3 = SM::E3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
     int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_next = reinterpret_cast<int *>(smem_raw + LY::next_off);
+    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
     if (done && *done) return;
-    const int4 un = units[blockIdx.x];
-    const int l = un.x, it0 = un.z, nit = un.w;
-    int tx0, ty0, tz0;
-    tile_origin(un.y, n, tx0, ty0, tz0);
     const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31;
     unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
     auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
     int *s_slot = const_cast<int *>(st.flag) + 1;
-    for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = T(0);
-    for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-    if (threadIdx.x == 0) *s_next = TPB;
     if (tid == 0) {
         mbar_init(&st.bar[0], 1);
         mbar_init(&st.bar[1], 1);
         mbar_fence_init();
     }
-    __syncthreads();
-    int bb[PPT], cc[PPT];
-    bool ok[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        int p = tid + NT * k;
-        ok[k] = p < NP;
-        bb[k] = ok[k] ? p % W2 : 0;
-        cc[k] = ok[k] ? p / W2 : 0;
-    }
-    T acc[PPT][W2];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k)
-#pragma unroll
-        for (int a = 0; a < W2; ++a) acc[k][a] = T(0);
-
-    ChunkCursor cur = make_cursor(s_items, team, nit);
-    T vcur = T(0);
-    if (cur.valid()) {
-        st.issue(0, wts, cur);
-        if (lane < cur.cnt) vcur = xs[cur.start + lane];
-    }
-    int b = 0;
-    while (cur.valid()) {
-        const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_next, s_slot, team, tid);
-        T vnxt = T(0);
-        if (nxt.valid()) {
-            st.issue(b ^ 1, wts, nxt);
-            if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
-        }
-        if (!st.wait(b, err)) {
-            st.drain(err);
-            break;
-        }
-        const T *sw = st.buf[b];
-        const int cn = min(kChunk, cur.cnt - cur.c0);
-        for (int j = 0; j < cn; ++j) {
-            const T *wp = sw + j * PWP;
-            T wx[W2];
-            load_line<T, W2>(wx, wp);
-            const T vj = __shfl_sync(0xffffffffu, vcur, j);
-#pragma unroll
-            for (int k = 0; k < PPT; ++k)
-                if (ok[k]) axpy_line(acc[k], vj * wp[W2 + bb[k]] * wp[2 * W2 + cc[k]], wx);
-        }
-        if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
-            int lx0, ly0, lz0;
-            item_local(cur.local, lx0, ly0, lz0);
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (ok[k]) {
-                    T *row = S + ((lz0 + cc[k]) * E + (ly0 + bb[k])) * E + lx0;
-#pragma unroll
-                    for (int a = 0; a < W2; ++a) atomicAdd(&row[a], acc[k][a]);
-                }
-#pragma unroll
-                for (int a = 0; a < W2; ++a) acc[k][a] = T(0);
-            }
-        }
-        team_sync<NW>(team);  // every read of buffer b is done before it is refilled
-        cur = nxt;
-        vcur = vnxt;
-        b ^= 1;
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) s_ctl[2] = 0;
+    Pairs<W2, NT, PPT> pr;
+    pr.init(tid);
     const int msk = n - 1;
-    T *g = grid + (int64_t)l * n * n * n;
-    for (int e = threadIdx.x; e < E3; e += blockDim.x) {
-        T val = S[e];
-        if (val != T(0)) {
-            int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
-            int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
-                gz = (tz0 - m + 1 + ez) & msk;
-            atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], val);
+    while (true) {
+        __syncthreads();  // previous unit fully flushed
+        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
+        __syncthreads();
+        const int uidx = s_ctl[1];
+        if (uidx >= n_units || s_ctl[2]) break;
+        const int4 un = units[uidx];
+        const int l = un.x, it0 = un.z, nit = un.w;
+        int tx0, ty0, tz0;
+        tile_origin(un.y, n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = T(0);
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        if (threadIdx.x == 0) s_ctl[0] = TPB;
+        __syncthreads();
+        Line<T, W2> acc[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) acc[k].zero();
+        ChunkCursor cur = make_cursor(s_items, team, nit);
+        T vcur = T(0);
+        if (cur.valid()) {
+            st.issue(0, wts, cur);
+            if (lane < cur.cnt) vcur = xs[cur.start + lane];
+        }
+        int bsel = 0;
+        while (cur.valid()) {
+            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
+            T vnxt = T(0);
+            if (nxt.valid()) {
+                st.issue(bsel ^ 1, wts, nxt);
+                if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
+            }
+            if (!st.wait(bsel, err)) {
+                st.drain(err);
+                s_ctl[2] = 1;
+                break;
+            }
+            const T *sw = st.buf(bsel);
+            const int cn = min(kChunk, cur.cnt - cur.c0);
+            for (int j = 0; j < cn; ++j) {
+                const T *wp = sw + j * PWP;
+                Line<T, W2> wx;
+                wx.load(wp);
+                const T vj = __shfl_sync(0xffffffffu, vcur, j);
+                if (Pairs<W2, NT, PPT>::kSameB) {
+                    const T vb = vj * wp[W2 + pr.b0];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k)
+                        if (pr.ok[k]) acc[k].axpy(vb * wp[2 * W2 + pr.cc[k]], wx);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k)
+                        if (pr.ok[k])
+                            acc[k].axpy(vj * wp[W2 + pr.bb[k]] * wp[2 * W2 + pr.cc[k]], wx);
+                }
+            }
+            if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
+                int lx0, ly0, lz0;
+                item_local(cur.local, lx0, ly0, lz0);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (pr.ok[k]) {
+                        T *row = S + ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
+#pragma unroll
+                        for (int a = 0; a < W2; ++a) atomicAdd(&row[a], acc[k].get(a));
+                    }
+                    acc[k].zero();
+                }
+            }
+            team_sync<NW>(team);  // every read of buffer bsel is done before it is refilled
+            cur = nxt;
+            vcur = vnxt;
+            bsel ^= 1;
+        }
+        __syncthreads();
+        T *g = grid + (int64_t)l * n * n * n;
+        for (int e = threadIdx.x; e < E3; e += blockDim.x) {
+            T val = S[e];
+            if (val != T(0)) {
+                int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+                int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                    gz = (tz0 - m + 1 + ez) & msk;
+                atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], val);
+            }
         }
     }
 }
 
 // ------------------------------------------------------------------ interpolation
-// One CTA per unit: the tile region of the convolved grid is staged in
-// shared memory; each team holds an item's stencil in registers and sums
-// every point's 2m^3 products.  The per-thread partial sums of a chunk of 32
-// points are reduce-scattered over the warp so that lane j ends with point
-// j's value.
+// Persistent CTAs over units as in k_spread.  The tile region of the
+// convolved grid is staged in shared memory; each team holds an item's
+// stencil in registers and sums every point's 2m^3 products.  The
+// per-thread partial sums of a chunk of 32 points are reduce-scattered over
+// the warp so that lane j ends with point j's value.
 template <typename T, int W2, int NW, int TPB>
 __global__ void __launch_bounds__(32 * NW * TPB)
-k_interp(const int4 *__restrict__ units, const int4 *__restrict__ items,
-         const int *__restrict__ perm, const T *__restrict__ wts, const T *__restrict__ grid,
-         double *__restrict__ Y, int n, int m, int64_t N, const int *__restrict__ done,
-         int *__restrict__ err) {
+k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
+         const int4 *__restrict__ items, const int *__restrict__ perm,
+         const T *__restrict__ wts, const T *__restrict__ grid, double *__restrict__ Y, int n,
+         int m, int64_t N, const int *__restrict__ done, int *__restrict__ err) {
     using SM = UnitSmem<T, W2, TPB>;
     using LY = UnitLayout<T, W2, TPB>;
-    constexpr int NT = 32 * NW, NP = W2 * W2, PPT = (NP + NT - 1) / NT, PWP = SM::PWP;
+    constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
     constexpr int E = SM::E, E3 = SM::E3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
     int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_next = reinterpret_cast<int *>(smem_raw + LY::next_off);
+    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
     if (done && *done) return;
-    const int4 un = units[blockIdx.x];
-    const int l = un.x, it0 = un.z, nit = un.w;
-    int tx0, ty0, tz0;
-    tile_origin(un.y, n, tx0, ty0, tz0);
     const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31, warp = tid >> 5;
     unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
     auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
@@ -408,111 +445,126 @@ k_interp(const int4 *__restrict__ units, const int4 *__restrict__ items,
         mbar_init(&st.bar[1], 1);
         mbar_fence_init();
     }
-    for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-    if (threadIdx.x == 0) *s_next = TPB;
+    if (threadIdx.x == 0) s_ctl[2] = 0;
+    Pairs<W2, NT, PPT> pr;
+    pr.init(tid);
     const int msk = n - 1;
-    const T *g = grid + (int64_t)l * n * n * n;
-    {
-        constexpr int UNR = 8;
-        for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
-            T vals[UNR];
+    while (true) {
+        __syncthreads();  // previous unit done with the tile
+        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
+        __syncthreads();
+        const int uidx = s_ctl[1];
+        if (uidx >= n_units || s_ctl[2]) break;
+        const int4 un = units[uidx];
+        const int l = un.x, it0 = un.z, nit = un.w;
+        int tx0, ty0, tz0;
+        tile_origin(un.y, n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        if (threadIdx.x == 0) s_ctl[0] = TPB;
+        const T *g = grid + (int64_t)l * n * n * n;
+        {
+            constexpr int UNR = 8;
+            for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
+                T vals[UNR];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                int e = base + u * blockDim.x;
-                vals[u] = T(0);
-                if (e < E3) {
-                    int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
-                    int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
-                        gz = (tz0 - m + 1 + ez) & msk;
-                    vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
+                for (int u = 0; u < UNR; ++u) {
+                    int e = base + u * blockDim.x;
+                    vals[u] = T(0);
+                    if (e < E3) {
+                        int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+                        int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                            gz = (tz0 - m + 1 + ez) & msk;
+                        vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    int e = base + u * blockDim.x;
+                    if (e < E3) S[e] = vals[u];
                 }
             }
+        }
+        __syncthreads();
+        ChunkCursor cur = make_cursor(s_items, team, nit);
+        if (cur.valid()) st.issue(0, wts, cur);
+        int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
+        Line<T, W2> H[PPT];
+        int bsel = 0;
+        while (cur.valid()) {
+            if (cur.c0 == 0) {  // first chunk of an item: its stencil from the tile
+                int lx0, ly0, lz0;
+                item_local(cur.local, lx0, ly0, lz0);
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                int e = base + u * blockDim.x;
-                if (e < E3) S[e] = vals[u];
+                for (int k = 0; k < PPT; ++k) {
+                    const T *row = S + ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
+#pragma unroll
+                    for (int a = 0; a < W2; ++a) H[k].set(a, pr.ok[k] ? row[a] : T(0));
+                }
             }
-        }
-    }
-    __syncthreads();
-    ChunkCursor cur = make_cursor(s_items, team, nit);
-    if (cur.valid()) st.issue(0, wts, cur);
-    int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
-    int bb[PPT], cc[PPT];
-    bool ok[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        int p = tid + NT * k;
-        ok[k] = p < NP;
-        bb[k] = ok[k] ? p % W2 : 0;
-        cc[k] = ok[k] ? p / W2 : 0;
-    }
-    T H[PPT][W2];
-    int b = 0;
-    while (cur.valid()) {
-        if (cur.c0 == 0) {  // first chunk of an item: its stencil from the tile
-            int lx0, ly0, lz0;
-            item_local(cur.local, lx0, ly0, lz0);
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const T *row = S + ((lz0 + cc[k]) * E + (ly0 + bb[k])) * E + lx0;
-#pragma unroll
-                for (int a = 0; a < W2; ++a) H[k][a] = ok[k] ? row[a] : T(0);
+            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
+            int pnxt = 0;
+            if (nxt.valid()) {
+                st.issue(bsel ^ 1, wts, nxt);
+                if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
             }
-        }
-        const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_next, s_slot, team, tid);
-        int pnxt = 0;
-        if (nxt.valid()) {
-            st.issue(b ^ 1, wts, nxt);
-            if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
-        }
-        if (!st.wait(b, err)) {
-            st.drain(err);
-            break;
-        }
-        const T *sw = st.buf[b];
-        const int cn = min(kChunk, cur.cnt - cur.c0);
-        T part[kChunk];
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            T sum = T(0);
-            if (j < cn) {
-                const T *wp = sw + j * PWP;
-                T wx[W2];
-                load_line<T, W2>(wx, wp);
-#pragma unroll
-                for (int k = 0; k < PPT; ++k)
-                    if (ok[k])
-                        sum = fma(wp[W2 + bb[k]] * wp[2 * W2 + cc[k]], dot_line(wx, H[k]), sum);
+            if (!st.wait(bsel, err)) {
+                st.drain(err);
+                s_ctl[2] = 1;
+                break;
             }
-            part[j] = sum;
-        }
+            const T *sw = st.buf(bsel);
+            const int cn = min(kChunk, cur.cnt - cur.c0);
+            T part[kChunk];
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const bool upper = lane & o;
+            for (int j = 0; j < kChunk; ++j) {
+                T sum = T(0);
+                if (j < cn) {
+                    const T *wp = sw + j * PWP;
+                    Line<T, W2> wx;
+                    wx.load(wp);
+                    if (Pairs<W2, NT, PPT>::kSameB) {
+                        T zs = T(0);
 #pragma unroll
-            for (int kk = 0; kk < o; ++kk) {
-                T send = upper ? part[kk] : part[kk + o];
-                T keep = upper ? part[kk + o] : part[kk];
-                part[kk] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        for (int k = 0; k < PPT; ++k)
+                            if (pr.ok[k]) zs = fma(wp[2 * W2 + pr.cc[k]], wx.dot(H[k]), zs);
+                        sum = wp[W2 + pr.b0] * zs;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k)
+                            if (pr.ok[k])
+                                sum = fma(wp[W2 + pr.bb[k]] * wp[2 * W2 + pr.cc[k]], wx.dot(H[k]),
+                                          sum);
+                    }
+                }
+                part[j] = sum;
             }
-        }
-        T tot = part[0];
-        if (NW > 1) {
-            if (warp == 0) sred[lane] = tot;
-            team_sync<NW>(team);
 #pragma unroll
-            for (int w = 1; w < NW; ++w) {
-                if (warp == w) sred[lane] += tot;
+            for (int o = 16; o >= 1; o >>= 1) {
+                const bool upper = lane & o;
+#pragma unroll
+                for (int kk = 0; kk < o; ++kk) {
+                    T send = upper ? part[kk] : part[kk + o];
+                    T keep = upper ? part[kk + o] : part[kk];
+                    part[kk] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            T tot = part[0];
+            if (NW > 1) {
+                if (warp == 0) sred[lane] = tot;
                 team_sync<NW>(team);
+#pragma unroll
+                for (int w = 1; w < NW; ++w) {
+                    if (warp == w) sred[lane] += tot;
+                    team_sync<NW>(team);
+                }
+                tot = sred[lane];
             }
-            tot = sred[lane];
+            if (warp == 0 && lane < cn) Y[(int64_t)l * N + pcur] = (double)tot;
+            team_sync<NW>(team);  // every read of buffer bsel (and sred) is done
+            cur = nxt;
+            pcur = pnxt;
+            bsel ^= 1;
         }
-        if (warp == 0 && lane < cn) Y[(int64_t)l * N + pcur] = (double)tot;
-        team_sync<NW>(team);  // every read of buffer b (and sred) is done
-        cur = nxt;
-        pcur = pnxt;
-        b ^= 1;
     }
 }
 
@@ -655,9 +707,13 @@ __global__ void __launch_bounds__(kRedThreads)
 k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restrict__ x,
            const double *__restrict__ d, double alpha, int op, double *__restrict__ y,
            double *__restrict__ partials, T *__restrict__ grid, int64_t grid_elems,
-           const int *__restrict__ done) {
+           int *__restrict__ unit_ctr, const int *__restrict__ done) {
     __shared__ double sh[33];
     if (done && *done) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unit_ctr[0] = 0;  // the spread and interpolation kernels have finished
+        unit_ctr[1] = 0;
+    }
     const double invL = 1.0 / L;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -688,26 +744,39 @@ k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restr
 template <typename T, int W2>
 static void launch_spread_interp(Plan &P, bool spread, const T *wts, T *grid,
                                  const T *xs, const int *done, cudaStream_t s) {
-    constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2;
+    constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2, NTH = 32 * NW * TPB;
     constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
     if (P.n_units == 0) return;
-    static bool configured = false;  // per template instance
-    if (!configured) {
+    static int blocks_spread = 0, blocks_interp = 0;  // per template instance
+    if (blocks_spread == 0) {
         NLH_CUDA(cudaFuncSetAttribute(k_spread<T, W2, NW, TPB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         NLH_CUDA(cudaFuncSetAttribute(k_interp<T, W2, NW, TPB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
+        int dev = 0, sms = 0, a = 0, b = 0;
+        NLH_CUDA(cudaGetDevice(&dev));
+        NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spread<T, W2, NW, TPB>, NTH,
+                                                               smem));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<T, W2, NW, TPB>, NTH,
+                                                               smem));
+        blocks_interp = sms * std::max(1, b);
+        blocks_spread = sms * std::max(1, a);
     }
     const int cls = spread ? (sizeof(T) == 8 ? NLH_K_SPREAD64 : NLH_K_SPREAD32)
                            : (sizeof(T) == 8 ? NLH_K_INTERP64 : NLH_K_INTERP32);
     ProfRange pr(cls, s);
-    if (spread)
-        k_spread<T, W2, NW, TPB><<<(unsigned)P.n_units, 32 * NW * TPB, smem, s>>>(
-            P.units, P.items, wts, xs, grid, P.n, P.m, done, P.err);
-    else
-        k_interp<T, W2, NW, TPB><<<(unsigned)P.n_units, 32 * NW * TPB, smem, s>>>(
-            P.units, P.items, P.perm, wts, grid, P.Y, P.n, P.m, P.N, done, P.err);
+    const int nu = (int)P.n_units;
+    if (spread) {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
+        k_spread<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, nu, P.unit_ctr, P.items, wts, xs,
+                                                      grid, P.n, P.m, done, P.err);
+    } else {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks_interp, nu);
+        k_interp<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, nu, P.unit_ctr + 1, P.items,
+                                                      P.perm, wts, grid, P.Y, P.n, P.m, P.N, done,
+                                                      P.err);
+    }
     NLH_CHECK_LAUNCH();
 }
 
@@ -760,7 +829,7 @@ static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
     const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
     ProfRange pr(NLH_K_EPILOGUE, s);
     k_epilogue<T><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, op, y, partials,
-                                                     grid, ge, done);
+                                                     grid, ge, P.unit_ctr, done);
     NLH_CHECK_LAUNCH();
 }
 
