@@ -181,6 +181,29 @@ const char *nlh_last_error(void);
 /* Library version string. */
 const char *nlh_version(void);
 
+/* Residual norms with no device allocation.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they need a
+ * residual -- code running while a framework captures a CUDA graph (where
+ * cudaMalloc is not allowed), real-time loops that must not pay allocation
+ * latency, processes whose device memory belongs to another allocator.
+ *   b, q   device FP64, length N (typically q = (alpha I + L) u from
+ *          nlh_matvec, op 2)
+ *   res    device FP64, length N, receives b - q; may be NULL
+ *   norms  device FP64, 2 values: ||b - q||_2 and ||b||_2
+ * The per-block partial sums go to one fixed array inside the library
+ * (128 KiB, allocated when the library is loaded on each device and kept
+ * until the process exits), so N is limited to 33,554,432 (8192 blocks of
+ * 4096 elements); larger N returns NLH_ERR_ARG.  Nothing in the array must
+ * start at zero: every call overwrites the slots it reads.  All calls, on
+ * every stream, share that array, so calls that overlap on the GPU race and
+ * must be ordered by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  The call allocates
+ * nothing and does not synchronise. */
+nlh_status nlh_residual_norms_noalloc(const double *b, const double *q,
+                                      int64_t N, double *res, double *norms,
+                                      void *stream);
+
 /* ---- Instrumentation (not part of the paper's method) ------------------
  * nlh_kernel_launches: number of CUDA kernels the library has launched in
  * this process.  nlh_profile_enable(1) makes the library bracket each launch

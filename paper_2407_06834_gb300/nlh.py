@@ -76,6 +76,8 @@ SIGNATURES = {
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
+    "nlh_residual_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
