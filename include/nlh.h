@@ -43,8 +43,10 @@ typedef enum {
 
 typedef struct nlh_plan_s *nlh_plan;
 
-/* NFFT arithmetic of a matvec. */
-enum { NLH_FP64 = 0, NLH_FP32 = 1 };
+/* NFFT arithmetic of a matvec.  NLH_DF32 carries every value as an
+ * unevaluated sum of two floats (about 46-48 significant bits) so that the
+ * FP64-accurate operator runs on the FP32 pipes; its grids and FFTs are FP64. */
+enum { NLH_FP64 = 0, NLH_FP32 = 1, NLH_DF32 = 2 };
 
 /* Patch features, Sec. 5: for every pixel the closed square patch of radius
  * `radius` of the image, zero padded (pad = 0, the paper's choice) or
@@ -71,7 +73,8 @@ typedef struct {
     int M;                  /* even, 4 <= M <= n_os                          */
     int n_os;               /* power of two, 32..256                         */
     int m;                  /* 2..8, and 2m < n_os                           */
-    int precision;          /* bit 0: build FP64 path, bit 1: FP32 path      */
+    int precision;          /* bit 0: FP64 path, bit 1: FP32 path,
+                               bit 2: double-float path (NLH_DF32)           */
     double torus_fill;      /* in (0, 1): fraction of the torus the points
                                span per dim; 0 = choose automatically        */
     int max_items_pts;      /* points per work item, 0 = default (256)       */
@@ -112,7 +115,8 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
  *   op 1: y = L x = d o x - Gamma_full x   (d = Gamma_full 1; the diagonal
  *                                           cancels, Sec. 2.3)
  *   op 2: y = (alpha I + L) x
- * precision: NLH_FP64 or NLH_FP32 (the NFFT stages; the output is FP64).
+ * precision: NLH_FP64, NLH_FP32 or NLH_DF32 (the NFFT stages; the output is
+ * FP64).
  * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers).  The
  * call does not synchronise: a device-side failure (NLH_ERR_TIMEOUT) is
  * reported by the next synchronising call on the plan. */
@@ -129,8 +133,11 @@ enum {
 /* Arithmetic of a solve. */
 enum {
     NLH_SOLVE_FP64 = 0,    /* every matvec FP64                               */
-    NLH_SOLVE_MIXED = 1    /* FP32-NFFT inner solves inside FP64 iterative
-                              refinement (FP64 residuals and dots)            */
+    NLH_SOLVE_MIXED = 1,   /* FP32-NFFT inner solves inside iterative
+                              refinement whose residuals use the FP64-accurate
+                              operator (double-float if the plan has it,
+                              else FP64); dots always FP64                    */
+    NLH_SOLVE_DF32 = 2     /* every matvec double-float                       */
 };
 
 typedef struct {
@@ -214,7 +221,7 @@ nlh_status nlh_residual_norms_noalloc(const double *b, const double *q,
 enum {
     NLH_K_SPREAD64 = 0, NLH_K_SPREAD32, NLH_K_CONV64, NLH_K_CONV32,
     NLH_K_INTERP64, NLH_K_INTERP32, NLH_K_EPILOGUE, NLH_K_KRYLOV, NLH_K_PLAN,
-    NLH_K_NCLASSES
+    NLH_K_SPREADDF, NLH_K_INTERPDF, NLH_K_NCLASSES
 };
 int64_t nlh_kernel_launches(void);
 nlh_status nlh_profile_enable(int enable);

@@ -18,7 +18,8 @@
 //   tab64/32 [n]             per-dim Fourier multiplier in bit-reversed order
 //   tw64/32  [n/2]           FFT twiddles exp(-2 pi i j / n)
 //   Y        [L][N]          per-window interpolated values, pixel order
-//   d64/d32  [N]             degrees d = Gamma_full 1 of each NFFT precision
+//   d64/d32/ddf [N]          degrees d = Gamma_full 1 of each NFFT arithmetic
+//   wtsdf    [L*N][6m]        double-float records: per dim 2m high, 2m low
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -95,7 +96,7 @@ struct SolveState {
 
 constexpr int kMaxHist = 4096;
 constexpr int kTile = 8;          // tile edge in grid cells (spread/interp units)
-constexpr int kUnitPoints = 1024; // points per work unit before a tile is split
+constexpr int kUnitPoints = 512;  // points per work unit before a tile is split
 constexpr int kUnitItems = 256;   // items per work unit (staged in shared memory)
 
 struct Plan {
@@ -111,6 +112,7 @@ struct Plan {
     int64_t n_units = 0;
     double *wts64 = nullptr;
     float *wts32 = nullptr;
+    float *wtsdf = nullptr;       // double-float records: per dim 2m high then 2m low parts
     double *tab64 = nullptr;
     float *tab32 = nullptr;
     double2 *tw64 = nullptr;
@@ -119,13 +121,14 @@ struct Plan {
     float *grid32 = nullptr;
     double *Y = nullptr;
     double *xs = nullptr;         // [L*N] matvec input in sorted order (T)
-    double *d64 = nullptr, *d32 = nullptr;
+    double *d64 = nullptr, *d32 = nullptr, *ddf = nullptr;
     // solver workspace
     double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
            *t = nullptr, *rhs = nullptr, *pinv = nullptr;
     double *partials = nullptr;   // kRedBlocks * 12 doubles
     SolveState *st = nullptr;     // device
     int *err = nullptr;           // device error word (bounded waits that gave up)
+    int *unit_ctr = nullptr;      // device [2]: next unit of spread / interpolation
     SolveState *st_host = nullptr; // pinned mirror
     double *hist = nullptr;       // device, kMaxHist
     std::vector<void *> allocs;

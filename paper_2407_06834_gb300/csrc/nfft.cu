@@ -16,6 +16,7 @@
 // stencil cell.
 #include "common.cuh"
 #include "async_copy.cuh"
+#include "df32.cuh"
 
 #include <algorithm>
 
@@ -39,6 +40,39 @@ template <typename C> __device__ __forceinline__ C cshfl(C a, int o) {
 
 constexpr int kChunk = 32;  // points staged in shared memory at a time
 
+// Storage of one arithmetic: R = element of the weight records, G = grid
+// element.  A weight record holds, per dim t, 2m values (R = T) or, for
+// df32, 2m high parts followed by 2m low parts.
+template <typename T> struct Num { using R = T; using G = T; static constexpr int kParts = 1; };
+template <> struct Num<df32> { using R = float; using G = double; static constexpr int kParts = 2; };
+
+template <typename T, int W2>
+__device__ __forceinline__ const typename Num<T>::R *rec_line(const typename Num<T>::R *wp, int t) {
+    return wp + t * Num<T>::kParts * W2;
+}
+template <typename T, int W2>
+__device__ __forceinline__ T rec_val(const typename Num<T>::R *wp, int t, int j) {
+    return wp[t * W2 + j];
+}
+template <int W2> struct RecDF {
+    static __device__ __forceinline__ df32 get(const float *wp, int t, int j) {
+        return df32(wp[t * 2 * W2 + j], wp[t * 2 * W2 + W2 + j]);
+    }
+};
+#define NLH_REC_DF(W)                                                                  \
+    template <>                                                                        \
+    __device__ __forceinline__ df32 rec_val<df32, W>(const float *wp, int t, int j) {  \
+        return RecDF<W>::get(wp, t, j);                                                \
+    }
+NLH_REC_DF(4)
+NLH_REC_DF(6)
+NLH_REC_DF(8)
+NLH_REC_DF(10)
+NLH_REC_DF(12)
+NLH_REC_DF(14)
+NLH_REC_DF(16)
+#undef NLH_REC_DF
+
 // A team is NW warps; a CTA holds TPB teams.  Teams synchronise among
 // themselves only (a warp sync, or a named barrier for two-warp teams).
 template <int NW>
@@ -54,7 +88,8 @@ __device__ __forceinline__ void team_sync(int team) {
 // bytes so that a chunk of records is one bulk copy.
 template <typename T, int W2>
 constexpr int padded_record() {
-    return ((3 * W2 * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
+    using R = typename Num<T>::R;
+    return ((3 * Num<T>::kParts * W2 * (int)sizeof(R) + 15) / 16) * 16 / (int)sizeof(R);
 }
 
 constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -66,7 +101,7 @@ template <typename T, int W2, int TPB>
 struct UnitSmem {
     static constexpr int E = kTile + W2 - 1, E3 = E * E * E, PWP = padded_record<T, W2>();
     static constexpr size_t tile = align16(sizeof(T) * E3);
-    static constexpr size_t stage = align16(sizeof(T) * kChunk * PWP);
+    static constexpr size_t stage = align16(sizeof(typename Num<T>::R) * kChunk * PWP);
     static constexpr size_t team = 2 * stage + 2 * sizeof(uint64_t) + 16 + align16(sizeof(T) * kChunk);
 };
 
@@ -129,22 +164,23 @@ __device__ __forceinline__ ChunkCursor next_chunk(const ChunkCursor &c, const in
 // a chunk's weight records and waits for it (bounded); the team then reads.
 template <typename T, int W2, int NW>
 struct Stager {
+    using R = typename Num<T>::R;
     static constexpr int PWP = padded_record<T, W2>();
     // two buffers, selected by b in {0, 1} without indexing an array (so the
     // state stays in registers)
-    T *buf0, *buf1;
+    R *buf0, *buf1;
     uint64_t *bar;
     volatile int *flag;
     uint32_t phase0, phase1;
     bool pending0, pending1;
     int team, tid;
 
-    __device__ __forceinline__ T *buf(int b) const { return b ? buf1 : buf0; }
+    __device__ __forceinline__ R *buf(int b) const { return b ? buf1 : buf0; }
 
-    __device__ __forceinline__ void issue(int b, const T *wts, const ChunkCursor &c) {
+    __device__ __forceinline__ void issue(int b, const R *wts, const ChunkCursor &c) {
         if (tid == 0) {
             const int cn = min(kChunk, c.cnt - c.c0);
-            const uint32_t bytes = (uint32_t)(cn * PWP * sizeof(T));
+            const uint32_t bytes = (uint32_t)(cn * PWP * sizeof(R));
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[b], bytes);
             bulk_copy_g2s(buf(b), wts + (int64_t)(c.start + c.c0) * PWP, bytes, &bar[b]);
@@ -178,8 +214,8 @@ __device__ __forceinline__ Stager<T, W2, NW> make_stager(unsigned char *team_bas
                                                          int tid) {
     using SM = UnitSmem<T, W2, TPB>;
     Stager<T, W2, NW> st;
-    st.buf0 = reinterpret_cast<T *>(team_base);
-    st.buf1 = reinterpret_cast<T *>(team_base + SM::stage);
+    st.buf0 = reinterpret_cast<typename Num<T>::R *>(team_base);
+    st.buf1 = reinterpret_cast<typename Num<T>::R *>(team_base + SM::stage);
     st.bar = reinterpret_cast<uint64_t *>(team_base + 2 * SM::stage);
     st.flag = reinterpret_cast<volatile int *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t));
     st.phase0 = st.phase1 = 0u;
@@ -260,6 +296,53 @@ template <int W2> struct Line<float, W2> {
     }
 };
 
+template <int W2> struct Line<df32, W2> {
+    static_assert(W2 % 2 == 0, "even stencil");
+    unsigned long long h[W2 / 2], l[W2 / 2];  // packed (cell a, cell a+1) high / low parts
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) h[a] = l[a] = 0ull;
+    }
+    // src: 2m high parts followed by 2m low parts (8-byte aligned)
+    __device__ __forceinline__ void load(const float *src) {
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) {
+            h[a] = reinterpret_cast<const unsigned long long *>(src)[a];
+            l[a] = reinterpret_cast<const unsigned long long *>(src + W2)[a];
+        }
+    }
+    __device__ __forceinline__ void axpy(df32 s, const Line &w) {  // this += s w
+        const unsigned long long sh = pk_dup(s.hi), nsh = pk_dup(-s.hi), nsl = pk_dup(-s.lo);
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) pk_df_axpy(h[a], l[a], sh, nsh, nsl, w.h[a], w.l[a]);
+    }
+    __device__ __forceinline__ df32 dot(const Line &x) const {  // sum_a this[a] x[a]
+        unsigned long long sh = 0ull, sl = 0ull;
+        const unsigned long long zero = 0ull;
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a)
+            pk_df_axpy(sh, sl, h[a], pk_sub(zero, h[a]), pk_sub(zero, l[a]), x.h[a], x.l[a]);
+        float h0, h1, l0, l1;
+        pk_split(sh, h0, h1);
+        pk_split(sl, l0, l1);
+        return df32(h0, l0) + df32(h1, l1);
+    }
+    __device__ __forceinline__ df32 get(int a) const {
+        float h0, h1, l0, l1;
+        pk_split(h[a / 2], h0, h1);
+        pk_split(l[a / 2], l0, l1);
+        return (a & 1) ? df32(h1, l1) : df32(h0, l0);
+    }
+    __device__ __forceinline__ void set(int a, df32 x) {
+        float h0, h1, l0, l1;
+        pk_split(h[a / 2], h0, h1);
+        pk_split(l[a / 2], l0, l1);
+        if (a & 1) { h1 = x.hi; l1 = x.lo; } else { h0 = x.hi; l0 = x.lo; }
+        h[a / 2] = pk_make(h0, h1);
+        l[a / 2] = pk_make(l0, l1);
+    }
+};
+
 // (y, z) stencil pairs owned by one thread: pair p = tid + NT k.  When the
 // team size is a multiple of 2m every pair of a thread has the same y offset.
 template <int W2, int NT, int PPT>
@@ -300,11 +383,13 @@ struct UnitLayout {
 // added into the global grid once (non-zero entries only).  xs holds the
 // input vector in sorted order.
 template <typename T, int W2, int NW, int TPB>
-__global__ void __launch_bounds__(32 * NW * TPB)
+__global__ void __launch_bounds__(32 * NW * TPB, 1)
 k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
-         const int4 *__restrict__ items, const T *__restrict__ wts, const T *__restrict__ xs,
-         T *__restrict__ grid, int n, int m, const int *__restrict__ done,
-         int *__restrict__ err) {
+         const int4 *__restrict__ items, const typename Num<T>::R *__restrict__ wts,
+         const T *__restrict__ xs, typename Num<T>::G *__restrict__ grid, int n, int m,
+         const int *__restrict__ done, int *__restrict__ err) {
+    using R = typename Num<T>::R;
+    using G = typename Num<T>::G;
     using SM = UnitSmem<T, W2, TPB>;
     using LY = UnitLayout<T, W2, TPB>;
     constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
@@ -363,23 +448,25 @@ k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
                 s_ctl[2] = 1;
                 break;
             }
-            const T *sw = st.buf(bsel);
+            const R *sw = st.buf(bsel);
             const int cn = min(kChunk, cur.cnt - cur.c0);
             for (int j = 0; j < cn; ++j) {
-                const T *wp = sw + j * PWP;
+                const R *wp = sw + j * PWP;
                 Line<T, W2> wx;
-                wx.load(wp);
+                wx.load(rec_line<T, W2>(wp, 0));
                 const T vj = __shfl_sync(0xffffffffu, vcur, j);
                 if (Pairs<W2, NT, PPT>::kSameB) {
-                    const T vb = vj * wp[W2 + pr.b0];
+                    const T vb = vj * rec_val<T, W2>(wp, 1, pr.b0);
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
-                        if (pr.ok[k]) acc[k].axpy(vb * wp[2 * W2 + pr.cc[k]], wx);
+                        if (pr.ok[k]) acc[k].axpy(vb * rec_val<T, W2>(wp, 2, pr.cc[k]), wx);
                 } else {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
                         if (pr.ok[k])
-                            acc[k].axpy(vj * wp[W2 + pr.bb[k]] * wp[2 * W2 + pr.cc[k]], wx);
+                            acc[k].axpy(vj * rec_val<T, W2>(wp, 1, pr.bb[k]) *
+                                            rec_val<T, W2>(wp, 2, pr.cc[k]),
+                                        wx);
                 }
             }
             if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
@@ -401,14 +488,14 @@ k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
             bsel ^= 1;
         }
         __syncthreads();
-        T *g = grid + (int64_t)l * n * n * n;
+        G *g = grid + (int64_t)l * n * n * n;
         for (int e = threadIdx.x; e < E3; e += blockDim.x) {
             T val = S[e];
             if (val != T(0)) {
                 int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
                 int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
                     gz = (tz0 - m + 1 + ez) & msk;
-                atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], val);
+                atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], (G)val);
             }
         }
     }
@@ -421,11 +508,14 @@ k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
 // per-thread partial sums of a chunk of 32 points are reduce-scattered over
 // the warp so that lane j ends with point j's value.
 template <typename T, int W2, int NW, int TPB>
-__global__ void __launch_bounds__(32 * NW * TPB)
+__global__ void __launch_bounds__(32 * NW * TPB, 1)
 k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
          const int4 *__restrict__ items, const int *__restrict__ perm,
-         const T *__restrict__ wts, const T *__restrict__ grid, double *__restrict__ Y, int n,
-         int m, int64_t N, const int *__restrict__ done, int *__restrict__ err) {
+         const typename Num<T>::R *__restrict__ wts, const typename Num<T>::G *__restrict__ grid,
+         double *__restrict__ Y, int n, int m, int64_t N, const int *__restrict__ done,
+         int *__restrict__ err) {
+    using R = typename Num<T>::R;
+    using G = typename Num<T>::G;
     using SM = UnitSmem<T, W2, TPB>;
     using LY = UnitLayout<T, W2, TPB>;
     constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
@@ -461,15 +551,15 @@ k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
         tile_origin(un.y, n, tx0, ty0, tz0);
         for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
         if (threadIdx.x == 0) s_ctl[0] = TPB;
-        const T *g = grid + (int64_t)l * n * n * n;
+        const G *g = grid + (int64_t)l * n * n * n;
         {
             constexpr int UNR = 8;
             for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
-                T vals[UNR];
+                G vals[UNR];
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     int e = base + u * blockDim.x;
-                    vals[u] = T(0);
+                    vals[u] = G(0);
                     if (e < E3) {
                         int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
                         int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
@@ -480,7 +570,7 @@ k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     int e = base + u * blockDim.x;
-                    if (e < E3) S[e] = vals[u];
+                    if (e < E3) S[e] = T(vals[u]);
                 }
             }
         }
@@ -512,54 +602,68 @@ k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
                 s_ctl[2] = 1;
                 break;
             }
-            const T *sw = st.buf(bsel);
+            const R *sw = st.buf(bsel);
             const int cn = min(kChunk, cur.cnt - cur.c0);
-            T part[kChunk];
+            // Points in groups of 8: each thread forms its partial sums for the
+            // group, an 8-lane reduce-scatter leaves lane l with the partial of
+            // point (l & 7) over its 8-lane group, and two shuffle-adds finish the
+            // warp sum.  A runtime loop over groups keeps the code small.
+            for (int g0 = 0; g0 < cn; g0 += 8) {
+                T part[8];
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) {
-                T sum = T(0);
-                if (j < cn) {
-                    const T *wp = sw + j * PWP;
-                    Line<T, W2> wx;
-                    wx.load(wp);
-                    if (Pairs<W2, NT, PPT>::kSameB) {
-                        T zs = T(0);
+                for (int jj = 0; jj < 8; ++jj) {
+                    T sum = T(0);
+                    const int j = g0 + jj;
+                    if (j < cn) {
+                        const R *wp = sw + j * PWP;
+                        Line<T, W2> wx;
+                        wx.load(rec_line<T, W2>(wp, 0));
+                        if (Pairs<W2, NT, PPT>::kSameB) {
+                            T zs = T(0);
 #pragma unroll
-                        for (int k = 0; k < PPT; ++k)
-                            if (pr.ok[k]) zs = fma(wp[2 * W2 + pr.cc[k]], wx.dot(H[k]), zs);
-                        sum = wp[W2 + pr.b0] * zs;
-                    } else {
+                            for (int k = 0; k < PPT; ++k)
+                                if (pr.ok[k])
+                                    zs = fma(rec_val<T, W2>(wp, 2, pr.cc[k]), wx.dot(H[k]), zs);
+                            sum = rec_val<T, W2>(wp, 1, pr.b0) * zs;
+                        } else {
 #pragma unroll
-                        for (int k = 0; k < PPT; ++k)
-                            if (pr.ok[k])
-                                sum = fma(wp[W2 + pr.bb[k]] * wp[2 * W2 + pr.cc[k]], wx.dot(H[k]),
-                                          sum);
+                            for (int k = 0; k < PPT; ++k)
+                                if (pr.ok[k])
+                                    sum = fma(rec_val<T, W2>(wp, 1, pr.bb[k]) *
+                                                  rec_val<T, W2>(wp, 2, pr.cc[k]),
+                                              wx.dot(H[k]), sum);
+                        }
+                    }
+                    part[jj] = sum;
+                }
+#pragma unroll
+                for (int o = 4; o >= 1; o >>= 1) {
+                    const bool upper = lane & o;
+#pragma unroll
+                    for (int kk = 0; kk < o; ++kk) {
+                        T send = upper ? part[kk] : part[kk + o];
+                        T keep = upper ? part[kk + o] : part[kk];
+                        part[kk] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
-                part[j] = sum;
-            }
+                T tot = part[0];
+                tot = tot + __shfl_xor_sync(0xffffffffu, tot, 8);
+                tot = tot + __shfl_xor_sync(0xffffffffu, tot, 16);
+                if (NW > 1) {
+                    if (warp == 0 && lane < 8) sred[lane] = tot;
+                    team_sync<NW>(team);
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const bool upper = lane & o;
-#pragma unroll
-                for (int kk = 0; kk < o; ++kk) {
-                    T send = upper ? part[kk] : part[kk + o];
-                    T keep = upper ? part[kk + o] : part[kk];
-                    part[kk] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                }
-            }
-            T tot = part[0];
-            if (NW > 1) {
-                if (warp == 0) sred[lane] = tot;
-                team_sync<NW>(team);
-#pragma unroll
-                for (int w = 1; w < NW; ++w) {
-                    if (warp == w) sred[lane] += tot;
+                    for (int w = 1; w < NW; ++w) {
+                        if (warp == w && lane < 8) sred[lane] += tot;
+                        team_sync<NW>(team);
+                    }
+                    tot = sred[lane & 7];
                     team_sync<NW>(team);
                 }
-                tot = sred[lane];
+                const int pidx = __shfl_sync(0xffffffffu, pcur, (g0 + lane) & 31);
+                if (warp == 0 && lane < 8 && g0 + lane < cn)
+                    Y[(int64_t)l * N + pidx] = (double)tot;
             }
-            if (warp == 0 && lane < cn) Y[(int64_t)l * N + pcur] = (double)tot;
             team_sync<NW>(team);  // every read of buffer bsel (and sred) is done
             cur = nxt;
             pcur = pnxt;
@@ -741,9 +845,17 @@ k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restr
 }
 
 // ------------------------------------------------------------------ dispatch
+template <typename T> constexpr int spread_class() {
+    return sizeof(T) == 4 ? NLH_K_SPREAD32 : (Num<T>::kParts == 2 ? NLH_K_SPREADDF : NLH_K_SPREAD64);
+}
+template <typename T> constexpr int interp_class() {
+    return sizeof(T) == 4 ? NLH_K_INTERP32 : (Num<T>::kParts == 2 ? NLH_K_INTERPDF : NLH_K_INTERP64);
+}
+
 template <typename T, int W2>
-static void launch_spread_interp(Plan &P, bool spread, const T *wts, T *grid,
-                                 const T *xs, const int *done, cudaStream_t s) {
+static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
+                                 typename Num<T>::G *grid, const T *xs, const int *done,
+                                 cudaStream_t s) {
     constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2, NTH = 32 * NW * TPB;
     constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
     if (P.n_units == 0) return;
@@ -763,9 +875,7 @@ static void launch_spread_interp(Plan &P, bool spread, const T *wts, T *grid,
         blocks_interp = sms * std::max(1, b);
         blocks_spread = sms * std::max(1, a);
     }
-    const int cls = spread ? (sizeof(T) == 8 ? NLH_K_SPREAD64 : NLH_K_SPREAD32)
-                           : (sizeof(T) == 8 ? NLH_K_INTERP64 : NLH_K_INTERP32);
-    ProfRange pr(cls, s);
+    ProfRange pr(spread ? spread_class<T>() : interp_class<T>(), s);
     const int nu = (int)P.n_units;
     if (spread) {
         const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
@@ -781,8 +891,8 @@ static void launch_spread_interp(Plan &P, bool spread, const T *wts, T *grid,
 }
 
 template <typename T>
-static void spread_interp(Plan &P, bool spread, const T *wts, T *grid, const T *v,
-                          const int *done, cudaStream_t s) {
+static void spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
+                          typename Num<T>::G *grid, const T *v, const int *done, cudaStream_t s) {
     switch (P.W2) {
         case 4: launch_spread_interp<T, 4>(P, spread, wts, grid, v, done, s); break;
         case 6: launch_spread_interp<T, 6>(P, spread, wts, grid, v, done, s); break;
@@ -795,28 +905,34 @@ static void spread_interp(Plan &P, bool spread, const T *wts, T *grid, const T *
     }
 }
 
-template <typename T>
-static void convolve(Plan &P, T *grid, const T *tab, const typename Vec2<T>::type *tw,
+template <typename G>
+static void convolve(Plan &P, G *grid, const G *tab, const typename Vec2<G>::type *tw,
                      const int *done, cudaStream_t s) {
     const int n = P.n;
     dim3 gdim((unsigned)(n * n / 16), (unsigned)P.L);
-    ProfRange pr(sizeof(T) == 8 ? NLH_K_CONV64 : NLH_K_CONV32, s);
+    ProfRange pr(sizeof(G) == 8 ? NLH_K_CONV64 : NLH_K_CONV32, s);
     for (int axis = 0; axis < 3; ++axis) {
         switch (n) {
-            case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 64: k_conv<T, 2><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 128: k_conv<T, 4><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 256: k_conv<T, 8><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 32: k_conv<G, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 64: k_conv<G, 2><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 128: k_conv<G, 4><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 256: k_conv<G, 8><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
             default: NLH_REQUIRE(false, "internal: unsupported grid size %d", n);
         }
         NLH_CHECK_LAUNCH();
     }
 }
 
+// One matvec in arithmetic T: gather the input into sorted order, spread,
+// convolve the grids, interpolate, and the epilogue (which also clears the
+// grids and the unit counters for the next matvec).
 template <typename T>
 static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
-                     double *partials, const int *done, const T *wts, T *grid, const T *tab,
-                     const typename Vec2<T>::type *tw, const double *d, cudaStream_t s) {
+                     double *partials, const int *done, const typename Num<T>::R *wts,
+                     typename Num<T>::G *grid, const typename Num<T>::G *tab,
+                     const typename Vec2<typename Num<T>::G>::type *tw, const double *d,
+                     cudaStream_t s) {
+    using G = typename Num<T>::G;
     T *xs = reinterpret_cast<T *>(P.xs);
     {
         ProfRange pr(NLH_K_EPILOGUE, s);
@@ -824,11 +940,11 @@ static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
         NLH_CHECK_LAUNCH();
     }
     spread_interp<T>(P, true, wts, grid, xs, done, s);
-    convolve<T>(P, grid, tab, tw, done, s);
+    convolve<G>(P, grid, tab, tw, done, s);
     spread_interp<T>(P, false, wts, grid, nullptr, done, s);
     const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
     ProfRange pr(NLH_K_EPILOGUE, s);
-    k_epilogue<T><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, op, y, partials,
+    k_epilogue<G><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, op, y, partials,
                                                      grid, ge, P.unit_ctr, done);
     NLH_CHECK_LAUNCH();
 }
@@ -839,10 +955,14 @@ void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
         NLH_REQUIRE(P.precision & 1, "matvec: FP64 path not built in this plan");
         matvec_t<double>(P, op, alpha, x, y, partials, done, P.wts64, P.grid64, P.tab64, P.tw64,
                          P.d64, s);
-    } else {
+    } else if (prec == NLH_FP32) {
         NLH_REQUIRE(P.precision & 2, "matvec: FP32 path not built in this plan");
         matvec_t<float>(P, op, alpha, x, y, partials, done, P.wts32, P.grid32, P.tab32, P.tw32,
                         P.d32, s);
+    } else {
+        NLH_REQUIRE(P.precision & 4, "matvec: double-float path not built in this plan");
+        matvec_t<df32>(P, op, alpha, x, y, partials, done, P.wtsdf, P.grid64, P.tab64, P.tw64,
+                       P.ddf, s);
     }
 }
 
@@ -855,8 +975,8 @@ extern "C" nlh_status nlh_matvec(nlh_plan plan, int op, int precision, double al
         NLH_REQUIRE(plan && x && y, "nlh_matvec: NULL pointer");
         NLH_REQUIRE(x != y, "nlh_matvec: x and y must not alias");
         NLH_REQUIRE(op >= 0 && op <= 2, "nlh_matvec: op=%d", op);
-        NLH_REQUIRE(precision == NLH_FP64 || precision == NLH_FP32, "nlh_matvec: precision=%d",
-                    precision);
+        NLH_REQUIRE(precision == NLH_FP64 || precision == NLH_FP32 || precision == NLH_DF32,
+                    "nlh_matvec: precision=%d", precision);
         plan->stream = (cudaStream_t)stream;
         nlh::matvec(*plan, op, precision, alpha, x, y, nullptr, nullptr, (cudaStream_t)stream);
         return NLH_OK;

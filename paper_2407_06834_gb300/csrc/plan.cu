@@ -399,7 +399,8 @@ static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &co
 
 __global__ void k_weights(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
                           int L, int m, int K, const double *__restrict__ coef, int rec64,
-                          int rec32, double *__restrict__ w64, float *__restrict__ w32) {
+                          int rec32, double *__restrict__ w64, float *__restrict__ w32,
+                          float *__restrict__ wdf) {
     __shared__ double sc[16 * kMaxPolyCoef];
     const int W2 = 2 * m;
     for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
@@ -419,6 +420,11 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
                 for (int q = K - 2; q >= 0; --q) w = fma(w, y, a[q]);
                 if (w64) w64[sidx * rec64 + t * W2 + j] = w;
                 if (w32) w32[sidx * rec32 + t * W2 + j] = (float)w;
+                if (wdf) {  // double-float record: per dim 2m high parts, then 2m low parts
+                    const float hi = (float)w;
+                    wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
+                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = (float)(w - (double)hi);
+                }
             }
         }
         if (w64)
@@ -569,6 +575,7 @@ void plan_degrees(Plan &P, cudaStream_t s) {
     NLH_CHECK_LAUNCH();
     if (P.precision & 1) matvec(P, 0, NLH_FP64, 0.0, P.t, P.d64, nullptr, nullptr, s);
     if (P.precision & 2) matvec(P, 0, NLH_FP32, 0.0, P.t, P.d32, nullptr, nullptr, s);
+    if (P.precision & 4) matvec(P, 0, NLH_DF32, 0.0, P.t, P.ddf, nullptr, nullptr, s);
 }
 
 static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *features,
@@ -671,8 +678,9 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         const int rec64 = record_len(P.W2, 8), rec32 = record_len(P.W2, 4);
         if (P.precision & 1) P.wts64 = P.alloc<double>((size_t)LN * rec64);
         if (P.precision & 2) P.wts32 = P.alloc<float>((size_t)LN * rec32);
+        if (P.precision & 4) P.wtsdf = P.alloc<float>((size_t)LN * 6 * P.W2);
         k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_coef, rec64, rec32, P.wts64,
-                                     P.wts32);
+                                     P.wts32, P.wtsdf);
         NLH_CHECK_LAUNCH();
         NLH_CUDA(cudaStreamSynchronize(s));
         P.occupied = occ;
@@ -683,13 +691,14 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     for (void *ptr : tmp) cudaFreeAsync(ptr, s);
 
     // tables, grids, outputs, solver workspace
-    if (P.precision & 1) {
+    if (P.precision & 5) {  // FP64 and double-float paths share FP64 grids and tables
         P.tab64 = P.alloc<double>(n);
         P.tw64 = P.alloc<double2>(n / 2);
         P.grid64 = P.alloc<double>((size_t)L * n3);
         NLH_CUDA(cudaMemsetAsync(P.grid64, 0, sizeof(double) * L * n3, s));
-        P.d64 = P.alloc<double>(N);
     }
+    if (P.precision & 1) P.d64 = P.alloc<double>(N);
+    if (P.precision & 4) P.ddf = P.alloc<double>(N);
     if (P.precision & 2) {
         P.tab32 = P.alloc<float>(n);
         P.tw32 = P.alloc<float2>(n / 2);
@@ -710,6 +719,8 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.st = P.alloc<SolveState>(1);
     P.err = P.alloc<int>(1);
     NLH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), s));
+    P.unit_ctr = P.alloc<int>(2);
+    NLH_CUDA(cudaMemsetAsync(P.unit_ctr, 0, sizeof(int) * 2, s));
     P.hist = P.alloc<double>(kMaxHist);
     NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
     plan_tables(P, s);
@@ -764,7 +775,7 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
         NLH_REQUIRE(d.m >= 2 && d.m <= 8 && 2 * d.m < d.n_os, "nlh_plan_create: m=%d", d.m);
         NLH_REQUIRE(d.sigma > 0.0 && std::isfinite(d.sigma), "nlh_plan_create: sigma=%g",
                     d.sigma);
-        NLH_REQUIRE(d.precision >= 1 && d.precision <= 3, "nlh_plan_create: precision=%d",
+        NLH_REQUIRE(d.precision >= 1 && d.precision <= 7, "nlh_plan_create: precision=%d",
                     d.precision);
         NLH_REQUIRE(d.torus_fill >= 0.0 && d.torus_fill < 1.0, "nlh_plan_create: torus_fill=%g",
                     d.torus_fill);

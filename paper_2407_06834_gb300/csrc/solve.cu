@@ -252,7 +252,7 @@ static KrylovResult krylov(Plan &P, int prec, double alpha, const double *rhs, c
     const int64_t N = P.N;
     const int deflate = (method == NLH_PCG_DEFLATED || method == NLH_CG_DEFLATED);
     const int precond = (method == NLH_PCG_JACOBI || method == NLH_PCG_DEFLATED);
-    const double *d = P.d64 ? P.d64 : P.d32;
+    const double *d = P.d64 ? P.d64 : (P.ddf ? P.ddf : P.d32);
     KrylovResult res;
     const int B = kRedBlocks, T = kRedThreads;
     double *part2 = P.partials + 5 * kRedBlocks;  // second stats region (init only)
@@ -316,11 +316,10 @@ static KrylovResult krylov(Plan &P, int prec, double alpha, const double *rhs, c
     return res;
 }
 
-// ||b - A u|| / ||b|| with an FP64 matvec (FP32 if the plan has no FP64
-// path); res (optional) receives b - A u.
-static double true_residual(Plan &P, double alpha, const double *b, const double *u, double *res,
-                            cudaStream_t s) {
-    int prec = (P.precision & 1) ? NLH_FP64 : NLH_FP32;
+// ||b - A u|| / ||b|| with the matvec arithmetic `prec`; res (optional)
+// receives b - A u.
+static double true_residual(Plan &P, int prec, double alpha, const double *b, const double *u,
+                            double *res, cudaStream_t s) {
     matvec(P, 2, prec, alpha, u, P.q, nullptr, nullptr, s);
     k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(b, P.q, P.N, res, P.partials);
     NLH_CHECK_LAUNCH();
@@ -355,25 +354,31 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     "nlh_solve: tol=%g maxit=%d", opts->tol, opts->maxit);
         NLH_REQUIRE(opts->method >= NLH_CG && opts->method <= NLH_CG_DEFLATED,
                     "nlh_solve: method=%d", opts->method);
-        NLH_REQUIRE(opts->arith == NLH_SOLVE_FP64 || opts->arith == NLH_SOLVE_MIXED,
+        NLH_REQUIRE(opts->arith >= NLH_SOLVE_FP64 && opts->arith <= NLH_SOLVE_DF32,
                     "nlh_solve: arith=%d", opts->arith);
         Plan &P = *plan;
         cudaStream_t s = (cudaStream_t)stream;
         P.stream = s;
+        // the FP64-accurate arithmetic: double-float if built, else FP64
+        const int accurate = (P.precision & 4) ? NLH_DF32 : NLH_FP64;
         if (opts->arith == NLH_SOLVE_FP64)
             NLH_REQUIRE(P.precision & 1, "nlh_solve: FP64 solve needs a plan with the FP64 path");
+        else if (opts->arith == NLH_SOLVE_DF32)
+            NLH_REQUIRE(P.precision & 4,
+                        "nlh_solve: double-float solve needs a plan with that path");
         else
-            NLH_REQUIRE((P.precision & 3) == 3,
-                        "nlh_solve: mixed solve needs a plan with both FP64 and FP32 paths");
+            NLH_REQUIRE((P.precision & 2) && (P.precision & 5),
+                        "nlh_solve: mixed solve needs the FP32 path and an FP64-accurate path");
+        const int solve_prec = opts->arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32;
         const double *scale = opts->diag_scale;
         for (int attempt = 0; attempt < 2; ++attempt) {
             const double *x0 = attempt == 0 ? opts->x0 : u;
             int ce = opts->check_every;
             int st = 0;
             inf.iters = 0;
-            if (opts->arith == NLH_SOLVE_FP64) {
-                KrylovResult kr = krylov(P, NLH_FP64, alpha, b, x0, u, 0, opts->tol, opts->maxit,
-                                         opts->method, scale, ce, s);
+            if (opts->arith != NLH_SOLVE_MIXED) {
+                KrylovResult kr = krylov(P, solve_prec, alpha, b, x0, u, 0, opts->tol,
+                                         opts->maxit, opts->method, scale, ce, s);
                 inf.iters = kr.iters;
                 inf.outer = 1;
                 inf.matvecs_fp64 += kr.matvecs + 1;
@@ -383,7 +388,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     NLH_CUDA(cudaMemcpyAsync(opts->hist, P.hist, sizeof(double) * cnt,
                                              cudaMemcpyDeviceToHost, s));
                 }
-                inf.rel_res_true = true_residual(P, alpha, b, u, nullptr, s);
+                inf.rel_res_true = true_residual(P, solve_prec, alpha, b, u, nullptr, s);
                 st = kr.status;
             } else {
                 const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
@@ -393,7 +398,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     if (x0 != u)
                         NLH_CUDA(cudaMemcpyAsync(u, x0, sizeof(double) * P.N,
                                                  cudaMemcpyDeviceToDevice, s));
-                    rel = true_residual(P, alpha, b, u, P.rhs, s);
+                    rel = true_residual(P, accurate, alpha, b, u, P.rhs, s);
                     inf.matvecs_fp64 += 1;
                 } else {
                     NLH_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * P.N, s));
@@ -410,7 +415,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     inf.matvecs_fp32 += kr.matvecs;
                     ++outer;
                     if (kr.status == -4) { st = -4; break; }
-                    rel = true_residual(P, alpha, b, u, P.rhs, s);
+                    rel = true_residual(P, accurate, alpha, b, u, P.rhs, s);
                     inf.matvecs_fp64 += 1;
                     if (opts->hist && outer - 1 < opts->hist_len) opts->hist[outer - 1] = rel;
                 }

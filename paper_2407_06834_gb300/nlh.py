@@ -21,9 +21,9 @@ _lock = threading.Lock()
 _lib = None
 
 NLH_OK, NLH_ERR_NOT_CONVERGED = 0, 1
-NLH_FP64, NLH_FP32 = 0, 1
+NLH_FP64, NLH_FP32, NLH_DF32 = 0, 1, 2
 CG, PCG_JACOBI, PCG_DEFLATED, CG_DEFLATED = 0, 1, 2, 3
-SOLVE_FP64, SOLVE_MIXED = 0, 1
+SOLVE_FP64, SOLVE_MIXED, SOLVE_DF32 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
                 -4: "ERR_BREAKDOWN", -5: "ERR_TIMEOUT"}
 
@@ -224,7 +224,7 @@ class Plan:
                               C.byref(opts), C.byref(info), _stream_ptr(stream))
         _check(st, allow_not_converged=True)
         d = info.as_dict()
-        n = (d["iters"] + 1) if arith == SOLVE_FP64 else d["outer"]
+        n = (d["iters"] + 1) if arith != SOLVE_MIXED else d["outer"]
         return SolveResult(u, d, hist[:max(0, min(n, hist_len))].copy())
 
     def close(self):

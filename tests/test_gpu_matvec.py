@@ -55,6 +55,33 @@ def test_fp64_tight_parameters_match_direct_sum(img64):
         assert relmax(y, ref) < 1e-10, relmax(y, ref)
 
 
+def test_df32_tight_parameters_match_direct_sum(img64):
+    """The double-float path (pairs of floats) is FP64-accurate: same 1e-10
+    bar against the direct sum as the FP64 path."""
+    img, coords = img64
+    P = make_plan(img, M=64, n_os=128, m=8, fill=0.5, precision=5)
+    v = random_vector(img.size, 21)
+    ref = orc.gamma_full_matvec(coords, SIGMA, v)
+    y = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_DF32))
+    assert relmax(y, ref) < 1e-10, relmax(y, ref)
+    y64 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+    assert relmax(y, y64) < 1e-12
+
+
+def test_df32_configured_parameters_and_laplacian(img64):
+    img, coords = img64
+    P = make_plan(img, precision=7)
+    N = img.size
+    v = random_vector(N, 22)
+    y64 = host(P.matvec(cuda(v), op=2, alpha=0.5, precision=nlh.NLH_FP64))
+    ydf = host(P.matvec(cuda(v), op=2, alpha=0.5, precision=nlh.NLH_DF32))
+    assert relmax(ydf, y64) < 1e-11, relmax(ydf, y64)
+    one = cuda(np.ones(N))
+    d = host(P.matvec(one, op=0, precision=nlh.NLH_DF32))
+    L1 = host(P.matvec(one, op=1, precision=nlh.NLH_DF32))
+    assert np.max(np.abs(L1)) < 1e-12 * np.max(d)
+
+
 def test_fp64_ragged_image_tight(img64):
     img = image(37, 53, seed=3)
     coords = orc.image_coords(img, 1, raster_windows(1))

@@ -90,6 +90,25 @@ def test_mixed_precision_reaches_fp64_residual():
     assert rel(host(rmx.u), host(r64.u)) < 1e-5
 
 
+def test_df32_solve_matches_oracle_iterates(tight64):
+    """The double-float solve follows the oracle's U-coordinate CG and its
+    solution is certified by the direct operator."""
+    img, coords, _ = tight64
+    P = make_plan(img, M=64, n_os=128, m=8, fill=0.5, precision=6)
+    b = ALPHA * img.ravel()
+    res = P.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_DF32)
+    o = orc.pcg_deflated(coords, SIGMA, ALPHA, 1.0, b, tol=1e-6, maxit=200)
+    assert res.info["iters"] == o.iters
+    np.testing.assert_allclose(res.hist, o.hist[:o.iters + 1], rtol=1e-7)
+    r = b - orc.A_apply(coords, SIGMA, ALPHA, 1.0, host(res.u))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 2e-6
+    # mixed form with double-float refinement residuals
+    rmx = P.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    assert rmx.info["status"] == 0 and rmx.info["rel_res_true"] <= 1e-6
+    r = b - orc.A_apply(coords, SIGMA, ALPHA, 1.0, host(rmx.u))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 2e-6
+
+
 def test_warm_start_and_diag_scale(tight64):
     img, coords, P = tight64
     b = ALPHA * img.ravel()
@@ -137,14 +156,21 @@ def test_breakdown_and_argument_errors(tight64):
 
 
 def test_solve_512_fp64_and_mixed():
-    """The timed workload: both forms reach the 1e-6 FP64 residual."""
+    """The timed workload: every form reaches the 1e-6 FP64-accurate residual
+    and they agree."""
     img = image(512)
-    P = make_plan(img, precision=3)
+    P = make_plan(img, precision=7)
     b = ALPHA * img.ravel()
     r64 = P.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_FP64)
     rmx = P.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    rdf = P.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_DF32)
     assert r64.info["rel_res_true"] <= 1.5e-6 and rmx.info["rel_res_true"] <= 1e-6
+    assert rdf.info["rel_res_true"] <= 1.5e-6
     assert rel(host(rmx.u), host(r64.u)) < 1e-5
+    assert rel(host(rdf.u), host(r64.u)) < 1e-9
+    # the mixed form's double-float residual agrees with an FP64 matvec
+    q = host(P.matvec(rmx.u, op=2, alpha=ALPHA, precision=nlh.NLH_FP64))
+    assert np.linalg.norm(b - q) / np.linalg.norm(b) <= 1.01e-6
     # maximum principle on the large image
     u = host(r64.u)
     assert u.min() >= img.min() - 1e-4 and u.max() <= img.max() + 1e-4
