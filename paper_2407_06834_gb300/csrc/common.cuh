@@ -117,6 +117,8 @@ struct Plan {
     float *tab32 = nullptr;
     double2 *tw64 = nullptr;
     float2 *tw32 = nullptr;
+    float2 *tabdf = nullptr;      // double-float multiplier (hi, lo)
+    float4 *twdf = nullptr;       // double-float twiddles (re hi, re lo, im hi, im lo)
     double *grid64 = nullptr;
     float *grid32 = nullptr;
     double *Y = nullptr;

@@ -45,10 +45,22 @@ __device__ __forceinline__ df32 operator+(df32 a, df32 b) {
     return df32(s, __fadd_rn(t, __fadd_rn(a.lo, b.lo)));
 }
 
+__device__ __forceinline__ df32 operator-(df32 a) { return df32(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+
 __device__ __forceinline__ df32 &operator+=(df32 &a, df32 b) {
     a = a + b;
     return a;
 }
+__device__ __forceinline__ df32 &operator*=(df32 &a, df32 b) {
+    a = a * b;
+    return a;
+}
+
+// Complex double-float (FFT data and twiddles).
+struct cdf {
+    df32 x, y;
+};
 
 __device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) { return a * b + c; }
 

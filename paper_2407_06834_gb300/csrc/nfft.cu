@@ -25,6 +25,7 @@ namespace nlh {
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<df32> { using type = cdf; };
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
@@ -693,14 +694,15 @@ __global__ void k_gather(const double *__restrict__ x, const int *__restrict__ p
 // the two independent convolved lines.
 template <typename T, int R>
 __global__ void __launch_bounds__(256)
-k_conv(T *__restrict__ grid, int axis, const T *__restrict__ tab,
+k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ tab,
        const typename Vec2<T>::type *__restrict__ tw, const int *__restrict__ done) {
+    using G = typename Num<T>::G;
     using C = typename Vec2<T>::type;
     constexpr int n = 32 * R, LPC = 16, PITCH = n + 1;
     __shared__ T S[LPC * PITCH];
     if (done && *done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    T *g = grid + (int64_t)blockIdx.y * n * n * n;
+    G *g = grid + (int64_t)blockIdx.y * n * n * n;
     const int li0 = blockIdx.x * LPC;  // first line of the CTA
     const int a0 = li0 % n, b0 = li0 / n;
     // element (line j, position e) -> global offset
@@ -712,12 +714,12 @@ k_conv(T *__restrict__ grid, int axis, const T *__restrict__ tab,
     if (axis == 0) {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q / n, e = q % n;
-            S[j * PITCH + e] = g[goff(j, e)];
+            S[j * PITCH + e] = T(g[goff(j, e)]);
         }
     } else {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q % LPC, e = q / LPC;
-            S[j * PITCH + e] = g[goff(j, e)];
+            S[j * PITCH + e] = T(g[goff(j, e)]);
         }
     }
     __syncthreads();
@@ -792,12 +794,12 @@ k_conv(T *__restrict__ grid, int axis, const T *__restrict__ tab,
     if (axis == 0) {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q / n, e = q % n;
-            g[goff(j, e)] = S[j * PITCH + e];
+            g[goff(j, e)] = (G)S[j * PITCH + e];
         }
     } else {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q % LPC, e = q / LPC;
-            g[goff(j, e)] = S[j * PITCH + e];
+            g[goff(j, e)] = (G)S[j * PITCH + e];
         }
     }
 }
@@ -905,18 +907,18 @@ static void spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
     }
 }
 
-template <typename G>
-static void convolve(Plan &P, G *grid, const G *tab, const typename Vec2<G>::type *tw,
-                     const int *done, cudaStream_t s) {
+template <typename T>
+static void convolve(Plan &P, typename Num<T>::G *grid, const T *tab,
+                     const typename Vec2<T>::type *tw, const int *done, cudaStream_t s) {
     const int n = P.n;
     dim3 gdim((unsigned)(n * n / 16), (unsigned)P.L);
-    ProfRange pr(sizeof(G) == 8 ? NLH_K_CONV64 : NLH_K_CONV32, s);
+    ProfRange pr(sizeof(T) == 4 ? NLH_K_CONV32 : NLH_K_CONV64, s);
     for (int axis = 0; axis < 3; ++axis) {
         switch (n) {
-            case 32: k_conv<G, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 64: k_conv<G, 2><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 128: k_conv<G, 4><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 256: k_conv<G, 8><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 64: k_conv<T, 2><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 128: k_conv<T, 4><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 256: k_conv<T, 8><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
             default: NLH_REQUIRE(false, "internal: unsupported grid size %d", n);
         }
         NLH_CHECK_LAUNCH();
@@ -929,9 +931,8 @@ static void convolve(Plan &P, G *grid, const G *tab, const typename Vec2<G>::typ
 template <typename T>
 static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
                      double *partials, const int *done, const typename Num<T>::R *wts,
-                     typename Num<T>::G *grid, const typename Num<T>::G *tab,
-                     const typename Vec2<typename Num<T>::G>::type *tw, const double *d,
-                     cudaStream_t s) {
+                     typename Num<T>::G *grid, const T *tab, const typename Vec2<T>::type *tw,
+                     const double *d, cudaStream_t s) {
     using G = typename Num<T>::G;
     T *xs = reinterpret_cast<T *>(P.xs);
     {
@@ -940,7 +941,7 @@ static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
         NLH_CHECK_LAUNCH();
     }
     spread_interp<T>(P, true, wts, grid, xs, done, s);
-    convolve<G>(P, grid, tab, tw, done, s);
+    convolve<T>(P, grid, tab, tw, done, s);
     spread_interp<T>(P, false, wts, grid, nullptr, done, s);
     const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
     ProfRange pr(NLH_K_EPILOGUE, s);
@@ -961,8 +962,9 @@ void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
                         P.d32, s);
     } else {
         NLH_REQUIRE(P.precision & 4, "matvec: double-float path not built in this plan");
-        matvec_t<df32>(P, op, alpha, x, y, partials, done, P.wtsdf, P.grid64, P.tab64, P.tw64,
-                       P.ddf, s);
+        matvec_t<df32>(P, op, alpha, x, y, partials, done, P.wtsdf, P.grid64,
+                       reinterpret_cast<const df32 *>(P.tabdf),
+                       reinterpret_cast<const cdf *>(P.twdf), P.ddf, s);
     }
 }
 

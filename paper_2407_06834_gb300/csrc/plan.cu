@@ -445,7 +445,8 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
 // bit-reversed order for the FFT of nfft.cu.
 __global__ void k_tables(int n, int logn, int M, int m, double beta, double inv_i0b,
                          double sigma_s, double *__restrict__ tab64, float *__restrict__ tab32,
-                         double2 *__restrict__ tw64, float2 *__restrict__ tw32) {
+                         double2 *__restrict__ tw64, float2 *__restrict__ tw32,
+                         float2 *__restrict__ tabdf, float4 *__restrict__ twdf) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int kk = (int)(__brev((unsigned)j) >> (32 - logn));
@@ -469,11 +470,15 @@ __global__ void k_tables(int n, int logn, int M, int m, double beta, double inv_
     }
     if (tab64) tab64[j] = w;
     if (tab32) tab32[j] = (float)w;
+    if (tabdf) tabdf[j] = make_float2((float)w, (float)(w - (double)(float)w));
     if (j < n / 2) {
         double sn, cs;
         sincospi(2.0 * j / n, &sn, &cs);
         if (tw64) tw64[j] = make_double2(cs, -sn);
         if (tw32) tw32[j] = make_float2((float)cs, (float)-sn);
+        if (twdf)
+            twdf[j] = make_float4((float)cs, (float)(cs - (double)(float)cs), (float)-sn,
+                                  (float)(-sn - (double)(float)-sn));
     }
 }
 
@@ -555,7 +560,8 @@ void plan_tables(Plan &P, cudaStream_t s) {
     double sigma_s = P.sigma * P.scale;
     double inv_i0b = 1.0 / std::cyl_bessel_i(0.0, P.kb_beta);
     k_tables<<<div_up(P.n, 256), 256, 0, s>>>(P.n, ilog2(P.n), P.M, P.m, P.kb_beta, inv_i0b,
-                                              sigma_s, P.tab64, P.tab32, P.tw64, P.tw32);
+                                              sigma_s, P.tab64, P.tab32, P.tw64, P.tw32, P.tabdf,
+                                              P.twdf);
     NLH_CHECK_LAUNCH();
 }
 
@@ -698,7 +704,11 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         NLH_CUDA(cudaMemsetAsync(P.grid64, 0, sizeof(double) * L * n3, s));
     }
     if (P.precision & 1) P.d64 = P.alloc<double>(N);
-    if (P.precision & 4) P.ddf = P.alloc<double>(N);
+    if (P.precision & 4) {
+        P.ddf = P.alloc<double>(N);
+        P.tabdf = P.alloc<float2>(n);
+        P.twdf = P.alloc<float4>(n / 2);
+    }
     if (P.precision & 2) {
         P.tab32 = P.alloc<float>(n);
         P.tw32 = P.alloc<float2>(n / 2);
