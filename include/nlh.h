@@ -152,8 +152,10 @@ typedef struct {
                                P_a (learned correction), or NULL             */
     double *hist;           /* HOST, optional residual history ||r_k||/||b||  */
     int hist_len;           /* capacity of hist                               */
-    int check_every;        /* iterations between host convergence checks
-                               (0 = default)                                  */
+    int check_every;        /* 0: the whole Krylov loop runs on the device as
+                               one CUDA graph with a WHILE conditional node
+                               (no host round trip); k > 0: host-driven loop
+                               checking convergence every k iterations       */
 } nlh_solve_opts;
 
 typedef struct {

@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/nlh.h"
@@ -92,6 +93,7 @@ struct SolveState {
     double rz;       // r^T z of the current iterate
     double rz_old;   // copy made by the update kernel
     double rr;       // ||r||^2 of the current iterate
+    double alpha;    // shift of A = alpha I + L
 };
 
 constexpr int kMaxHist = 4096;
@@ -126,12 +128,15 @@ struct Plan {
     double *d64 = nullptr, *d32 = nullptr, *ddf = nullptr;
     // solver workspace
     double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
-           *t = nullptr, *rhs = nullptr, *pinv = nullptr;
+           *t = nullptr, *rhs = nullptr, *pinv = nullptr, *x0 = nullptr, *cbuf = nullptr;
     double *partials = nullptr;   // kRedBlocks * 12 doubles
     SolveState *st = nullptr;     // device
     int *err = nullptr;           // device error word (bounded waits that gave up)
     int *unit_ctr = nullptr;      // device [2]: next unit of spread / interpolation
     SolveState *st_host = nullptr; // pinned mirror
+    double *red_host = nullptr;   // pinned, 2 * kRedBlocks residual partials
+    std::map<int, cudaGraphExec_t> graphs;  // solve graphs (see solve.cu)
+    cudaStream_t capture_stream = nullptr;
     double *hist = nullptr;       // device, kMaxHist
     std::vector<void *> allocs;
     int64_t bytes = 0;
@@ -200,8 +205,10 @@ void retain_pool_memory();
 // gave up (synchronises s).
 void check_device_error(Plan &P, cudaStream_t s);
 void plan_degrees(Plan &P, cudaStream_t s);
+// alpha_dev (optional): read alpha from device memory instead of `alpha`.
 void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
-            double *partials, const int *done, cudaStream_t s);
+            double *partials, const int *done, cudaStream_t s,
+            const double *alpha_dev = nullptr);
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

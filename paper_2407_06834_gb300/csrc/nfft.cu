@@ -811,11 +811,13 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restrict__ x,
-           const double *__restrict__ d, double alpha, int op, double *__restrict__ y,
+           const double *__restrict__ d, double alpha_val, const double *__restrict__ alpha_dev,
+           int op, double *__restrict__ y,
            double *__restrict__ partials, T *__restrict__ grid, int64_t grid_elems,
            int *__restrict__ unit_ctr, const int *__restrict__ done) {
     __shared__ double sh[33];
     if (done && *done) return;
+    const double alpha = alpha_dev ? *alpha_dev : alpha_val;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         unit_ctr[0] = 0;  // the spread and interpolation kernels have finished
         unit_ctr[1] = 0;
@@ -929,10 +931,10 @@ static void convolve(Plan &P, typename Num<T>::G *grid, const T *tab,
 // convolve the grids, interpolate, and the epilogue (which also clears the
 // grids and the unit counters for the next matvec).
 template <typename T>
-static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
-                     double *partials, const int *done, const typename Num<T>::R *wts,
-                     typename Num<T>::G *grid, const T *tab, const typename Vec2<T>::type *tw,
-                     const double *d, cudaStream_t s) {
+static void matvec_t(Plan &P, int op, double alpha, const double *alpha_dev, const double *x,
+                     double *y, double *partials, const int *done,
+                     const typename Num<T>::R *wts, typename Num<T>::G *grid, const T *tab,
+                     const typename Vec2<T>::type *tw, const double *d, cudaStream_t s) {
     using G = typename Num<T>::G;
     T *xs = reinterpret_cast<T *>(P.xs);
     {
@@ -945,24 +947,24 @@ static void matvec_t(Plan &P, int op, double alpha, const double *x, double *y,
     spread_interp<T>(P, false, wts, grid, nullptr, done, s);
     const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
     ProfRange pr(NLH_K_EPILOGUE, s);
-    k_epilogue<G><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, op, y, partials,
-                                                     grid, ge, P.unit_ctr, done);
+    k_epilogue<G><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, alpha_dev, op, y,
+                                                     partials, grid, ge, P.unit_ctr, done);
     NLH_CHECK_LAUNCH();
 }
 
 void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
-            double *partials, const int *done, cudaStream_t s) {
+            double *partials, const int *done, cudaStream_t s, const double *alpha_dev) {
     if (prec == NLH_FP64) {
         NLH_REQUIRE(P.precision & 1, "matvec: FP64 path not built in this plan");
-        matvec_t<double>(P, op, alpha, x, y, partials, done, P.wts64, P.grid64, P.tab64, P.tw64,
-                         P.d64, s);
+        matvec_t<double>(P, op, alpha, alpha_dev, x, y, partials, done, P.wts64, P.grid64,
+                         P.tab64, P.tw64, P.d64, s);
     } else if (prec == NLH_FP32) {
         NLH_REQUIRE(P.precision & 2, "matvec: FP32 path not built in this plan");
-        matvec_t<float>(P, op, alpha, x, y, partials, done, P.wts32, P.grid32, P.tab32, P.tw32,
-                        P.d32, s);
+        matvec_t<float>(P, op, alpha, alpha_dev, x, y, partials, done, P.wts32, P.grid32,
+                        P.tab32, P.tw32, P.d32, s);
     } else {
         NLH_REQUIRE(P.precision & 4, "matvec: double-float path not built in this plan");
-        matvec_t<df32>(P, op, alpha, x, y, partials, done, P.wtsdf, P.grid64,
+        matvec_t<df32>(P, op, alpha, alpha_dev, x, y, partials, done, P.wtsdf, P.grid64,
                        reinterpret_cast<const df32 *>(P.tabdf),
                        reinterpret_cast<const cdf *>(P.twdf), P.ddf, s);
     }

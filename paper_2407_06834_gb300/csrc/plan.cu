@@ -28,11 +28,15 @@ void set_error(const char *fmt, ...) {
 void clear_error() { g_err.clear(); }
 
 Plan::~Plan() {
+    cudaStreamSynchronize(stream);
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
     for (void *ptr : allocs) cudaFreeAsync(ptr, stream);
-    if (st_host) {
+    if (st_host || red_host) {
         cudaStreamSynchronize(stream);
-        cudaFreeHost(st_host);
+        if (st_host) cudaFreeHost(st_host);
+        if (red_host) cudaFreeHost(red_host);
     }
+    if (capture_stream) cudaStreamDestroy(capture_stream);
 }
 
 void retain_pool_memory() {
@@ -725,6 +729,8 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.t = P.alloc<double>(N);
     P.rhs = P.alloc<double>(N);
     P.pinv = P.alloc<double>(N);
+    P.x0 = P.alloc<double>(N);
+    P.cbuf = P.alloc<double>(N);
     P.partials = P.alloc<double>((size_t)kRedBlocks * 12);
     P.st = P.alloc<SolveState>(1);
     P.err = P.alloc<int>(1);
@@ -733,6 +739,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     NLH_CUDA(cudaMemsetAsync(P.unit_ctr, 0, sizeof(int) * 2, s));
     P.hist = P.alloc<double>(kMaxHist);
     NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
+    NLH_CUDA(cudaMallocHost(&P.red_host, sizeof(double) * 2 * kRedBlocks));
     plan_tables(P, s);
     plan_degrees(P, s);
     check_device_error(P, s);

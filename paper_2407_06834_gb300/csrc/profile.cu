@@ -37,6 +37,9 @@ static cudaEvent_t take_event() {
 ProfRange::ProfRange(int cls, cudaStream_t s) : idx_(-1), s_(s) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_enabled) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return;  // event records are not allowed inside a solve graph
     ProfRec r{cls, take_event(), take_event()};
     cudaEventRecord(r.a, s);
     g_recs.push_back(r);

@@ -28,9 +28,11 @@ __device__ __forceinline__ double *pq_parts(double *partials) { return partials 
 
 // ------------------------------------------------------------------ kernels
 // pinv = 1 / (c o (alpha + max(d - 1, 0))) for Jacobi (eta = d - 1, the
-// exact diagonal 1 removed), or 1.
-__global__ void k_pinv(const double *__restrict__ d, const double *__restrict__ c, double alpha,
-                       int precond, int64_t N, double *__restrict__ pinv) {
+// exact diagonal 1 removed), or 1.  alpha is read from the solve state.
+__global__ void k_pinv(const double *__restrict__ d, const double *__restrict__ c,
+                       const SolveState *__restrict__ st, int precond, int64_t N,
+                       double *__restrict__ pinv) {
+    const double alpha = st->alpha;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v = 1.0;
@@ -108,12 +110,22 @@ k_init2(double *__restrict__ r, const double *__restrict__ pinv, int64_t N, int 
 // Shared tail of the init and direction kernels: from the stats partials
 // (sum t, r.t, r.r, sum r) form z = t - mean(t) (deflated) or t, then
 // p = z + beta p.  Block 0 records the scalars and the convergence flag.
+// cond != 0: the WHILE node of a solve graph; block 0 sets it to continue
+// (1) or stop (0) on every path, so the device-side loop always ends once
+// `done` is set (converged, broken down, or k == maxit).
+__device__ __forceinline__ void set_loop(unsigned long long cond, const SolveState *st) {
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, st->done ? 0u : 1u);
+}
+
 __global__ void __launch_bounds__(kRedThreads)
 k_direction(const double *__restrict__ t, double *__restrict__ p, int64_t N, int deflate,
             int first, const double *__restrict__ partials, SolveState *__restrict__ st,
-            double *__restrict__ hist) {
+            double *__restrict__ hist, unsigned long long cond) {
     __shared__ double sh[33];
-    if (st->done) return;
+    if (st->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_loop(cond, st);
+        return;
+    }
     double sum_t = reduce_partials(partials, gridDim.x, 4, 0, sh);
     double rt = reduce_partials(partials, gridDim.x, 4, 1, sh);
     double rr = reduce_partials(partials, gridDim.x, 4, 2, sh);
@@ -140,6 +152,7 @@ k_direction(const double *__restrict__ t, double *__restrict__ p, int64_t N, int
         } else if (rel <= st->tol || k >= st->maxit) {
             st->done = 1;
         }
+        set_loop(cond, st);
     }
 }
 
@@ -185,18 +198,24 @@ k_update(double *__restrict__ w, double *__restrict__ r, const double *__restric
     }
 }
 
-// w = x0 with its mean removed (deflated) or x0; w = 0 if x0 == NULL.
-__global__ void k_start(const double *__restrict__ x0, int64_t N, double mean,
-                        double *__restrict__ w) {
+// w = x0 with its mean removed (deflated; the sum of x0 is in partials
+// slot 0 of the previous k_init1) or x0; w = 0 if x0 == NULL.
+__global__ void __launch_bounds__(kRedThreads)
+k_start(const double *__restrict__ x0, int64_t N, const double *__restrict__ partials,
+        int deflate, double *__restrict__ w) {
+    __shared__ double sh[33];
+    double mean = 0.0;
+    if (x0 && deflate) mean = reduce_partials(partials, gridDim.x, 4, 0, sh) / (double)N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x)
         w[i] = x0 ? x0[i] - mean : 0.0;
 }
 
-// out = (accumulate ? out : 0) + w + shift
+// out = (accumulate ? out : 0) + w + shift, shift = mean(rhs)/alpha for the
+// deflated methods (the exactly solved first block).
 __global__ void k_finish(const double *__restrict__ w, int64_t N, const SolveState *st,
-                         double inv_alpha, int deflate, int accumulate, double *__restrict__ out) {
-    double shift = deflate ? st->bmean * inv_alpha : 0.0;
+                         int deflate, int accumulate, double *__restrict__ out) {
+    double shift = deflate ? st->bmean / st->alpha : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v = w[i] + shift;
@@ -234,103 +253,190 @@ struct KrylovResult {
 
 static double *pq_parts_host(Plan &P) { return P.partials + 4 * kRedBlocks; }
 
-static double host_sum_partials(Plan &P, int count, int stride, int off, cudaStream_t s) {
-    std::vector<double> h((size_t)count * stride);
-    NLH_CUDA(cudaMemcpyAsync(h.data(), P.partials, sizeof(double) * count * stride,
-                             cudaMemcpyDeviceToHost, s));
-    NLH_CUDA(cudaStreamSynchronize(s));
-    double v = 0.0;
-    for (int j = 0; j < count; ++j) v += h[(size_t)j * stride + off];
-    return v;
+static void method_flags(int method, int &deflate, int &precond) {
+    deflate = (method == NLH_PCG_DEFLATED || method == NLH_CG_DEFLATED);
+    precond = (method == NLH_PCG_JACOBI || method == NLH_PCG_DEFLATED);
 }
 
-// One Krylov solve A x = rhs with the NFFT matvec of precision `prec`.
-// x_out = solution (overwritten, or accumulated into if `accumulate`).
-static KrylovResult krylov(Plan &P, int prec, double alpha, const double *rhs, const double *x0,
-                           double *x_out, int accumulate, double tol, int maxit, int method,
-                           const double *diag_scale, int check_every, cudaStream_t s) {
+// Start of a solve: preconditioner, start vector, initial residual and first
+// direction.  The right-hand side is P.rhs, the warm start P.x0, the
+// optional diagonal scale P.cbuf; alpha, tol, maxit come from P.st.
+static void enqueue_init(Plan &P, int prec, int method, bool has_x0, bool has_scale,
+                         unsigned long long cond, cudaStream_t s) {
+    int deflate, precond;
+    method_flags(method, deflate, precond);
     const int64_t N = P.N;
-    const int deflate = (method == NLH_PCG_DEFLATED || method == NLH_CG_DEFLATED);
-    const int precond = (method == NLH_PCG_JACOBI || method == NLH_PCG_DEFLATED);
-    const double *d = P.d64 ? P.d64 : (P.ddf ? P.ddf : P.d32);
-    KrylovResult res;
     const int B = kRedBlocks, T = kRedThreads;
-    double *part2 = P.partials + 5 * kRedBlocks;  // second stats region (init only)
+    const double *d = P.d64 ? P.d64 : (P.ddf ? P.ddf : P.d32);
+    double *part2 = P.partials + 5 * kRedBlocks;
+    k_pinv<<<B, T, 0, s>>>(d, has_scale ? P.cbuf : nullptr, P.st, precond, N, P.pinv);
+    NLH_CHECK_LAUNCH();
+    const double *qptr = nullptr;
+    if (has_x0) {
+        k_init1<<<B, T, 0, s>>>(P.x0, nullptr, N, P.t, P.partials);  // sum x0 -> slot 0
+        NLH_CHECK_LAUNCH();
+        k_start<<<B, T, 0, s>>>(P.x0, N, P.partials, deflate, P.w);
+        NLH_CHECK_LAUNCH();
+        matvec(P, 2, prec, 0.0, P.w, P.q, nullptr, nullptr, s, &P.st->alpha);
+        qptr = P.q;
+    } else {
+        k_start<<<B, T, 0, s>>>(nullptr, N, nullptr, 0, P.w);
+        NLH_CHECK_LAUNCH();
+    }
+    k_init1<<<B, T, 0, s>>>(P.rhs, qptr, N, P.r, P.partials);
+    NLH_CHECK_LAUNCH();
+    k_init2<<<B, T, 0, s>>>(P.r, P.pinv, N, deflate, P.t, P.partials, part2, P.st);
+    NLH_CHECK_LAUNCH();
+    k_direction<<<B, T, 0, s>>>(P.t, P.p, N, deflate, 1, part2, P.st, P.hist, cond);
+    NLH_CHECK_LAUNCH();
+}
 
+// One CG iteration: matvec with the fused p^T A p, update, new direction.
+static void enqueue_iteration(Plan &P, int prec, int method, unsigned long long cond,
+                              cudaStream_t s) {
+    int deflate, precond;
+    method_flags(method, deflate, precond);
+    const int B = kRedBlocks, T = kRedThreads;
+    matvec(P, 2, prec, 0.0, P.p, P.q, pq_parts_host(P), &P.st->done, s, &P.st->alpha);
+    k_update<<<B, T, 0, s>>>(P.w, P.r, P.p, P.q, P.pinv, P.t, P.N, P.partials, P.st);
+    NLH_CHECK_LAUNCH();
+    k_direction<<<B, T, 0, s>>>(P.t, P.p, P.N, deflate, 0, P.partials, P.st, P.hist, cond);
+    NLH_CHECK_LAUNCH();
+}
+
+// A whole solve as one CUDA graph: the start-up kernels, then a WHILE
+// conditional node whose body is one iteration; the direction kernel sets
+// the loop condition from the device-side convergence flag, so the solve
+// runs without any host round trip.  Graphs are cached per plan.
+static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, bool has_scale) {
+    const int key = prec | (method << 2) | ((int)has_x0 << 4) | ((int)has_scale << 5);
+    auto it = P.graphs.find(key);
+    if (it != P.graphs.end()) return it->second;
+    if (!P.capture_stream)
+        NLH_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = P.capture_stream;
+    cudaGraph_t top = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    NLH_CUDA(cudaGraphCreate(&top, 0));
+    try {
+        cudaGraphConditionalHandle h;
+        NLH_CUDA(cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault));
+        NLH_CUDA(cudaStreamBeginCaptureToGraph(cs, top, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_init(P, prec, method, has_x0, has_scale, (unsigned long long)h, cs);
+        } catch (...) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+            throw;
+        }
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        NLH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+        std::vector<cudaGraphNode_t> leaves(deps, deps + ndeps);
+        NLH_CUDA(cudaStreamEndCapture(cs, &top));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        NLH_CUDA(cudaGraphAddNode(&wnode, top, leaves.data(), nullptr, leaves.size(), &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        NLH_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_iteration(P, prec, method, (unsigned long long)h, cs);
+        } catch (...) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+            throw;
+        }
+        NLH_CUDA(cudaStreamEndCapture(cs, &body));
+        NLH_CUDA(cudaGraphInstantiate(&exec, top, 0));
+    } catch (...) {
+        cudaGraphDestroy(top);
+        throw;
+    }
+    cudaGraphDestroy(top);
+    P.graphs[key] = exec;
+    return exec;
+}
+
+// Enqueue one Krylov solve A x = rhs (NFFT arithmetic `prec`): state and
+// inputs into the plan's buffers, the solve (graph, or a host-driven loop
+// when check_every > 0), x_out = solution (or += when accumulate), and a
+// copy of the device state to the pinned mirror.  krylov_collect reads it
+// after the stream has been synchronised.
+static void krylov_launch(Plan &P, int prec, double alpha, const double *rhs, const double *x0,
+                          double *x_out, int accumulate, double tol, int maxit, int method,
+                          const double *scale, int check_every, cudaStream_t s) {
+    int deflate, precond;
+    method_flags(method, deflate, precond);
     SolveState init{};
     init.tol = tol;
     init.maxit = maxit;
     init.rz_old = 1.0;
-    NLH_CUDA(cudaMemcpyAsync(P.st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-    k_pinv<<<B, T, 0, s>>>(d, diag_scale, alpha, precond, N, P.pinv);
-    NLH_CHECK_LAUNCH();
-    // start vector and initial residual
-    const double *qptr = nullptr;
-    if (x0) {
-        double mean = 0.0;
-        if (deflate) {
-            k_init1<<<B, T, 0, s>>>(x0, nullptr, N, P.t, P.partials);  // sum x0 in slot 0
-            NLH_CHECK_LAUNCH();
-            mean = host_sum_partials(P, B, 4, 0, s) / (double)N;
-        }
-        k_start<<<B, T, 0, s>>>(x0, N, mean, P.w);
-        NLH_CHECK_LAUNCH();
-        matvec(P, 2, prec, alpha, P.w, P.q, nullptr, nullptr, s);
-        res.matvecs++;
-        qptr = P.q;
+    init.alpha = alpha;
+    *P.st_host = init;
+    NLH_CUDA(cudaMemcpyAsync(P.st, P.st_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    if (rhs != P.rhs)
+        NLH_CUDA(cudaMemcpyAsync(P.rhs, rhs, sizeof(double) * P.N, cudaMemcpyDeviceToDevice, s));
+    if (x0) NLH_CUDA(cudaMemcpyAsync(P.x0, x0, sizeof(double) * P.N, cudaMemcpyDeviceToDevice, s));
+    if (scale)
+        NLH_CUDA(cudaMemcpyAsync(P.cbuf, scale, sizeof(double) * P.N, cudaMemcpyDeviceToDevice, s));
+    if (check_every <= 0) {
+        cudaGraphExec_t g = solve_graph(P, prec, method, x0 != nullptr, scale != nullptr);
+        NLH_CUDA(cudaGraphLaunch(g, s));
+        count_launch();
     } else {
-        k_start<<<B, T, 0, s>>>(nullptr, N, 0.0, P.w);
-        NLH_CHECK_LAUNCH();
-    }
-    k_init1<<<B, T, 0, s>>>(rhs, qptr, N, P.r, P.partials);
-    NLH_CHECK_LAUNCH();
-    k_init2<<<B, T, 0, s>>>(P.r, P.pinv, N, deflate, P.t, P.partials, part2, P.st);
-    NLH_CHECK_LAUNCH();
-    k_direction<<<B, T, 0, s>>>(P.t, P.p, N, deflate, 1, part2, P.st, P.hist);
-    NLH_CHECK_LAUNCH();
-
-    const int ce = check_every > 0 ? check_every : 4;
-    int launched = 0;
-    while (true) {
-        for (int j = 0; j < ce && launched < maxit; ++j, ++launched) {
-            matvec(P, 2, prec, alpha, P.p, P.q, pq_parts_host(P), &P.st->done, s);
-            k_update<<<B, T, 0, s>>>(P.w, P.r, P.p, P.q, P.pinv, P.t, N, P.partials, P.st);
-            NLH_CHECK_LAUNCH();
-            k_direction<<<B, T, 0, s>>>(P.t, P.p, N, deflate, 0, P.partials, P.st, P.hist);
-            NLH_CHECK_LAUNCH();
+        enqueue_init(P, prec, method, x0 != nullptr, scale != nullptr, 0ull, s);
+        int launched = 0;
+        while (true) {
+            for (int j = 0; j < check_every && launched < maxit; ++j, ++launched)
+                enqueue_iteration(P, prec, method, 0ull, s);
+            NLH_CUDA(cudaMemcpyAsync(P.st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                                     s));
+            NLH_CUDA(cudaStreamSynchronize(s));
+            if (P.st_host->done || launched >= maxit) break;
         }
-        NLH_CUDA(cudaMemcpyAsync(P.st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-        NLH_CUDA(cudaStreamSynchronize(s));
-        if (P.st_host->done || launched >= maxit) break;
     }
+    k_finish<<<kRedBlocks, kRedThreads, 0, s>>>(P.w, P.N, P.st, deflate, accumulate, x_out);
+    NLH_CHECK_LAUNCH();
+    NLH_CUDA(cudaMemcpyAsync(P.st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+}
+
+static KrylovResult krylov_collect(Plan &P, int tol_ok_status_tol_dummy = 0) {
+    (void)tol_ok_status_tol_dummy;
     const SolveState &h = *P.st_host;
+    KrylovResult res;
     res.iters = h.k;
-    res.matvecs += h.k;
+    res.matvecs = h.k;
     res.rel = std::sqrt(h.rr) / (h.bnorm > 0 ? h.bnorm : 1.0);
     if (h.status == -4)
         res.status = -4;
     else
-        res.status = (res.rel <= tol) ? 0 : 1;
-    k_finish<<<B, T, 0, s>>>(P.w, N, P.st, 1.0 / alpha, deflate, accumulate, x_out);
-    NLH_CHECK_LAUNCH();
+        res.status = (res.rel <= h.tol) ? 0 : 1;
     return res;
 }
 
-// ||b - A u|| / ||b|| with the matvec arithmetic `prec`; res (optional)
-// receives b - A u.
-static double true_residual(Plan &P, int prec, double alpha, const double *b, const double *u,
+// b - A u into res (optional) and the partial sums of ||b - A u||^2, ||b||^2
+// copied to the pinned mirror; residual_collect sums them after a sync.
+static void residual_launch(Plan &P, int prec, double alpha, const double *b, const double *u,
                             double *res, cudaStream_t s) {
     matvec(P, 2, prec, alpha, u, P.q, nullptr, nullptr, s);
     k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(b, P.q, P.N, res, P.partials);
     NLH_CHECK_LAUNCH();
-    std::vector<double> h(2 * kRedBlocks);
-    NLH_CUDA(cudaMemcpyAsync(h.data(), P.partials, sizeof(double) * 2 * kRedBlocks,
+    NLH_CUDA(cudaMemcpyAsync(P.red_host, P.partials, sizeof(double) * 2 * kRedBlocks,
                              cudaMemcpyDeviceToHost, s));
-    NLH_CUDA(cudaStreamSynchronize(s));
+}
+
+static double residual_collect(Plan &P) {
     double rr = 0, bb = 0;
     for (int j = 0; j < kRedBlocks; ++j) {
-        rr += h[2 * j];
-        bb += h[2 * j + 1];
+        rr += P.red_host[2 * j];
+        bb += P.red_host[2 * j + 1];
     }
     return std::sqrt(rr) / (bb > 0 ? std::sqrt(bb) : 1.0);
 }
@@ -377,18 +483,21 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
             int st = 0;
             inf.iters = 0;
             if (opts->arith != NLH_SOLVE_MIXED) {
-                KrylovResult kr = krylov(P, solve_prec, alpha, b, x0, u, 0, opts->tol,
-                                         opts->maxit, opts->method, scale, ce, s);
+                krylov_launch(P, solve_prec, alpha, b, x0, u, 0, opts->tol, opts->maxit,
+                              opts->method, scale, ce, s);
+                residual_launch(P, solve_prec, alpha, b, u, nullptr, s);
+                NLH_CUDA(cudaStreamSynchronize(s));
+                KrylovResult kr = krylov_collect(P);
                 inf.iters = kr.iters;
                 inf.outer = 1;
-                inf.matvecs_fp64 += kr.matvecs + 1;
+                inf.matvecs_fp64 += kr.matvecs + 1 + (x0 ? 1 : 0);
                 inf.rel_res = kr.rel;
                 if (opts->hist && opts->hist_len > 0) {
                     int cnt = std::min(opts->hist_len, kr.iters + 1);
-                    NLH_CUDA(cudaMemcpyAsync(opts->hist, P.hist, sizeof(double) * cnt,
-                                             cudaMemcpyDeviceToHost, s));
+                    NLH_CUDA(cudaMemcpy(opts->hist, P.hist, sizeof(double) * cnt,
+                                        cudaMemcpyDeviceToHost));
                 }
-                inf.rel_res_true = true_residual(P, solve_prec, alpha, b, u, nullptr, s);
+                inf.rel_res_true = residual_collect(P);
                 st = kr.status;
             } else {
                 const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
@@ -398,7 +507,9 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     if (x0 != u)
                         NLH_CUDA(cudaMemcpyAsync(u, x0, sizeof(double) * P.N,
                                                  cudaMemcpyDeviceToDevice, s));
-                    rel = true_residual(P, accurate, alpha, b, u, P.rhs, s);
+                    residual_launch(P, accurate, alpha, b, u, P.rhs, s);
+                    NLH_CUDA(cudaStreamSynchronize(s));
+                    rel = residual_collect(P);
                     inf.matvecs_fp64 += 1;
                 } else {
                     NLH_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * P.N, s));
@@ -409,13 +520,16 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 int outer = 0;
                 st = 1;
                 while (rel > opts->tol && outer < max_outer) {
-                    KrylovResult kr = krylov(P, NLH_FP32, alpha, P.rhs, nullptr, u, 1, inner,
-                                             opts->maxit, opts->method, scale, ce, s);
+                    krylov_launch(P, NLH_FP32, alpha, P.rhs, nullptr, u, 1, inner, opts->maxit,
+                                  opts->method, scale, ce, s);
+                    residual_launch(P, accurate, alpha, b, u, P.rhs, s);
+                    NLH_CUDA(cudaStreamSynchronize(s));
+                    KrylovResult kr = krylov_collect(P);
                     inf.iters += kr.iters;
                     inf.matvecs_fp32 += kr.matvecs;
                     ++outer;
                     if (kr.status == -4) { st = -4; break; }
-                    rel = true_residual(P, accurate, alpha, b, u, P.rhs, s);
+                    rel = residual_collect(P);
                     inf.matvecs_fp64 += 1;
                     if (opts->hist && outer - 1 < opts->hist_len) opts->hist[outer - 1] = rel;
                 }

@@ -109,6 +109,24 @@ def test_df32_solve_matches_oracle_iterates(tight64):
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 2e-6
 
 
+@pytest.mark.parametrize("arith", [nlh.SOLVE_FP64, nlh.SOLVE_MIXED])
+def test_graph_solve_equals_host_loop(tight64, arith):
+    """The solve as one CUDA graph (device-side WHILE loop) and the
+    host-driven loop run the same kernels: same iterations, and histories and
+    solutions equal up to the run-to-run rounding of the atomic grid sums."""
+    img, coords, P = tight64
+    b = cuda(ALPHA * img.ravel())
+    g = P.solve(ALPHA, b, tol=1e-7, arith=arith, inner_tol=1e-3)
+    h = P.solve(ALPHA, b, tol=1e-7, arith=arith, inner_tol=1e-3, check_every=3)
+    assert g.info["iters"] == h.info["iters"] and g.info["outer"] == h.info["outer"]
+    np.testing.assert_allclose(g.hist, h.hist, rtol=1e-8)
+    assert rel(host(g.u), host(h.u)) < 1e-10
+    # a second graph launch (cached graph) reproduces the first
+    g2 = P.solve(ALPHA, b, tol=1e-7, arith=arith, inner_tol=1e-3)
+    assert g2.info["iters"] == g.info["iters"]
+    assert rel(host(g2.u), host(g.u)) < 1e-10
+
+
 def test_warm_start_and_diag_scale(tight64):
     img, coords, P = tight64
     b = ALPHA * img.ravel()
