@@ -72,12 +72,16 @@ typedef struct {
     double sigma;           /* kernel width, > 0                             */
     int M;                  /* even, 4 <= M <= n_os                          */
     int n_os;               /* power of two, 32..256                         */
-    int m;                  /* 2..8, and 2m < n_os                           */
+    int m;                  /* 2..8, and 2m < n_os (0 with nfft_eps: auto)   */
     int precision;          /* bit 0: FP64 path, bit 1: FP32 path,
                                bit 2: double-float path (NLH_DF32)           */
     double torus_fill;      /* in (0, 1): fraction of the torus the points
                                span per dim; 0 = choose automatically        */
-    int max_items_pts;      /* points per work item, 0 = default (256)       */
+    int max_items_pts;      /* points per work item, 0 = default (64)        */
+    double nfft_eps;        /* > 0: choose torus_fill, M and n_os (and m when
+                               m = 0) so that the a-priori per-dim alias,
+                               truncation and window errors are <= nfft_eps;
+                               M, n_os, torus_fill are then ignored          */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
@@ -180,6 +184,20 @@ typedef struct {
 nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, double *u,
                      const nlh_solve_opts *opts, nlh_solve_info *info,
                      void *stream);
+
+/* Many solves at once (the batched form of the bilevel sweep): solve i is
+ * (alphas[i] I + L_i) u[i] = b[i] with the operator of plans[i] (each plan
+ * carries its own image, sigma and NFFT parameters).  Solves on distinct
+ * plans run concurrently on internal streams, each solve as one CUDA graph
+ * (or, for NLH_SOLVE_MIXED, one graph per refinement step); solves that
+ * share a plan run one after another.  opts applies to every solve; x0 and
+ * diag_scale must be NULL.  b[i], u[i] are device vectors of the plan's N.
+ * Work is ordered after `stream`; the call synchronises and fills infos[i]
+ * (seconds = wall time of the whole batch).  Returns the worst status. */
+nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, const double *alphas,
+                             const double *const *b, double *const *u,
+                             const nlh_solve_opts *opts, nlh_solve_info *infos,
+                             void *stream);
 
 /* Free a plan and everything it owns.  NULL is accepted. */
 nlh_status nlh_plan_destroy(nlh_plan plan);

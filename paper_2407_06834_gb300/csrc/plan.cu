@@ -549,6 +549,36 @@ static void error_estimates(double sigma, double R, double fill, int M, double *
     *alias = 2.0 * std::exp(-a * a);
 }
 
+// Inverse of erfc on (0, 1] by bisection on std::erfc (monotone).
+static double erfc_inv(double y) {
+    double lo = 0.0, hi = 10.0;
+    for (int k = 0; k < 200; ++k) {
+        double mid = 0.5 * (lo + hi);
+        if (std::erfc(mid) > y) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// NFFT parameters for a per-dim error target eps (used when nfft_eps > 0):
+// alias 2 exp(-((1 - fill)/sigma_s)^2) <= eps gives the torus fill,
+// truncation erfc(pi sigma_s (M/2 - 1)) <= eps the bandwidth M, the grid is
+// the next power of two >= 2M (oversampling >= 2, at most 256), and the
+// Kaiser-Bessel window error ~ exp(-4.44 m) at oversampling 2 gives m.
+static void auto_params(double sigma, double R, double eps, int m_in, int &M, int &n_os, int &m,
+                        double &fill) {
+    const double a = std::sqrt(std::log(2.0 / eps));
+    fill = std::min(0.9, 1.0 / (1.0 + a * sigma / R));
+    const double ss = sigma * fill / R;
+    const double half = 1.0 + erfc_inv(eps) / (M_PI * ss);
+    M = 2 * (int)std::ceil(half);
+    if (M < 8) M = 8;
+    if (M > 128) M = 128;
+    n_os = 32;
+    while (n_os < 2 * M && n_os < 256) n_os *= 2;
+    m = m_in > 0 ? m_in : std::min(8, std::max(2, (int)std::ceil(std::log(1.0 / eps) / 4.44)));
+    if (2 * m >= n_os) m = n_os / 2 - 1;
+}
+
 static double choose_fill(double sigma, double R, int M) {
     double best = 0.5, best_err = INFINITY;
     for (int k = 5; k <= 95; ++k) {
@@ -602,8 +632,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
     P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
     const int64_t N = P.N;
-    const int L = P.L, n = P.n;
-    const int64_t n3 = (int64_t)n * n * n;
+    const int L = P.L;
 
     int *d_win = P.alloc<int>(3 * L);
     NLH_CUDA(cudaMemcpyAsync(d_win, P.windows.data(), sizeof(int) * 3 * L,
@@ -629,9 +658,16 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     }
     if (!(R > 0.0)) R = 1.0;
     P.R = R;
-    P.fill = desc.torus_fill > 0.0 ? desc.torus_fill : choose_fill(P.sigma, R, P.M);
+    if (desc.nfft_eps > 0.0) {
+        auto_params(P.sigma, R, desc.nfft_eps, desc.m, P.M, P.n, P.m, P.fill);
+        P.W2 = 2 * P.m;
+    } else {
+        P.fill = desc.torus_fill > 0.0 ? desc.torus_fill : choose_fill(P.sigma, R, P.M);
+    }
     P.scale = P.fill / R;
     P.kb_beta = M_PI * P.m * (2.0 - (double)P.M / P.n);
+    const int n = P.n;
+    const int64_t n3 = (int64_t)n * n * n;
     double *d_center = P.alloc<double>(3 * L);
     NLH_CUDA(cudaMemcpyAsync(d_center, center.data(), sizeof(double) * 3 * L,
                              cudaMemcpyHostToDevice, s));
@@ -785,11 +821,17 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
         NLH_REQUIRE(d.N >= 2 && d.N <= (int64_t)1 << 30, "nlh_plan_create: N=%lld out of range",
                     (long long)d.N);
         NLH_REQUIRE(d.D >= 1 && d.L >= 1 && d.L <= 64, "nlh_plan_create: D=%d L=%d", d.D, d.L);
-        NLH_REQUIRE(d.n_os >= 32 && d.n_os <= 256 && (d.n_os & (d.n_os - 1)) == 0,
-                    "nlh_plan_create: n_os=%d must be a power of two in [32, 256]", d.n_os);
-        NLH_REQUIRE(d.M >= 4 && d.M <= d.n_os && d.M % 2 == 0,
-                    "nlh_plan_create: M=%d must be even, 4 <= M <= n_os", d.M);
-        NLH_REQUIRE(d.m >= 2 && d.m <= 8 && 2 * d.m < d.n_os, "nlh_plan_create: m=%d", d.m);
+        NLH_REQUIRE(d.nfft_eps >= 0.0 && d.nfft_eps < 0.1, "nlh_plan_create: nfft_eps=%g",
+                    d.nfft_eps);
+        if (d.nfft_eps == 0.0) {
+            NLH_REQUIRE(d.n_os >= 32 && d.n_os <= 256 && (d.n_os & (d.n_os - 1)) == 0,
+                        "nlh_plan_create: n_os=%d must be a power of two in [32, 256]", d.n_os);
+            NLH_REQUIRE(d.M >= 4 && d.M <= d.n_os && d.M % 2 == 0,
+                        "nlh_plan_create: M=%d must be even, 4 <= M <= n_os", d.M);
+            NLH_REQUIRE(d.m >= 2 && d.m <= 8 && 2 * d.m < d.n_os, "nlh_plan_create: m=%d", d.m);
+        } else {
+            NLH_REQUIRE(d.m == 0 || (d.m >= 2 && d.m <= 8), "nlh_plan_create: m=%d", d.m);
+        }
         NLH_REQUIRE(d.sigma > 0.0 && std::isfinite(d.sigma), "nlh_plan_create: sigma=%g",
                     d.sigma);
         NLH_REQUIRE(d.precision >= 1 && d.precision <= 7, "nlh_plan_create: precision=%d",

@@ -19,6 +19,8 @@
 
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 namespace nlh {
 
@@ -554,4 +556,163 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
     inf.status = ret;
     if (info) *info = inf;
     return ret;
+}
+
+// ------------------------------------------------------------------ batched solves
+namespace nlh {
+
+// Library-wide pool of non-blocking streams for batched solves.
+static std::mutex g_pool_mu;
+static std::vector<cudaStream_t> g_pool;
+static std::vector<cudaEvent_t> g_pool_ev;
+
+static void pool_reserve(int n) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    while ((int)g_pool.size() < n) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        NLH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        NLH_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        g_pool.push_back(st);
+        g_pool_ev.push_back(ev);
+    }
+}
+
+}  // namespace nlh
+
+extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, const double *alphas,
+                                        const double *const *b, double *const *u,
+                                        const nlh_solve_opts *opts, nlh_solve_info *infos,
+                                        void *stream) {
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        NLH_REQUIRE(nsolves >= 0 && (nsolves == 0 || (plans && alphas && b && u && opts)),
+                    "nlh_solve_batched: NULL pointer");
+        if (nsolves == 0) return NLH_OK;
+        NLH_REQUIRE(opts->tol > 0.0 && opts->maxit >= 1 && opts->maxit < kMaxHist,
+                    "nlh_solve_batched: tol=%g maxit=%d", opts->tol, opts->maxit);
+        NLH_REQUIRE(opts->method >= NLH_CG && opts->method <= NLH_CG_DEFLATED,
+                    "nlh_solve_batched: method=%d", opts->method);
+        NLH_REQUIRE(opts->arith >= NLH_SOLVE_FP64 && opts->arith <= NLH_SOLVE_DF32,
+                    "nlh_solve_batched: arith=%d", opts->arith);
+        NLH_REQUIRE(opts->x0 == nullptr && opts->diag_scale == nullptr,
+                    "nlh_solve_batched: x0 and diag_scale are per-solve; use nlh_solve");
+        // group the solves by plan (a plan's workspace serves one solve at a time)
+        std::map<nlh_plan, std::vector<int>> by_plan;
+        for (int i = 0; i < nsolves; ++i) {
+            NLH_REQUIRE(plans[i] && b[i] && u[i], "nlh_solve_batched: NULL in solve %d", i);
+            NLH_REQUIRE(alphas[i] > 0.0 && std::isfinite(alphas[i]),
+                        "nlh_solve_batched: alpha[%d]=%g", i, alphas[i]);
+            const int pr = plans[i]->precision;
+            if (opts->arith == NLH_SOLVE_FP64)
+                NLH_REQUIRE(pr & 1, "nlh_solve_batched: plan %d lacks the FP64 path", i);
+            else if (opts->arith == NLH_SOLVE_DF32)
+                NLH_REQUIRE(pr & 4, "nlh_solve_batched: plan %d lacks the double-float path", i);
+            else
+                NLH_REQUIRE((pr & 2) && (pr & 5),
+                            "nlh_solve_batched: plan %d lacks the FP32 or an accurate path", i);
+            by_plan[plans[i]].push_back(i);
+        }
+        std::vector<std::vector<int>> groups;
+        for (auto &kv : by_plan) groups.push_back(kv.second);
+        const int ns = std::min<int>((int)groups.size(), 16);
+        pool_reserve(ns);
+        cudaStream_t caller = (cudaStream_t)stream;
+        cudaEvent_t start_ev;
+        NLH_CUDA(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+        NLH_CUDA(cudaEventRecord(start_ev, caller));
+        for (int k = 0; k < ns; ++k) NLH_CUDA(cudaStreamWaitEvent(g_pool[k], start_ev, 0));
+        cudaEventDestroy(start_ev);
+
+        std::vector<nlh_solve_info> inf(nsolves);
+        std::vector<double> rel(nsolves, 1.0);
+        std::vector<int> outer(nsolves, 0), done(nsolves, 0), status(nsolves, 1);
+        std::vector<size_t> pos(groups.size(), 0);  // next solve of each group
+        const bool mixed = opts->arith == NLH_SOLVE_MIXED;
+        const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        const int max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
+        while (true) {
+            // one round: the current solve of every unfinished group advances one step
+            std::vector<std::pair<int, int>> active;  // (group, solve)
+            for (size_t gi = 0; gi < groups.size(); ++gi) {
+                if (pos[gi] >= groups[gi].size()) continue;
+                const int i = groups[gi][pos[gi]];
+                Plan &P = *plans[i];
+                cudaStream_t s = g_pool[gi % ns];
+                P.stream = s;
+                const int accurate = (P.precision & 4) ? NLH_DF32 : NLH_FP64;
+                if (!mixed) {
+                    const int prec = opts->arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32;
+                    krylov_launch(P, prec, alphas[i], b[i], nullptr, u[i], 0, opts->tol,
+                                  opts->maxit, opts->method, nullptr, 0, s);
+                    residual_launch(P, prec, alphas[i], b[i], u[i], nullptr, s);
+                } else {
+                    if (outer[i] == 0) {
+                        NLH_CUDA(cudaMemsetAsync(u[i], 0, sizeof(double) * P.N, s));
+                        NLH_CUDA(cudaMemcpyAsync(P.rhs, b[i], sizeof(double) * P.N,
+                                                 cudaMemcpyDeviceToDevice, s));
+                    }
+                    krylov_launch(P, NLH_FP32, alphas[i], P.rhs, nullptr, u[i], 1, inner,
+                                  opts->maxit, opts->method, nullptr, 0, s);
+                    residual_launch(P, accurate, alphas[i], b[i], u[i], P.rhs, s);
+                }
+                active.push_back({(int)gi, i});
+            }
+            if (active.empty()) break;
+            for (int k = 0; k < ns; ++k) NLH_CUDA(cudaStreamSynchronize(g_pool[k]));
+            for (auto &a : active) {
+                const int gi = a.first, i = a.second;
+                Plan &P = *plans[i];
+                KrylovResult kr = krylov_collect(P);
+                const double r = residual_collect(P);
+                inf[i].iters += kr.iters;
+                ++outer[i];
+                if (!mixed) {
+                    inf[i].matvecs_fp64 += kr.matvecs + 1;
+                    inf[i].rel_res = kr.rel;
+                    status[i] = kr.status;
+                    done[i] = 1;
+                } else {
+                    inf[i].matvecs_fp32 += kr.matvecs;
+                    inf[i].matvecs_fp64 += 1;
+                    inf[i].rel_res = r;
+                    if (kr.status == -4) {
+                        status[i] = -4;
+                        done[i] = 1;
+                    } else if (r <= opts->tol) {
+                        status[i] = 0;
+                        done[i] = 1;
+                    } else if (outer[i] >= max_outer) {
+                        status[i] = 1;
+                        done[i] = 1;
+                    }
+                }
+                inf[i].rel_res_true = r;
+                inf[i].outer = outer[i];
+                if (done[i]) ++pos[gi];
+            }
+        }
+        for (int k = 0; k < ns; ++k) {
+            NLH_CUDA(cudaEventRecord(g_pool_ev[k], g_pool[k]));
+            NLH_CUDA(cudaStreamWaitEvent(caller, g_pool_ev[k], 0));
+        }
+        for (int i = 0; i < nsolves; ++i) check_device_error(*plans[i], g_pool[0]);
+        const double secs =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        nlh_status worst = NLH_OK;
+        for (int i = 0; i < nsolves; ++i) {
+            inf[i].status = status[i] == 0 ? NLH_OK
+                                           : (status[i] == -4 ? NLH_ERR_BREAKDOWN
+                                                              : NLH_ERR_NOT_CONVERGED);
+            inf[i].seconds = secs;
+            if (infos) infos[i] = inf[i];
+            if (inf[i].status == NLH_ERR_BREAKDOWN) worst = NLH_ERR_BREAKDOWN;
+            else if (inf[i].status == NLH_ERR_NOT_CONVERGED && worst == NLH_OK)
+                worst = NLH_ERR_NOT_CONVERGED;
+        }
+        return worst;
+    } catch (Failure &f) {
+        return f.st;
+    }
 }

@@ -32,7 +32,8 @@ class PlanDesc(C.Structure):
     _fields_ = [("N", C.c_int64), ("D", C.c_int), ("L", C.c_int),
                 ("windows", C.POINTER(C.c_int32)), ("sigma", C.c_double), ("M", C.c_int),
                 ("n_os", C.c_int), ("m", C.c_int), ("precision", C.c_int),
-                ("torus_fill", C.c_double), ("max_items_pts", C.c_int)]
+                ("torus_fill", C.c_double), ("max_items_pts", C.c_int),
+                ("nfft_eps", C.c_double)]
 
 
 class PlanInfo(C.Structure):
@@ -73,6 +74,9 @@ SIGNATURES = {
                              C.c_void_p, C.c_void_p]),
     "nlh_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
                             C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
+    "nlh_solve_batched": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
@@ -165,7 +169,7 @@ class Plan:
 
     def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
                  precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
-                 stream=None):
+                 nfft_eps: float = 0.0, stream=None):
         lib = load()
         N, D = features.shape
         win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
@@ -173,7 +177,8 @@ class Plan:
         desc = PlanDesc(N=N, D=D, L=win.shape[0],
                         windows=win.ctypes.data_as(C.POINTER(C.c_int32)), sigma=float(sigma),
                         M=M, n_os=n_os, m=m, precision=precision,
-                        torus_fill=float(torus_fill), max_items_pts=max_items_pts)
+                        torus_fill=float(torus_fill), max_items_pts=max_items_pts,
+                        nfft_eps=float(nfft_eps))
         h = C.c_void_p()
         _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
                                    _stream_ptr(stream)))
@@ -237,3 +242,23 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(plans, alphas, bs, us=None, tol: float = 1e-6, maxit: int = 200,
+                  method: int = PCG_DEFLATED, arith: int = SOLVE_MIXED, inner_tol: float = 0.0,
+                  max_outer: int = 0, stream=None):
+    """Solve (alpha_i I + L_i) u_i = b_i for many plans at once (nlh_solve_batched)."""
+    torch = _torch()
+    n = len(plans)
+    us = us if us is not None else [torch.empty_like(b) for b in bs]
+    hp = (C.c_void_p * n)(*[p.handle for p in plans])
+    ha = (C.c_double * n)(*[float(a) for a in alphas])
+    hb = (C.c_void_p * n)(*[_dptr(b, p.N) for b, p in zip(bs, plans)])
+    hu = (C.c_void_p * n)(*[_dptr(u, p.N) for u, p in zip(us, plans)])
+    opts = SolveOpts(tol=tol, maxit=maxit, method=method, arith=arith, inner_tol=inner_tol,
+                     max_outer=max_outer, x0=None, diag_scale=None, hist=None, hist_len=0,
+                     check_every=0)
+    infos = (SolveInfo * n)()
+    st = load().nlh_solve_batched(n, hp, ha, hb, hu, C.byref(opts), infos, _stream_ptr(stream))
+    _check(st, allow_not_converged=True)
+    return us, [infos[i].as_dict() for i in range(n)]

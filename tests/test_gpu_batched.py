@@ -1,0 +1,68 @@
+"""GPU tests of the batched solves and of the automatic NFFT parameters.
+
+Batched solves must give the same answers as one-at-a-time solves (the
+same kernels run; only the atomic grid sums may round in another order),
+including two solves that share one plan.  Automatic parameters must meet
+their error target against the oracle's direct sums across the sigma range
+of the bilevel sweep.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2407_06834_gb300.inputs import random_vector, raster_windows
+from gpu_helpers import cuda, host, image, make_plan, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2407_06834_gb300 import nlh  # noqa: E402
+
+
+def _auto_plan(img, sigma, eps=1e-7, precision=6):
+    return nlh.Plan.from_image(cuda(img), 1, raster_windows(1), sigma, precision=precision,
+                               nfft_eps=eps, m=0)
+
+
+@pytest.mark.parametrize("sigma", [0.05, 0.2, 1.0])
+def test_auto_parameters_meet_target(sigma):
+    img = image(32, 32, seed=5)
+    P = _auto_plan(img, sigma, precision=7)
+    info = P.info()
+    assert max(info["est_trunc_err"], info["est_alias_err"]) <= 1e-7 * 1.0001
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    v = random_vector(img.size, 31)
+    ref = orc.gamma_full_matvec(coords, sigma, v)
+    y = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_DF32))
+    assert np.max(np.abs(y - ref)) <= 30 * 1e-7 * np.abs(v).sum(), (info, np.max(np.abs(y - ref)))
+
+
+@pytest.mark.parametrize("arith", [nlh.SOLVE_DF32, nlh.SOLVE_MIXED])
+def test_batched_equals_single(arith):
+    imgs = [image(24, 24, seed=1), image(32, 40, seed=2), image(16, 16, seed=3)]
+    sig = [0.1, 0.2, 0.5]
+    plans = [_auto_plan(im, s) for im, s in zip(imgs, sig)]
+    # solve 3 shares plan 0 with solve 0 (another alpha): they must serialise
+    use = [0, 1, 2, 0]
+    alphas = [0.5, 0.05, 2.0, 0.01]
+    bs = [cuda(a * imgs[p].ravel()) for p, a in zip(use, alphas)]
+    us, infos = nlh.solve_batched([plans[p] for p in use], alphas, bs, tol=1e-6, arith=arith,
+                                  inner_tol=1e-3)
+    for k, (p, a) in enumerate(zip(use, alphas)):
+        single = plans[p].solve(a, bs[k], tol=1e-6, arith=arith, inner_tol=1e-3)
+        assert infos[k]["status"] == 0 and infos[k]["rel_res_true"] <= 1.5e-6
+        assert infos[k]["iters"] == single.info["iters"]
+        assert rel(host(us[k]), host(single.u)) < 1e-9
+
+
+def test_batched_rejects_bad_arguments():
+    img = image(16, 16, seed=4)
+    P = _auto_plan(img, 0.2)
+    b = cuda(img.ravel())
+    with pytest.raises(nlh.NLHError):
+        nlh.solve_batched([P], [0.0], [b])
+    with pytest.raises(nlh.NLHError):
+        nlh.solve_batched([P], [0.5], [b], arith=nlh.SOLVE_FP64)   # plan has no FP64 path
