@@ -202,7 +202,7 @@ def run_ours(args):
 
     def step(image, u):
         P = nlh.Plan.from_image(image, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                                n_os=wl.n_os, m=wl.m, precision=6)
+                                n_os=wl.n_os, m=wl.m, precision=6, autotune=True)
         b = image.reshape(-1) * wl.alpha
         res = P.solve(wl.alpha, b, tol=wl.tol, arith=nlh.SOLVE_MIXED, inner_tol=1e-3, u=u)
         P.close()

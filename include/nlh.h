@@ -82,6 +82,7 @@ typedef struct {
                                m = 0) so that the a-priori per-dim alias,
                                truncation and window errors are <= nfft_eps;
                                M, n_os, torus_fill are then ignored          */
+    int unit_points;        /* points per work unit (one CTA), 0 = 512       */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
@@ -109,9 +110,26 @@ typedef struct {
     int64_t occupied_cells;          /* non-empty (window, cell) pairs       */
     double est_trunc_err, est_alias_err; /* a-priori per-dim error estimates */
     int64_t device_bytes;            /* device memory owned by the plan      */
+    int64_t n_units;                 /* work units (one CTA each)            */
+    int max_items_pts, unit_points;  /* current tiling of the work           */
 } nlh_plan_info;
 
 nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
+
+/* Re-split the plan's sorted points into work items of at most
+ * max_items_pts points (all of one grid cell) and work units of at most
+ * unit_points points (one CTA each), in place.  Changes only the
+ * decomposition of the work, never the result beyond rounding.
+ * Synchronises `stream`. */
+nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream);
+
+/* Autotuner: time `reps` matvecs (0 = 3) of every NFFT arithmetic in the
+ * bit mask `precisions` (0 = all the plan built) for each tiling of a fixed
+ * grid (max_items_pts in {32, 64, 128, 256} x unit_points in {256, 512, 1024,
+ * 2048}) and leave the plan in the fastest; report it (any output pointer
+ * may be NULL) and its summed matvec time in ms.  Synchronises `stream`. */
+nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_kmax,
+                             int *best_unit_points, double *best_ms, void *stream);
 
 /* Matrix-free products (Sec. 3 and Eq. discretized-state), y and x device
  * FP64 vectors of length N (y must not alias x):

@@ -98,12 +98,13 @@ struct SolveState {
 
 constexpr int kMaxHist = 4096;
 constexpr int kTile = 8;          // tile edge in grid cells (spread/interp units)
-constexpr int kUnitPoints = 512;  // points per work unit before a tile is split
+constexpr int kUnitPoints = 512;  // default points per work unit before a tile is split
 constexpr int kUnitItems = 256;   // items per work unit (staged in shared memory)
 
 struct Plan {
     int64_t N = 0;
-    int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 256;
+    int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 64;
+    int unit_points = kUnitPoints;
     double sigma = 0, fill = 0, scale = 0, R = 0, kb_beta = 0;
     int64_t n_items = 0, occupied = 0;
     std::vector<int32_t> windows;
@@ -143,6 +144,16 @@ struct Plan {
     // Device memory comes from the stream-ordered pool allocator on the
     // stream of the current call; it is released on the last such stream.
     cudaStream_t stream = nullptr;
+
+    // Frees one array of `allocs` early (stream-ordered).
+    void release(void *ptr) {
+        for (size_t k = 0; k < allocs.size(); ++k)
+            if (allocs[k] == ptr) {
+                cudaFreeAsync(ptr, stream);
+                allocs.erase(allocs.begin() + k);
+                return;
+            }
+    }
 
     template <typename T> T *alloc(size_t count) {
         void *ptr = nullptr;

@@ -510,7 +510,7 @@ static void build_units(Plan &P, cudaStream_t s) {
         int64_t j = i;
         int pts = 0;
         while (j < P.n_items && (items[j].x >> 16) == l && items[j].y == tile &&
-               j - i < kUnitItems && (j == i || pts + items[j].w <= kUnitPoints)) {
+               j - i < kUnitItems && (j == i || pts + items[j].w <= P.unit_points)) {
             pts += items[j].w;
             ++j;
         }
@@ -524,11 +524,48 @@ static void build_units(Plan &P, cudaStream_t s) {
     std::vector<int4> u(units.size());
     for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
     P.n_units = (int64_t)u.size();
+    if (P.units) P.release(P.units);
     P.units = P.alloc<int4>(u.size());
     if (!u.empty())
         NLH_CUDA(cudaMemcpyAsync(P.units, u.data(), sizeof(int4) * u.size(),
                                  cudaMemcpyHostToDevice, s));
     NLH_CUDA(cudaStreamSynchronize(s));
+}
+
+// Re-split the plan's points into items of at most kmax points and units of
+// at most unit_points points, in place: the cells of the current items are
+// recovered on the host (items of one cell are consecutive and contiguous
+// in sorted order) and cut again; no re-sort, no new weights.
+static void retile(Plan &P, int kmax, int unit_points, cudaStream_t s) {
+    std::vector<int4> items(P.n_items);
+    if (P.n_items)
+        NLH_CUDA(cudaMemcpyAsync(items.data(), P.items, sizeof(int4) * P.n_items,
+                                 cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    std::vector<int4> out;
+    out.reserve(items.size());
+    size_t i = 0;
+    while (i < items.size()) {
+        int4 cell = items[i];
+        size_t j = i + 1;
+        while (j < items.size() && items[j].x == cell.x && items[j].y == cell.y &&
+               items[j].z == cell.z + cell.w) {
+            cell.w += items[j].w;
+            ++j;
+        }
+        for (int t = 0; t < cell.w; t += kmax)
+            out.push_back(make_int4(cell.x, cell.y, cell.z + t, std::min(kmax, cell.w - t)));
+        i = j;
+    }
+    if (P.items) P.release(P.items);
+    P.n_items = (int64_t)out.size();
+    P.items = P.alloc<int4>(out.size());
+    if (!out.empty())
+        NLH_CUDA(cudaMemcpyAsync(P.items, out.data(), sizeof(int4) * out.size(),
+                                 cudaMemcpyHostToDevice, s));
+    P.kmax = kmax;
+    P.unit_points = unit_points;
+    build_units(P, s);
 }
 
 static int ilog2(int n) {
@@ -630,6 +667,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.precision = desc.precision;
     P.sigma = desc.sigma;
     P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
+    P.unit_points = desc.unit_points > 0 ? desc.unit_points : kUnitPoints;
     P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
     const int64_t N = P.N;
     const int L = P.L;
@@ -891,10 +929,87 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info) {
         info->sigma_torus = plan->sigma * plan->scale;
         info->max_range = plan->R;
         info->n_items = plan->n_items;
+        info->n_units = plan->n_units;
+        info->max_items_pts = plan->kmax;
+        info->unit_points = plan->unit_points;
         info->occupied_cells = plan->occupied;
         error_estimates(plan->sigma, plan->R, plan->fill, plan->M, &info->est_trunc_err,
                         &info->est_alias_err);
         info->device_bytes = plan->bytes;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan, "nlh_plan_retile: NULL plan");
+        NLH_REQUIRE(max_items_pts >= 1 && max_items_pts <= 4096,
+                    "nlh_plan_retile: max_items_pts=%d", max_items_pts);
+        NLH_REQUIRE(unit_points >= 1 && unit_points <= (1 << 20), "nlh_plan_retile: unit_points=%d",
+                    unit_points);
+        cudaStream_t s = (cudaStream_t)stream;
+        plan->stream = s;
+        retile(*plan, max_items_pts, unit_points, s);
+        NLH_CUDA(cudaStreamSynchronize(s));
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_kmax,
+                             int *best_unit_points, double *best_ms, void *stream) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan, "nlh_plan_autotune: NULL plan");
+        const int mask = precisions ? precisions : plan->precision;
+        NLH_REQUIRE((mask & plan->precision) == mask && mask > 0,
+                    "nlh_plan_autotune: precisions=%d not built", precisions);
+        cudaStream_t s = (cudaStream_t)stream;
+        plan->stream = s;
+        Plan &P = *plan;
+        const int r = reps > 0 ? reps : 3;
+        // probe vector: the degree input (ones) is already in P.t
+        k_fill<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N, 1.0);
+        NLH_CHECK_LAUNCH();
+        cudaEvent_t e0, e1;
+        NLH_CUDA(cudaEventCreate(&e0));
+        NLH_CUDA(cudaEventCreate(&e1));
+        const int kmaxes[] = {32, 64, 128, 256};
+        const int unitpts[] = {256, 512, 1024, 2048};
+        double best = INFINITY;
+        int bk = P.kmax, bu = P.unit_points;
+        for (int km : kmaxes)
+            for (int up : unitpts) {
+                retile(P, km, up, s);
+                double ms_total = 0.0;
+                for (int prec = 0; prec < 3; ++prec) {
+                    if (!(mask & (prec == NLH_FP64 ? 1 : prec == NLH_FP32 ? 2 : 4))) continue;
+                    matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);  // warm
+                    NLH_CUDA(cudaEventRecord(e0, s));
+                    for (int k = 0; k < r; ++k) matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);
+                    NLH_CUDA(cudaEventRecord(e1, s));
+                    NLH_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    NLH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    ms_total += ms / r;
+                }
+                if (ms_total < best) {
+                    best = ms_total;
+                    bk = km;
+                    bu = up;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        retile(P, bk, bu, s);
+        check_device_error(P, s);
+        if (best_kmax) *best_kmax = bk;
+        if (best_unit_points) *best_unit_points = bu;
+        if (best_ms) *best_ms = best;
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;

@@ -33,7 +33,7 @@ class PlanDesc(C.Structure):
                 ("windows", C.POINTER(C.c_int32)), ("sigma", C.c_double), ("M", C.c_int),
                 ("n_os", C.c_int), ("m", C.c_int), ("precision", C.c_int),
                 ("torus_fill", C.c_double), ("max_items_pts", C.c_int),
-                ("nfft_eps", C.c_double)]
+                ("nfft_eps", C.c_double), ("unit_points", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -42,7 +42,8 @@ class PlanInfo(C.Structure):
                 ("torus_fill", C.c_double), ("scale", C.c_double), ("sigma_torus", C.c_double),
                 ("max_range", C.c_double), ("n_items", C.c_int64),
                 ("occupied_cells", C.c_int64), ("est_trunc_err", C.c_double),
-                ("est_alias_err", C.c_double), ("device_bytes", C.c_int64)]
+                ("est_alias_err", C.c_double), ("device_bytes", C.c_int64),
+                ("n_units", C.c_int64), ("max_items_pts", C.c_int), ("unit_points", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -77,6 +78,9 @@ SIGNATURES = {
     "nlh_solve_batched": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_double),
                                     C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                     C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
+    "nlh_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "nlh_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]),
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
@@ -169,22 +173,32 @@ class Plan:
 
     def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
                  precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
-                 nfft_eps: float = 0.0, stream=None):
+                 nfft_eps: float = 0.0, unit_points: int = 0, autotune: bool = False,
+                 stream=None):
         lib = load()
         N, D = features.shape
         win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
         self._win = win
+        tuned = None
+        if autotune and nfft_eps == 0.0 and not max_items_pts and not unit_points:
+            from . import autotune as _at
+            tuned = _at.lookup(n_os, m, win.shape[0], N)
+            if tuned:
+                max_items_pts, unit_points = tuned["max_items_pts"], tuned["unit_points"]
         desc = PlanDesc(N=N, D=D, L=win.shape[0],
                         windows=win.ctypes.data_as(C.POINTER(C.c_int32)), sigma=float(sigma),
                         M=M, n_os=n_os, m=m, precision=precision,
                         torus_fill=float(torus_fill), max_items_pts=max_items_pts,
-                        nfft_eps=float(nfft_eps))
+                        nfft_eps=float(nfft_eps), unit_points=unit_points)
         h = C.c_void_p()
         _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
                                    _stream_ptr(stream)))
         self._h = h
         self.N = N
         self.L = win.shape[0]
+        if autotune and not tuned:
+            from . import autotune as _at
+            _at.tune_and_record(self, stream=stream)
 
     @classmethod
     def from_image(cls, image, radius: int, windows, sigma: float, pad: str = "reflect",
@@ -200,6 +214,16 @@ class Plan:
         inf = PlanInfo()
         _check(load().nlh_plan_get_info(self._h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def retile(self, max_items_pts: int, unit_points: int, stream=None):
+        _check(load().nlh_plan_retile(self._h, int(max_items_pts), int(unit_points),
+                                      _stream_ptr(stream)))
+
+    def autotune(self, precisions: int = 0, reps: int = 3, stream=None):
+        k, u, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        _check(load().nlh_plan_autotune(self._h, precisions, reps, C.byref(k), C.byref(u),
+                                        C.byref(ms), _stream_ptr(stream)))
+        return {"max_items_pts": k.value, "unit_points": u.value, "ms": ms.value}
 
     def set_sigma(self, sigma: float, stream=None):
         _check(load().nlh_plan_set_sigma(self._h, float(sigma), _stream_ptr(stream)))

@@ -66,3 +66,32 @@ def test_batched_rejects_bad_arguments():
         nlh.solve_batched([P], [0.0], [b])
     with pytest.raises(nlh.NLHError):
         nlh.solve_batched([P], [0.5], [b], arith=nlh.SOLVE_FP64)   # plan has no FP64 path
+
+
+def test_retile_and_autotune_keep_results(tmp_path, monkeypatch):
+    """Retiling changes only how the work is split: results agree to
+    rounding (df32 tightly, FP32 at its atomic-order rounding)."""
+    from paper_2407_06834_gb300 import autotune
+    from gpu_helpers import relmax
+    img = image(48, 48, seed=6)
+    P = make_plan(img, precision=7)
+    v = cuda(random_vector(img.size, 41))
+    y0 = host(P.matvec(v, precision=nlh.NLH_DF32))
+    y0f = host(P.matvec(v, precision=nlh.NLH_FP32))
+    for k, u in ((32, 256), (256, 2048), (7, 100), (1, 1)):
+        P.retile(k, u)
+        inf = P.info()
+        assert inf["max_items_pts"] == k and inf["unit_points"] == u
+        assert relmax(host(P.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
+        assert relmax(host(P.matvec(v, precision=nlh.NLH_FP32)), y0f) < 1e-5
+    res = P.autotune(reps=1)
+    assert res["max_items_pts"] in (32, 64, 128, 256)
+    assert res["unit_points"] in (256, 512, 1024, 2048) and res["ms"] > 0
+    assert relmax(host(P.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "at.json"))
+    Q = nlh.Plan.from_image(cuda(img), 1, raster_windows(1), 0.2, precision=7, autotune=True)
+    first = Q.info()
+    R = nlh.Plan.from_image(cuda(img), 1, raster_windows(1), 0.2, precision=7, autotune=True)
+    assert R.info()["max_items_pts"] == first["max_items_pts"]
+    assert R.info()["unit_points"] == first["unit_points"]
+    assert relmax(host(R.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
