@@ -129,3 +129,34 @@ def sweep_pairs():
         for j in range(8):
             out.append(((i + j) % 8, float(sig[i]), float(alp[j])))
     return out
+
+
+# ---- learned warm start: seeded training / evaluation draws --------------
+
+def net_init(shapes, seed: int) -> np.ndarray:
+    """Initial parameters of a convolutional network, flat float32.
+
+    shapes: (cout, k, cin) per layer, in parameter order; each layer's
+    weights [cout][k][k][cin] are drawn N(0, 2 / (k k cin)) (He et al. 2015),
+    its biases are zero.  The last layer (the linear head) is drawn 100x
+    smaller, so that the network starts close to u0 = f, c = 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for i, (cout, k, cin) in enumerate(shapes):
+        std = np.sqrt(2.0 / (k * k * cin))
+        if i == len(shapes) - 1:
+            std *= 0.01
+        parts.append(rng.normal(0.0, std, size=cout * k * k * cin))
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def learned_draws(count: int, seed: int, sigma_range=(0.05, 1.0), alpha_range=(0.01, 10.0)):
+    """(image seed, sigma, alpha) triples, sigma and alpha log-uniform over
+    the bilevel search ranges; image seeds start at 1000 * (seed + 1) so the
+    training images differ from the workload images (seed 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ls = rng.uniform(np.log(sigma_range[0]), np.log(sigma_range[1]), size=count)
+    la = rng.uniform(np.log(alpha_range[0]), np.log(alpha_range[1]), size=count)
+    base = 1000 * (seed + 1)
+    return [(base + i, float(np.exp(s)), float(np.exp(a))) for i, (s, a) in enumerate(zip(ls, la))]
