@@ -13,15 +13,21 @@ The paper has no learned component; this part of the method is defined here
     pooling between encoder levels; nearest-neighbour 2x upsampling, then
     concatenation [upsampled, skip] on the way up; a final 1x1 convolution to
     2 channels (o0, o1) without activation.
-  * Outputs: the initial guess u0 = f + o0 and the log-correction
-    c = clamp(o1, -4, 4) of the Jacobi preconditioner, P_c = P_a * exp(c).
+  * Outputs: the initial guess u0 = mean(f) 1 + o0 (an untrained network,
+    o0 = 0, gives the deflated solver's own start, (mean(b) / alpha) 1 with
+    b = alpha f) and the log-correction c = clamp(o1, -4, 4) of the Jacobi
+    preconditioner, P_c = P_a * exp(c), P_a = alpha + max(d - 1, 0) with
+    d = Gamma_full 1.
   * Loss of one sample (u* the converged solution, r0 = b - A u0 and
-    e0 = u* - u0 for the current u0, both treated as data, beta >= 0):
-        l = ||u0 - u*||^2 / ||f - u*||^2
+    e0 = u* - u0 for a snapshot of u0, both treated as data, beta >= 0):
+        l = ||P_a (u0 - u*)||^2 / ||b - mean(b) 1||^2
             + beta ||r0 / (P_a exp(c)) - e0||^2 / ||e0||^2,
-    averaged over the batch.  The second term fits a diagonal that maps the
-    initial residual to the initial error (the one-step ideal
-    preconditioner).
+    averaged over the batch.  The first term measures the initial error the
+    way the residual b - A u0 = A (u* - u0) does for its rough part (A acts
+    like P_a on components that Gamma averages away) and is normalised by
+    the residual of the solver's own start, b - mean(b) 1.  The second term
+    fits a diagonal that maps the initial residual to the initial error (the
+    one-step ideal preconditioner).
   * Adam (Kingma & Ba 2015, Algorithm 1) on all parameters.
 
 Canonical parameter layout (float, one flat vector): for every 3x3 layer in
@@ -30,8 +36,8 @@ head, weights [2][C] and bias [2].
 
 `forward(..., bf16=True)` rounds the values the GPU stores in bfloat16 (the
 3x3 weights, the input planes, every convolution and pooling output) to
-bfloat16, round-to-nearest-even, so that parity can be tested at the
-accumulation error alone.
+bfloat16, round-to-nearest-even: the difference to the exact network is the
+size of the bfloat16 effect that bounds the GPU's parity.
 """
 from __future__ import annotations
 
@@ -157,7 +163,7 @@ def forward(theta, f, sigma, alpha, base: int = 32, levels: int = 4, bf16: bool 
         x = conv("dec%db" % l, conv("dec%da" % l, x))
     Wh, bh = P["head"]
     o = np.tensordot(x, Wh[:, 0, 0, :], axes=([3], [1])) + bh
-    u0 = f + o[..., 0]
+    u0 = f.mean(axis=(1, 2))[:, None, None] + o[..., 0]
     c = np.clip(o[..., 1], -4.0, 4.0)
     return o, u0, c
 
@@ -172,8 +178,10 @@ def loss(theta, f, sigma, alpha, ustar, r0, e0, pa, beta: float,
     _, u0, c = forward(theta, f, sigma, alpha, base, levels, bf16)
     B = f.shape[0]
     tot = 0.0
+    alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64).reshape(-1), (B,))
     for n in range(B):
-        lu = np.sum((u0[n] - ustar[n]) ** 2) / np.sum((f[n] - ustar[n]) ** 2)
+        lu = (np.sum((pa[n] * (u0[n] - ustar[n])) ** 2)
+              / np.sum((alpha[n] * (f[n] - f[n].mean())) ** 2))
         pr = r0[n] / (pa[n] * np.exp(c[n]))
         lc = np.sum((pr - e0[n]) ** 2) / np.sum(e0[n] ** 2) if beta > 0 else 0.0
         tot += lu + beta * lc

@@ -113,7 +113,7 @@ def test_forward_equals_torch_composition():
     Pt = _torch_unet(theta, base, levels)
     ot = _torch_forward(Pt, torch.from_numpy(f), sig, alp, levels).permute(0, 2, 3, 1).numpy()
     np.testing.assert_allclose(o, ot, rtol=1e-11, atol=1e-13)
-    np.testing.assert_allclose(u0, f + ot[..., 0], rtol=1e-12)
+    np.testing.assert_allclose(u0, f.mean(axis=(1, 2))[:, None, None] + ot[..., 0], rtol=1e-12)
     assert np.all(np.abs(c) <= 4.0)
     # the bf16 emulation stays within bfloat16 resolution of the exact network
     ob, _, _ = unet.forward(theta, f, sig, alp, base, levels, bf16=True)
@@ -135,13 +135,16 @@ def test_loss_closed_forms():
     base, levels = 32, 2
     theta = np.zeros(unet.param_count(base, levels))
     f, _, r0, e0, pa = _loss_data(5, 2, 8, 8)
-    ustar = f + 0.3
+    fbar = f.mean(axis=(1, 2))[:, None, None]
+    ustar = fbar + 0.3 + 0.0 * f
     sig, alp = [0.2, 0.3], [0.5, 0.1]
     theta[-2:] = [0.3, 0.7]
     r0 = pa * np.exp(0.7) * e0
     assert unet.loss(theta, f, sig, alp, ustar, r0, e0, pa, 2.0, base, levels) == pytest.approx(0.0, abs=1e-24)
+    # u0 - u* = 0.01 everywhere: sum (0.01 P_a)^2 / ||alpha (f - mean f)||^2
     theta[-2] = 0.3 + 0.01
-    lu = np.mean([f[0].size * 1e-4 / np.sum((f[n] - ustar[n]) ** 2) for n in range(2)])
+    lu = np.mean([np.sum((0.01 * pa[n]) ** 2) / np.sum((alp[n] * (f[n] - f[n].mean())) ** 2)
+                  for n in range(2)])
     assert unet.loss(theta, f, sig, alp, ustar, r0, e0, pa, 2.0, base, levels) == pytest.approx(lu, rel=1e-9)
     # beyond the clamp c stays at 4
     theta[-1] = 9.0
@@ -171,9 +174,11 @@ def test_finite_difference_matches_autograd():
         Pt[l.name] = (W, b)
     out = _torch_forward(Pt, torch.from_numpy(f), sig, alp, levels)
     ft, ut, rt, et, pt = (torch.from_numpy(a) for a in (f, ustar, r0, e0, pa))
-    u0 = ft + out[:, 0]
+    fbar = ft.mean((1, 2), keepdim=True)
+    u0 = fbar + out[:, 0]
     c = torch.clamp(out[:, 1], -4.0, 4.0)
-    lu = ((u0 - ut) ** 2).sum((1, 2)) / ((ft - ut) ** 2).sum((1, 2))
+    at = torch.from_numpy(alp).reshape(-1, 1, 1)
+    lu = ((pt * (u0 - ut)) ** 2).sum((1, 2)) / ((at * (ft - fbar)) ** 2).sum((1, 2))
     lc = ((rt / (pt * torch.exp(c)) - et) ** 2).sum((1, 2)) / (et ** 2).sum((1, 2))
     (lu + beta * lc).mean().backward()
     g = th.grad.numpy()
