@@ -178,6 +178,10 @@ typedef struct {
                                one CUDA graph with a WHILE conditional node
                                (no host round trip); k > 0: host-driven loop
                                checking convergence every k iterations       */
+    int x0_check;           /* 1: use x0 only if its residual is below that of
+                               the method's own start ((mean(b)/alpha) 1 for
+                               the deflated methods, 0 otherwise), else start
+                               there (info.x0_rejected); 0: use x0 as given */
 } nlh_solve_opts;
 
 typedef struct {
@@ -189,6 +193,8 @@ typedef struct {
     double seconds;         /* wall time of the call                          */
     int used_fallback;      /* 1 if diag_scale was dropped after a failure    */
     int status;             /* same as the return value                       */
+    int x0_rejected;        /* 1 if x0 was not used: its residual was not
+                               below that of the method's own start          */
 } nlh_solve_info;
 
 /* Solve (alpha I + L) u = b (Eq. discretized-state with mu = 1).

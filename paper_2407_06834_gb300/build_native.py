@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnlh.so")
 ROOT = os.path.dirname(HERE)
-HEADER = os.path.join(ROOT, "include", "nlh.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -34,7 +34,7 @@ def _sources():
 
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [HEADER, __file__]:
+    for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + HEADERS + [__file__]:
         with open(p, "rb") as f:
             h.update(p.encode() + f.read())
     h.update(" ".join(NVCC_FLAGS).encode())

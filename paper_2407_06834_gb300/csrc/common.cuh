@@ -135,7 +135,7 @@ struct Plan {
     int *err = nullptr;           // device error word (bounded waits that gave up)
     int *unit_ctr = nullptr;      // device [2]: next unit of spread / interpolation
     SolveState *st_host = nullptr; // pinned mirror
-    double *red_host = nullptr;   // pinned, 2 * kRedBlocks residual partials
+    double *red_host = nullptr;   // pinned, 3 * kRedBlocks residual partials
     std::map<int, cudaGraphExec_t> graphs;  // solve graphs (see solve.cu)
     cudaStream_t capture_stream = nullptr;
     double *hist = nullptr;       // device, kMaxHist

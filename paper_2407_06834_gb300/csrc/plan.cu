@@ -813,7 +813,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     NLH_CUDA(cudaMemsetAsync(P.unit_ctr, 0, sizeof(int) * 2, s));
     P.hist = P.alloc<double>(kMaxHist);
     NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
-    NLH_CUDA(cudaMallocHost(&P.red_host, sizeof(double) * 2 * kRedBlocks));
+    NLH_CUDA(cudaMallocHost(&P.red_host, sizeof(double) * 3 * kRedBlocks));
     plan_tables(P, s);
     plan_degrees(P, s);
     check_device_error(P, s);
@@ -907,6 +907,20 @@ nlh_status nlh_plan_set_sigma(nlh_plan plan, double sigma, void *stream) {
         plan_tables(*plan, s);
         plan_degrees(*plan, s);
         check_device_error(*plan, s);
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_plan_get_degrees(nlh_plan plan, double *d, void *stream) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan && d, "nlh_plan_get_degrees: NULL pointer");
+        const double *src = (plan->precision & 1) ? plan->d64
+                            : (plan->precision & 4) ? plan->ddf : plan->d32;
+        NLH_CUDA(cudaMemcpyAsync(d, src, sizeof(double) * plan->N, cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream));
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;

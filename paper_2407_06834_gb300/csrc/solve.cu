@@ -230,18 +230,20 @@ __global__ void __launch_bounds__(kRedThreads)
 k_residual(const double *__restrict__ b, const double *__restrict__ q, int64_t N,
            double *__restrict__ res, double *__restrict__ partials) {
     __shared__ double sh[33];
-    double s_rr = 0, s_bb = 0;
+    double s_rr = 0, s_bb = 0, s_b = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double bi = b[i], ri = bi - q[i];
         if (res) res[i] = ri;
         s_rr = fma(ri, ri, s_rr);
         s_bb = fma(bi, bi, s_bb);
+        s_b += bi;
     }
-    double v0 = block_sum(s_rr, sh), v1 = block_sum(s_bb, sh);
+    double v0 = block_sum(s_rr, sh), v1 = block_sum(s_bb, sh), v2 = block_sum(s_b, sh);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x * 2 + 0] = v0;
-        partials[blockIdx.x * 2 + 1] = v1;
+        partials[blockIdx.x * 3 + 0] = v0;
+        partials[blockIdx.x * 3 + 1] = v1;
+        partials[blockIdx.x * 3 + 2] = v2;
     }
 }
 
@@ -430,17 +432,22 @@ static void residual_launch(Plan &P, int prec, double alpha, const double *b, co
     matvec(P, 2, prec, alpha, u, P.q, nullptr, nullptr, s);
     k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(b, P.q, P.N, res, P.partials);
     NLH_CHECK_LAUNCH();
-    NLH_CUDA(cudaMemcpyAsync(P.red_host, P.partials, sizeof(double) * 2 * kRedBlocks,
+    NLH_CUDA(cudaMemcpyAsync(P.red_host, P.partials, sizeof(double) * 3 * kRedBlocks,
                              cudaMemcpyDeviceToHost, s));
 }
 
-static double residual_collect(Plan &P) {
-    double rr = 0, bb = 0;
+// ||b - A u|| / ||b||; optionally also ||b - mean(b) 1|| / ||b||, the
+// residual of the deflated methods' own start (mean(b) / alpha) 1 (L 1 = 0).
+static double residual_collect(Plan &P, double *rel_mean_start = nullptr) {
+    double rr = 0, bb = 0, bs = 0;
     for (int j = 0; j < kRedBlocks; ++j) {
-        rr += P.red_host[2 * j];
-        bb += P.red_host[2 * j + 1];
+        rr += P.red_host[3 * j];
+        bb += P.red_host[3 * j + 1];
+        bs += P.red_host[3 * j + 2];
     }
-    return std::sqrt(rr) / (bb > 0 ? std::sqrt(bb) : 1.0);
+    const double nb = bb > 0 ? std::sqrt(bb) : 1.0;
+    if (rel_mean_start) *rel_mean_start = std::sqrt(std::max(0.0, bb - bs * bs / P.N)) / nb;
+    return std::sqrt(rr) / nb;
 }
 
 }  // namespace nlh
@@ -479,8 +486,29 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                         "nlh_solve: mixed solve needs the FP32 path and an FP64-accurate path");
         const int solve_prec = opts->arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32;
         const double *scale = opts->diag_scale;
+        // With x0_check a warm start is used only if its residual is below
+        // that of the method's own start: (mean(b) / alpha) 1 for the
+        // deflated methods, 0 for CG and Jacobi-PCG.
+        const bool mixed = opts->arith == NLH_SOLVE_MIXED;
+        const double *x0_user = opts->x0;
+        double rel_x0 = 1.0;
+        const bool screen = x0_user && opts->x0_check;
+        if (screen) {
+            // mixed: the residual is kept in P.rhs as the first right-hand side
+            residual_launch(P, mixed ? accurate : solve_prec, alpha, b, x0_user,
+                            mixed ? P.rhs : nullptr, s);
+            NLH_CUDA(cudaStreamSynchronize(s));
+            double rel_plain = 1.0;
+            rel_x0 = residual_collect(P, &rel_plain);
+            inf.matvecs_fp64 += 1;
+            const bool deflated = opts->method == NLH_PCG_DEFLATED || opts->method == NLH_CG_DEFLATED;
+            if (!(rel_x0 < (deflated ? rel_plain : 1.0))) {
+                x0_user = nullptr;
+                inf.x0_rejected = 1;
+            }
+        }
         for (int attempt = 0; attempt < 2; ++attempt) {
-            const double *x0 = attempt == 0 ? opts->x0 : u;
+            const double *x0 = attempt == 0 ? x0_user : u;
             int ce = opts->check_every;
             int st = 0;
             inf.iters = 0;
@@ -492,7 +520,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 KrylovResult kr = krylov_collect(P);
                 inf.iters = kr.iters;
                 inf.outer = 1;
-                inf.matvecs_fp64 += kr.matvecs + 1 + (x0 ? 1 : 0);
+                inf.matvecs_fp64 += kr.matvecs + 1 + (x0 && attempt > 0 ? 1 : 0);
                 inf.rel_res = kr.rel;
                 if (opts->hist && opts->hist_len > 0) {
                     int cnt = std::min(opts->hist_len, kr.iters + 1);
@@ -505,7 +533,13 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
                 const int max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
                 double rel;
-                if (x0) {
+                if (x0 && attempt == 0 && screen) {
+                    // screened above: P.rhs = b - A x0
+                    if (x0 != u)
+                        NLH_CUDA(cudaMemcpyAsync(u, x0, sizeof(double) * P.N,
+                                                 cudaMemcpyDeviceToDevice, s));
+                    rel = rel_x0;
+                } else if (x0) {
                     if (x0 != u)
                         NLH_CUDA(cudaMemcpyAsync(u, x0, sizeof(double) * P.N,
                                                  cudaMemcpyDeviceToDevice, s));

@@ -50,14 +50,21 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("method", C.c_int),
                 ("arith", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
                 ("x0", C.c_void_p), ("diag_scale", C.c_void_p), ("hist", C.c_void_p),
-                ("hist_len", C.c_int), ("check_every", C.c_int)]
+                ("hist_len", C.c_int), ("check_every", C.c_int), ("x0_check", C.c_int)]
+
+
+class NetBatch(C.Structure):
+    _fields_ = [("B", C.c_int), ("H", C.c_int), ("W", C.c_int), ("f", C.c_void_p),
+                ("sigma", C.POINTER(C.c_double)), ("alpha", C.POINTER(C.c_double)),
+                ("ustar", C.c_void_p), ("e0", C.c_void_p), ("r0", C.c_void_p),
+                ("deg", C.c_void_p), ("beta", C.c_double)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("matvecs_fp64", C.c_int),
                 ("matvecs_fp32", C.c_int), ("rel_res", C.c_double),
                 ("rel_res_true", C.c_double), ("seconds", C.c_double),
-                ("used_fallback", C.c_int), ("status", C.c_int)]
+                ("used_fallback", C.c_int), ("status", C.c_int), ("x0_rejected", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +93,23 @@ SIGNATURES = {
     "nlh_version": (C.c_char_p, []),
     "nlh_residual_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                              C.c_void_p, C.c_void_p]),
+    "nlh_plan_get_degrees": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nlh_net_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "nlh_net_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "nlh_net_layer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int)]),
+    "nlh_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "nlh_net_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "nlh_net_get_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "nlh_net_forward": (C.c_int, [C.c_void_p, C.POINTER(NetBatch), C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "nlh_net_residual_error": (C.c_int, [C.c_void_p, C.POINTER(NetBatch), C.c_void_p,
+                                         C.c_void_p]),
+    "nlh_net_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(NetBatch), C.POINTER(C.c_double),
+                                    C.c_void_p]),
+    "nlh_net_adam": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_void_p]),
+    "nlh_net_destroy": (C.c_int, [C.c_void_p]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
@@ -225,6 +249,13 @@ class Plan:
                                         C.byref(ms), _stream_ptr(stream)))
         return {"max_items_pts": k.value, "unit_points": u.value, "ms": ms.value}
 
+    def degrees(self, out=None, stream=None):
+        """d = Gamma_full 1 in pixel order (nlh_plan_get_degrees)."""
+        torch = _torch()
+        d = out if out is not None else torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(load().nlh_plan_get_degrees(self._h, _dptr(d, self.N), _stream_ptr(stream)))
+        return d
+
     def set_sigma(self, sigma: float, stream=None):
         _check(load().nlh_plan_set_sigma(self._h, float(sigma), _stream_ptr(stream)))
 
@@ -239,6 +270,7 @@ class Plan:
     def solve(self, alpha: float, b, tol: float = 1e-6, maxit: int = 200,
               method: int = PCG_DEFLATED, arith: int = SOLVE_FP64, inner_tol: float = 0.0,
               max_outer: int = 0, x0=None, diag_scale=None, u=None, check_every: int = 0,
+              x0_check: bool = False,
               hist_len: int = 256, stream=None) -> SolveResult:
         torch = _torch()
         u = u if u is not None else torch.empty_like(b)
@@ -247,7 +279,8 @@ class Plan:
                          max_outer=max_outer,
                          x0=None if x0 is None else _dptr(x0, self.N),
                          diag_scale=None if diag_scale is None else _dptr(diag_scale, self.N),
-                         hist=hist.ctypes.data, hist_len=hist_len, check_every=check_every)
+                         hist=hist.ctypes.data, hist_len=hist_len, check_every=check_every,
+                         x0_check=1 if x0_check else 0)
         info = SolveInfo()
         st = load().nlh_solve(self._h, float(alpha), _dptr(b, self.N), _dptr(u, self.N),
                               C.byref(opts), C.byref(info), _stream_ptr(stream))
@@ -281,8 +314,109 @@ def solve_batched(plans, alphas, bs, us=None, tol: float = 1e-6, maxit: int = 20
     hu = (C.c_void_p * n)(*[_dptr(u, p.N) for u, p in zip(us, plans)])
     opts = SolveOpts(tol=tol, maxit=maxit, method=method, arith=arith, inner_tol=inner_tol,
                      max_outer=max_outer, x0=None, diag_scale=None, hist=None, hist_len=0,
-                     check_every=0)
+                     check_every=0, x0_check=0)
     infos = (SolveInfo * n)()
     st = load().nlh_solve_batched(n, hp, ha, hb, hu, C.byref(opts), infos, _stream_ptr(stream))
     _check(st, allow_not_converged=True)
     return us, [infos[i].as_dict() for i in range(n)]
+
+
+class Net:
+    """The learned warm start and diagonal correction (include/nlh_net.h).
+
+    Images are CUDA float64 tensors of shape (B, H, W) (or (H, W)); sigma and
+    alpha are sequences of B floats."""
+
+    def __init__(self, base: int = 32, levels: int = 4):
+        h = C.c_void_p()
+        _check(load().nlh_net_create(int(base), int(levels), C.byref(h)))
+        self._h = h
+        self.base, self.levels = base, levels
+        nl, npar = C.c_int(), C.c_int64()
+        _check(load().nlh_net_info(h, C.byref(nl), C.byref(npar)))
+        self.n_params = npar.value
+        self.layers = []
+        for i in range(nl.value):
+            a, b, k = C.c_int(), C.c_int(), C.c_int()
+            _check(load().nlh_net_layer(h, i, C.byref(a), C.byref(b), C.byref(k)))
+            self.layers.append((a.value, b.value, k.value))
+
+    def shapes(self):
+        """(cout, k, cin) per layer, the order of the parameter vector."""
+        return [(cout, k, cin) for cin, cout, k in self.layers]
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().nlh_net_set_params(self._h, th.ctypes.data, th.size))
+
+    def params(self) -> np.ndarray:
+        th = np.empty(self.n_params, dtype=np.float32)
+        _check(load().nlh_net_get_params(self._h, th.ctypes.data, th.size))
+        return th
+
+    def grads(self) -> np.ndarray:
+        g = np.empty(self.n_params, dtype=np.float32)
+        _check(load().nlh_net_get_grads(self._h, g.ctypes.data, g.size))
+        return g
+
+    @staticmethod
+    def _batch(f, sigma, alpha, ustar=None, e0=None, r0=None, deg=None, beta=0.0):
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        B, H, W = f.shape
+        n = B * H * W
+        sig = (C.c_double * B)(*[float(x) for x in np.broadcast_to(np.asarray(sigma, float), (B,))])
+        alp = (C.c_double * B)(*[float(x) for x in np.broadcast_to(np.asarray(alpha, float), (B,))])
+        opt = lambda t: None if t is None else _dptr(t, n)
+        nb = NetBatch(B=B, H=H, W=W, f=_dptr(f, n), sigma=sig, alpha=alp, ustar=opt(ustar),
+                      e0=opt(e0), r0=opt(r0), deg=opt(deg), beta=float(beta))
+        nb._keep = (sig, alp)
+        return nb, f.shape
+
+    def forward(self, f, sigma, alpha, u0=None, scale=None, want=("u0", "scale"), stream=None):
+        """Return (u0, scale) as CUDA float64 tensors shaped like f."""
+        torch = _torch()
+        nb, shape = self._batch(f, sigma, alpha)
+        if "u0" in want and u0 is None:
+            u0 = torch.empty(shape, dtype=torch.float64, device=f.device)
+        if "scale" in want and scale is None:
+            scale = torch.empty(shape, dtype=torch.float64, device=f.device)
+        n = nb.B * nb.H * nb.W
+        _check(load().nlh_net_forward(self._h, C.byref(nb),
+                                      None if u0 is None else _dptr(u0, n),
+                                      None if scale is None else _dptr(scale, n),
+                                      _stream_ptr(stream)))
+        return u0, scale
+
+    def residual_error(self, f, sigma, alpha, ustar, e0=None, stream=None):
+        """e0 = ustar - u0 for the current parameters."""
+        torch = _torch()
+        nb, shape = self._batch(f, sigma, alpha, ustar=ustar)
+        e0 = e0 if e0 is not None else torch.empty(shape, dtype=torch.float64, device=f.device)
+        _check(load().nlh_net_residual_error(self._h, C.byref(nb), _dptr(e0, e0.numel()),
+                                             _stream_ptr(stream)))
+        return e0
+
+    def loss_grad(self, f, sigma, alpha, ustar, e0=None, r0=None, deg=None, beta=0.0,
+                  want_loss=True, stream=None):
+        nb, _ = self._batch(f, sigma, alpha, ustar, e0, r0, deg, beta)
+        loss = C.c_double(float("nan"))
+        _check(load().nlh_net_loss_grad(self._h, C.byref(nb), C.byref(loss) if want_loss else None,
+                                        _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             stream=None):
+        _check(load().nlh_net_adam(self._h, float(lr), float(beta1), float(beta2), float(eps),
+                                   _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().nlh_net_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -196,3 +196,29 @@ def test_solve_512_fp64_and_mixed():
     # maximum principle on the large image
     u = host(r64.u)
     assert u.min() >= img.min() - 1e-4 and u.max() <= img.max() + 1e-4
+
+
+def test_warm_start_screening(tight64):
+    """With x0_check a warm start whose residual is not below that of the
+    method's own start is dropped (the solve equals the plain one); a good
+    one is kept."""
+    img, coords, P = tight64
+    b = ALPHA * img.ravel()
+    plain = P.solve(ALPHA, cuda(b), tol=1e-6)
+    bad = cuda(img.ravel() + random_vector(img.size, 31))
+    r = P.solve(ALPHA, cuda(b), tol=1e-6, x0=bad, x0_check=True)
+    assert r.info["x0_rejected"] == 1 and r.info["iters"] == plain.info["iters"]
+    np.testing.assert_allclose(r.hist, plain.hist, rtol=1e-9)   # FP64 atomic-order rounding
+    good = P.solve(ALPHA, cuda(b), tol=1e-3).u
+    r = P.solve(ALPHA, cuda(b), tol=1e-6, x0=good, x0_check=True)
+    assert r.info["x0_rejected"] == 0 and r.info["iters"] < plain.info["iters"]
+    for arith in (nlh.SOLVE_MIXED,):
+        m0 = P.solve(ALPHA, cuda(b), tol=1e-6, arith=arith, inner_tol=1e-3)
+        m1 = P.solve(ALPHA, cuda(b), tol=1e-6, arith=arith, inner_tol=1e-3, x0=bad, x0_check=True)
+        assert m1.info["x0_rejected"] == 1 and m1.info["rel_res_true"] <= 1e-6
+        assert abs(m1.info["iters"] - m0.info["iters"]) <= 1
+        m2 = P.solve(ALPHA, cuda(b), tol=1e-6, arith=arith, inner_tol=1e-3, x0=good, x0_check=True)
+        assert m2.info["x0_rejected"] == 0 and m2.info["rel_res_true"] <= 1e-6
+    # without the check the paper's CG start (x0 = f) is used as given
+    r = P.solve(ALPHA, cuda(b), tol=1e-6, method=nlh.CG, x0=cuda(img.ravel()))
+    assert r.info["x0_rejected"] == 0
