@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--workload", default="img512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle row sample (0 = auto)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-form leg")
+    ap.add_argument("--learned-triples", type=int, default=512,
+                    help="training triples at 256x256 for the learned leg")
+    ap.add_argument("--learned-steps", type=int, default=1000, help="Adam steps (batch 16)")
+    ap.add_argument("--learned-eval", type=int, default=4, help="(sigma, alpha) draws at 1024x1024")
     ap.add_argument("--sweep", action="store_true",
                     help="batched bilevel sweep: 64 (sigma, alpha) solves on 8 uneven images")
     ap.add_argument("--matvec-case", action="store_true",
@@ -336,6 +341,7 @@ def run_ours(args):
         mv_gpts[nm] = N * L / (a.elapsed_time(b_) / 10 * 1e-3) / 1e9
     pinfo = P.info()
     P.close()
+    learned_out = None if args.no_learned or world > 1 else learned_leg(args, dev)
 
     if rank != 0:
         if world > 1:
@@ -370,12 +376,79 @@ def run_ours(args):
         "clocks": clk.summary(),
         "roofline": roof,
         "kernel_ms": prof,
+        "learned": learned_out,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def net_flops_per_image(net, H, W):
+    """Tensor-core FLOPs of one forward pass (3x3 layers; the head is not a GEMM)."""
+    fl = 0.0
+    names = []
+    L = net.levels
+    for l in range(L):
+        names += [l, l]
+    for l in range(L - 2, -1, -1):
+        names += [l, l]
+    for (cin, cout, k), lv in zip(net.layers[:-1], names):
+        cinp = (cin + 31) // 32 * 32
+        fl += 2.0 * 9 * cinp * cout * (H >> lv) * (W >> lv)
+    return fl
+
+
+def learned_leg(args, dev):
+    """Train the network on method-generated 256x256 triples with the
+    library's kernels, then time plain vs learned mixed solves to 1e-6 on
+    1024x1024 images (the learned time includes the network's forward)."""
+    import torch
+
+    from paper_2407_06834_gb300 import learned, nlh
+    from paper_2407_06834_gb300.inputs import learned_draws, synthetic_image
+    out = {}
+    net = learned.new_net(seed=0)
+    data = learned.make_triples(args.learned_triples, 256, 256, seed=0, per_image=4, net=net,
+                                workers=min(16, os.cpu_count() or 1))
+    out["triples"] = {"count": data.count, "size": "256x256", "seconds": data.seconds,
+                      "worst_rel_res_fp64": data.worst_rel_res,
+                      "plain_iters_mean": float(data.iters.mean())}
+    batch = 16
+    epochs = args.learned_steps * batch / data.count
+    log = learned.train(net, data, epochs=epochs, batch=batch, lr=1e-3, beta=0.25,
+                        beta_from=0.5, log_every=100)
+    fl = 3.0 * net_flops_per_image(net, 256, 256) * batch * log.steps
+    out["training"] = {"steps": log.steps, "batch": batch, "seconds": log.seconds,
+                       "snapshot_refresh_seconds": log.refresh_seconds,
+                       "tensor_tflops": fl / log.seconds / 1e12,
+                       "loss_first": log.losses[0][2], "loss_last": log.losses[-1][2]}
+    rows = []
+    for k, (_, sg, al) in enumerate(learned_draws(args.learned_eval, 99)):
+        img = torch.as_tensor(synthetic_image(1024, 1024, 5000 + k)[1], device=dev)
+        P = learned._plan(img, sg)
+        b = img.reshape(-1) * al
+        for _ in range(2):
+            pl = P.solve(al, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+            t0 = time.perf_counter()
+            lr_, t_net = learned.learned_solve(net, P, img, sg, al)
+            t_l = time.perf_counter() - t0
+        rows.append({"sigma": sg, "alpha": al, "plain_iters": pl.info["iters"],
+                     "plain_seconds": pl.info["seconds"], "learned_iters": lr_.info["iters"],
+                     "learned_seconds": t_l, "net_forward_seconds": t_net,
+                     "x0_rejected": lr_.info["x0_rejected"],
+                     "used_fallback": lr_.info["used_fallback"],
+                     "learned_rel_res_fp64": lr_.info["rel_res_true"]})
+        P.close()
+    out["eval_1024"] = rows
+    out["time_ratio_learned_over_plain"] = (sum(r["learned_seconds"] for r in rows)
+                                            / sum(r["plain_seconds"] for r in rows))
+    out["net_forward_tflops_1024"] = (net_flops_per_image(net, 1024, 1024)
+                                      / statistics.mean(r["net_forward_seconds"] for r in rows)
+                                      / 1e12)
+    net.close()
+    return out
 
 
 def matvec_case(args):
