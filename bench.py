@@ -42,6 +42,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32: 152 SMs x 128 FMA lanes x 2 flop; FP64: GB300 nominal 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+# FP32 FLOPs of one double-float stencil multiply-add: TwoProduct by FMA with
+# the two cross terms (1 mul + 3 FMA = 7 FLOP) and TwoSum into the high word
+# with the low word accumulated (8 add/sub) -- 12 instructions, 15 FLOP.
+DF32_FLOP_PER_UPDATE = 15
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/k_nfft_fp32_df32_img512.md (512 x 512 workload); None elsewhere.
+NCU_TRAFFIC_IMG512 = {"spread32": 82.08e6, "interp32": 83.65e6,
+                      "spread_df32": 163.28e6, "interp_df32": 161.94e6}
 
 
 def parse():
@@ -266,23 +274,29 @@ def run_ours(args):
     lib.nlh_profile_reset()
     dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
     W2 = 2 * wl.m
-    flop_per_launch = 2.0 * N * L * W2 ** 3   # (2m)^3 FMAs per point-window
+    updates = float(N * L * W2 ** 3)          # (2m)^3 stencil updates per point-window
     roof = None
     if dom and dom.startswith(("spread", "interp")):
         avg_s = prof[dom]["ms"] / prof[dom]["launches"] * 1e-3
-        ach = flop_per_launch / avg_s / 1e12
-        if dom.endswith("64"):
-            peak, src = FP64_PEAK_TFLOPS, "GB300 nominal FP64 1.25 TFLOP/s"
-            unit = "TFLOP/s"
+        traffic = NCU_TRAFFIC_IMG512.get(dom) if wl.name == "img512" else None
+        if dom.endswith("df32"):
+            ach = DF32_FLOP_PER_UPDATE * updates / avg_s / 1e12
+            peak = FP32_PEAK_TFLOPS
+            src = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; achieved = 15 FP32 FLOP "
+                   "per double-float stencil update (TwoProduct + TwoSum) x (2m)^3 N L / launch "
+                   "time; FP64-accurate rate %.2f TFLOP/s vs FP64 nominal 1.25"
+                   % (2.0 * updates / avg_s / 1e12))
+        elif dom.endswith("64"):
+            ach, peak = 2.0 * updates / avg_s / 1e12, FP64_PEAK_TFLOPS
+            src = "GB300 nominal FP64 1.25 TFLOP/s"
         else:
-            peak, src = FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-            unit = "TFLOP/s"
-            if dom.endswith("df32"):
-                src += "; achieved counts FP64-accurate stencil FLOPs, each done as a " \
-                       "double-float multiply-add of ~11 FP32 operations"
+            ach, peak = 2.0 * updates / avg_s / 1e12, FP32_PEAK_TFLOPS
+            src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak,
-                "unit": unit, "frac": ach / peak, "traffic": None,
-                "peak_source": "derived: " + src}
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                "traffic_note": "ncu DRAM read+write bytes per launch, 512x512 capture"
+                if traffic else None,
+                "mean_launch_ms": avg_s * 1e3, "peak_source": src}
     elif dom:
         roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": None, "unit": "GB/s",
                 "frac": None, "traffic": None}

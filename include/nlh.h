@@ -83,6 +83,11 @@ typedef struct {
                                truncation and window errors are <= nfft_eps;
                                M, n_os, torus_fill are then ignored          */
     int unit_points;        /* points per work unit (one CTA), 0 = 512       */
+    int team[3];            /* launch shape of the spread / interpolation
+                               kernels per NFFT arithmetic (index NLH_FP64,
+                               NLH_FP32, NLH_DF32): 0 default, 1 and 2 the
+                               alternatives compiled for 2m = 8 and 12 (other
+                               widths use 0); results equal up to rounding */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
@@ -112,6 +117,7 @@ typedef struct {
     int64_t device_bytes;            /* device memory owned by the plan      */
     int64_t n_units;                 /* work units (one CTA each)            */
     int max_items_pts, unit_points;  /* current tiling of the work           */
+    int team[3];                     /* current launch shapes (see desc)     */
 } nlh_plan_info;
 
 nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
@@ -123,13 +129,22 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
  * Synchronises `stream`. */
 nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream);
 
+/* Set the launch shape (0, 1, 2; see nlh_plan_desc.team) of the spread and
+ * interpolation kernels of one NFFT arithmetic (NLH_FP64, NLH_FP32,
+ * NLH_DF32).  Changes no result beyond rounding. */
+nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
+
 /* Autotuner: time `reps` matvecs (0 = 3) of every NFFT arithmetic in the
  * bit mask `precisions` (0 = all the plan built) for each tiling of a fixed
  * grid (max_items_pts in {32, 64, 128, 256} x unit_points in {256, 512, 1024,
- * 2048}) and leave the plan in the fastest; report it (any output pointer
- * may be NULL) and its summed matvec time in ms.  Synchronises `stream`. */
+ * 2048}) and, per arithmetic, each launch shape; leave the plan in the
+ * tiling with the smallest sum over the arithmetics of their fastest shape,
+ * with those shapes; report it (any output pointer may be NULL; best_team
+ * has 3 entries indexed like nlh_plan_desc.team) and its summed matvec time
+ * in ms.  Synchronises `stream`. */
 nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_kmax,
-                             int *best_unit_points, double *best_ms, void *stream);
+                             int *best_unit_points, int *best_team, double *best_ms,
+                             void *stream);
 
 /* Matrix-free products (Sec. 3 and Eq. discretized-state), y and x device
  * FP64 vectors of length N (y must not alias x):

@@ -1,6 +1,7 @@
 """Autotuner cache: the fastest work tiling (points per item, points per
-unit) per problem class, found by nlh_plan_autotune and kept in a JSON file
-(one per machine, next to the built library).
+unit) and the spread / interpolation launch shape per arithmetic, per
+problem class, found by nlh_plan_autotune and kept in a JSON file (one per
+machine, next to the built library).
 
 Problem class key: grid size n_os, stencil half-width m, window count L and
 log2 of N; it is known before a plan is built, so a cached tiling goes
@@ -51,6 +52,6 @@ def tune_and_record(plan, stream=None) -> dict:
         d = _read()
         d[key_of(info["n_os"], info["m"], info["L"], info["N"])] = {
             "max_items_pts": res["max_items_pts"], "unit_points": res["unit_points"],
-            "ms": res["ms"]}
+            "team": res["team"], "ms": res["ms"]}
         _write(d)
     return res

@@ -105,6 +105,7 @@ struct Plan {
     int64_t N = 0;
     int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 64;
     int unit_points = kUnitPoints;
+    int team[3] = {0, 0, 0};  // spread / interpolation team shape per arithmetic
     double sigma = 0, fill = 0, scale = 0, R = 0, kb_beta = 0;
     int64_t n_items = 0, occupied = 0;
     std::vector<int32_t> windows;

@@ -15,6 +15,8 @@
 // point.  Spreading flushes each item's accumulators with one atomic add per
 // stencil cell.
 #include "common.cuh"
+
+#include <type_traits>
 #include "async_copy.cuh"
 #include "df32.cuh"
 
@@ -856,11 +858,11 @@ template <typename T> constexpr int interp_class() {
     return sizeof(T) == 4 ? NLH_K_INTERP32 : (Num<T>::kParts == 2 ? NLH_K_INTERPDF : NLH_K_INTERP64);
 }
 
-template <typename T, int W2>
-static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
+template <typename T, int W2, int NW, int TPB>
+static void launch_spread_interp_shape(Plan &P, bool spread, const typename Num<T>::R *wts,
                                  typename Num<T>::G *grid, const T *xs, const int *done,
                                  cudaStream_t s) {
-    constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2, NTH = 32 * NW * TPB;
+    constexpr int NTH = 32 * NW * TPB;
     constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
     if (P.n_units == 0) return;
     static int blocks_spread = 0, blocks_interp = 0;  // per template instance
@@ -892,6 +894,33 @@ static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R 
                                                       P.err);
     }
     NLH_CHECK_LAUNCH();
+}
+
+template <typename T> constexpr int arith_index() {
+    return sizeof(T) == 8 && !std::is_same<T, df32>::value ? NLH_FP64
+           : std::is_same<T, df32>::value                   ? NLH_DF32
+                                                            : NLH_FP32;
+}
+
+// Team shape (warps per team NW, teams per CTA TPB) of the spread and
+// interpolation kernels: fewer accumulator lines per thread (larger teams)
+// against more independent teams per SM.  Shape 0 is the default; shapes 1
+// and 2 are compiled for the stencil widths of the workloads (2m = 8, 12)
+// and picked per arithmetic by the autotuner (plan.team[]).
+template <typename T, int W2>
+static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
+                                 typename Num<T>::G *grid, const T *xs, const int *done,
+                                 cudaStream_t s) {
+    const int shape = P.team[arith_index<T>()];
+    if constexpr (W2 == 8) {
+        if (shape == 1) return launch_spread_interp_shape<T, W2, 2, 2>(P, spread, wts, grid, xs, done, s);
+        if (shape == 2) return launch_spread_interp_shape<T, W2, 2, 4>(P, spread, wts, grid, xs, done, s);
+    } else if constexpr (W2 == 12) {
+        if (shape == 1) return launch_spread_interp_shape<T, W2, 4, 1>(P, spread, wts, grid, xs, done, s);
+        if (shape == 2) return launch_spread_interp_shape<T, W2, 2, 1>(P, spread, wts, grid, xs, done, s);
+    }
+    constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2;
+    launch_spread_interp_shape<T, W2, NW, TPB>(P, spread, wts, grid, xs, done, s);
 }
 
 template <typename T>

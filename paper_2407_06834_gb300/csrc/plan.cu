@@ -5,6 +5,7 @@
 // per window (adjoint NFFT, multiply by the Gaussian's Fourier coefficients,
 // NFFT): Sec. 3, Eq. NFFT and Eq. DGT.  Degrees eta = Gamma 1: Sec. 2.3.
 #include "common.cuh"
+#include "df32.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -438,6 +439,47 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
     }
 }
 
+// The same polynomials evaluated in double-float arithmetic on the FP32
+// pipes (Horner with TwoProduct / TwoSum steps, coefficients split into
+// high and low floats), for plans without the FP64 path: ~46-bit weights
+// for the double-float records, their rounded high parts for the FP32
+// records.  GB300 runs FP32 ~59x faster than FP64, so this is several times
+// faster than the FP64 Horner above.
+__global__ void k_weights_df(const int *__restrict__ perm, const double *__restrict__ u,
+                             int64_t N, int L, int m, int K, const float2 *__restrict__ coef,
+                             int rec32, float *__restrict__ w32, float *__restrict__ wdf) {
+    __shared__ float2 sc[16 * kMaxPolyCoef];
+    const int W2 = 2 * m;
+    for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
+    __syncthreads();
+    const int64_t total = (int64_t)L * N;
+    for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < total;
+         sidx += (int64_t)gridDim.x * blockDim.x) {
+        int l = (int)(sidx / N);
+        int64_t i = perm[sidx];
+        const double *up = u + ((int64_t)l * N + i) * 3;
+        for (int t = 0; t < 3; ++t) {
+            const double ut = up[t];
+            const df32 y(2.0 * (ut - floor(ut)) - 1.0);
+            for (int j = 0; j < W2; ++j) {
+                const float2 *a = sc + j * K;
+                df32 w(a[K - 1].x, a[K - 1].y);
+                for (int q = K - 2; q >= 0; --q) w = w * y + df32(a[q].x, a[q].y);
+                // renormalise (Fast2Sum; |lo| is a few ulps of hi at most)
+                const float hi = __fadd_rn(w.hi, w.lo);
+                const float lo = __fsub_rn(w.lo, __fsub_rn(hi, w.hi));
+                if (w32) w32[sidx * rec32 + t * W2 + j] = hi;
+                if (wdf) {
+                    wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
+                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = lo;
+                }
+            }
+        }
+        if (w32)
+            for (int j = 3 * W2; j < rec32; ++j) w32[sidx * rec32 + j] = 0.0f;
+    }
+}
+
 // ------------------------------------------------------------------ multiplier tables
 // Per dim, the adjoint NFFT, the multiply by the Gaussian's Fourier
 // coefficients and the NFFT (Sec. 3) collapse into one circular convolution
@@ -647,6 +689,12 @@ void check_device_error(Plan &P, cudaStream_t s) {
     }
 }
 
+// d = Gamma_full 1 for each arithmetic of the plan, each from its own
+// operator: the deflated methods rely on L 1 = d - Gamma_full 1 = 0 holding
+// to the rounding of the arithmetic that applies L.  (Taking the FP32 path's
+// degrees from the accurate path leaves L 1 at the FP32 NFFT error times d,
+// which the mixed form's inner solves see: 14 instead of 10 iterations at
+// 512 x 512.)
 void plan_degrees(Plan &P, cudaStream_t s) {
     k_fill<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N, 1.0);
     NLH_CHECK_LAUNCH();
@@ -668,6 +716,11 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.sigma = desc.sigma;
     P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
     P.unit_points = desc.unit_points > 0 ? desc.unit_points : kUnitPoints;
+    for (int a = 0; a < 3; ++a) {
+        NLH_REQUIRE(desc.team[a] >= 0 && desc.team[a] <= 2, "nlh_plan_create: team[%d]=%d", a,
+                    desc.team[a]);
+        P.team[a] = desc.team[a];
+    }
     P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
     const int64_t N = P.N;
     const int L = P.L;
@@ -763,8 +816,23 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         if (P.precision & 1) P.wts64 = P.alloc<double>((size_t)LN * rec64);
         if (P.precision & 2) P.wts32 = P.alloc<float>((size_t)LN * rec32);
         if (P.precision & 4) P.wtsdf = P.alloc<float>((size_t)LN * 6 * P.W2);
-        k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_coef, rec64, rec32, P.wts64,
-                                     P.wts32, P.wtsdf);
+        if (P.precision & 1) {
+            k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_coef, rec64, rec32, P.wts64,
+                                         P.wts32, P.wtsdf);
+        } else {
+            std::vector<float2> cdf(coef.size());
+            for (size_t e = 0; e < coef.size(); ++e) {
+                const float hi = (float)coef[e];
+                cdf[e] = make_float2(hi, (float)(coef[e] - (double)hi));
+            }
+            float2 *d_cdf = nullptr;
+            NLH_CUDA(cudaMallocAsync(&d_cdf, sizeof(float2) * cdf.size(), s));
+            tmp.push_back(d_cdf);
+            NLH_CUDA(cudaMemcpyAsync(d_cdf, cdf.data(), sizeof(float2) * cdf.size(),
+                                     cudaMemcpyHostToDevice, s));
+            k_weights_df<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_cdf, rec32, P.wts32,
+                                            P.wtsdf);
+        }
         NLH_CHECK_LAUNCH();
         NLH_CUDA(cudaStreamSynchronize(s));
         P.occupied = occ;
@@ -946,6 +1014,7 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info) {
         info->n_units = plan->n_units;
         info->max_items_pts = plan->kmax;
         info->unit_points = plan->unit_points;
+        for (int a = 0; a < 3; ++a) info->team[a] = plan->team[a];
         info->occupied_cells = plan->occupied;
         error_estimates(plan->sigma, plan->R, plan->fill, plan->M, &info->est_trunc_err,
                         &info->est_alias_err);
@@ -974,8 +1043,22 @@ nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, vo
     }
 }
 
+nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan, "nlh_plan_set_team: NULL plan");
+        NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 2,
+                    "nlh_plan_set_team: arith=%d shape=%d", arith, shape);
+        plan->team[arith] = shape;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
 nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_kmax,
-                             int *best_unit_points, double *best_ms, void *stream) {
+                             int *best_unit_points, int *best_team, double *best_ms,
+                             void *stream) {
     clear_error();
     try {
         NLH_REQUIRE(plan, "nlh_plan_autotune: NULL plan");
@@ -994,35 +1077,51 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
         NLH_CUDA(cudaEventCreate(&e1));
         const int kmaxes[] = {32, 64, 128, 256};
         const int unitpts[] = {256, 512, 1024, 2048};
+        const int nshapes = (P.W2 == 8 || P.W2 == 12) ? 3 : 1;
         double best = INFINITY;
         int bk = P.kmax, bu = P.unit_points;
+        int bt[3] = {P.team[0], P.team[1], P.team[2]};
         for (int km : kmaxes)
             for (int up : unitpts) {
                 retile(P, km, up, s);
                 double ms_total = 0.0;
+                int tt[3] = {P.team[0], P.team[1], P.team[2]};
                 for (int prec = 0; prec < 3; ++prec) {
                     if (!(mask & (prec == NLH_FP64 ? 1 : prec == NLH_FP32 ? 2 : 4))) continue;
-                    matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);  // warm
-                    NLH_CUDA(cudaEventRecord(e0, s));
-                    for (int k = 0; k < r; ++k) matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);
-                    NLH_CUDA(cudaEventRecord(e1, s));
-                    NLH_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    NLH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    ms_total += ms / r;
+                    double best_shape = INFINITY;
+                    for (int sh = 0; sh < nshapes; ++sh) {
+                        P.team[prec] = sh;
+                        matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);  // warm
+                        NLH_CUDA(cudaEventRecord(e0, s));
+                        for (int k = 0; k < r; ++k)
+                            matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);
+                        NLH_CUDA(cudaEventRecord(e1, s));
+                        NLH_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        NLH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        if (ms / r < best_shape) {
+                            best_shape = ms / r;
+                            tt[prec] = sh;
+                        }
+                    }
+                    ms_total += best_shape;
                 }
                 if (ms_total < best) {
                     best = ms_total;
                     bk = km;
                     bu = up;
+                    for (int a = 0; a < 3; ++a) bt[a] = tt[a];
                 }
             }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         retile(P, bk, bu, s);
+        for (int a = 0; a < 3; ++a) P.team[a] = bt[a];
         check_device_error(P, s);
         if (best_kmax) *best_kmax = bk;
         if (best_unit_points) *best_unit_points = bu;
+        if (best_team)
+            for (int a = 0; a < 3; ++a) best_team[a] = bt[a];
         if (best_ms) *best_ms = best;
         return NLH_OK;
     } catch (Failure &f) {

@@ -33,7 +33,7 @@ class PlanDesc(C.Structure):
                 ("windows", C.POINTER(C.c_int32)), ("sigma", C.c_double), ("M", C.c_int),
                 ("n_os", C.c_int), ("m", C.c_int), ("precision", C.c_int),
                 ("torus_fill", C.c_double), ("max_items_pts", C.c_int),
-                ("nfft_eps", C.c_double), ("unit_points", C.c_int)]
+                ("nfft_eps", C.c_double), ("unit_points", C.c_int), ("team", C.c_int * 3)]
 
 
 class PlanInfo(C.Structure):
@@ -43,7 +43,8 @@ class PlanInfo(C.Structure):
                 ("max_range", C.c_double), ("n_items", C.c_int64),
                 ("occupied_cells", C.c_int64), ("est_trunc_err", C.c_double),
                 ("est_alias_err", C.c_double), ("device_bytes", C.c_int64),
-                ("n_units", C.c_int64), ("max_items_pts", C.c_int), ("unit_points", C.c_int)]
+                ("n_units", C.c_int64), ("max_items_pts", C.c_int), ("unit_points", C.c_int),
+                ("team", C.c_int * 3)]
 
 
 class SolveOpts(C.Structure):
@@ -87,7 +88,9 @@ SIGNATURES = {
                                     C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
     "nlh_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "nlh_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
-                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.c_void_p]),
+    "nlh_plan_set_team": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
@@ -198,7 +201,7 @@ class Plan:
     def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
                  precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
                  nfft_eps: float = 0.0, unit_points: int = 0, autotune: bool = False,
-                 stream=None):
+                 team=None, stream=None):
         lib = load()
         N, D = features.shape
         win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
@@ -209,11 +212,13 @@ class Plan:
             tuned = _at.lookup(n_os, m, win.shape[0], N)
             if tuned:
                 max_items_pts, unit_points = tuned["max_items_pts"], tuned["unit_points"]
+                team = tuned.get("team", team)
         desc = PlanDesc(N=N, D=D, L=win.shape[0],
                         windows=win.ctypes.data_as(C.POINTER(C.c_int32)), sigma=float(sigma),
                         M=M, n_os=n_os, m=m, precision=precision,
                         torus_fill=float(torus_fill), max_items_pts=max_items_pts,
-                        nfft_eps=float(nfft_eps), unit_points=unit_points)
+                        nfft_eps=float(nfft_eps), unit_points=unit_points,
+                        team=(C.c_int * 3)(*(team or (0, 0, 0))))
         h = C.c_void_p()
         _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
                                    _stream_ptr(stream)))
@@ -237,7 +242,9 @@ class Plan:
     def info(self) -> dict:
         inf = PlanInfo()
         _check(load().nlh_plan_get_info(self._h, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in inf._fields_}
+        d = {k: getattr(inf, k) for k, _ in inf._fields_}
+        d["team"] = list(inf.team)
+        return d
 
     def retile(self, max_items_pts: int, unit_points: int, stream=None):
         _check(load().nlh_plan_retile(self._h, int(max_items_pts), int(unit_points),
@@ -245,9 +252,14 @@ class Plan:
 
     def autotune(self, precisions: int = 0, reps: int = 3, stream=None):
         k, u, ms = C.c_int(0), C.c_int(0), C.c_double(0)
-        _check(load().nlh_plan_autotune(self._h, precisions, reps, C.byref(k), C.byref(u),
+        t = (C.c_int * 3)()
+        _check(load().nlh_plan_autotune(self._h, precisions, reps, C.byref(k), C.byref(u), t,
                                         C.byref(ms), _stream_ptr(stream)))
-        return {"max_items_pts": k.value, "unit_points": u.value, "ms": ms.value}
+        return {"max_items_pts": k.value, "unit_points": u.value, "team": list(t),
+                "ms": ms.value}
+
+    def set_team(self, arith: int, shape: int):
+        _check(load().nlh_plan_set_team(self._h, int(arith), int(shape)))
 
     def degrees(self, out=None, stream=None):
         """d = Gamma_full 1 in pixel order (nlh_plan_get_degrees)."""

@@ -84,7 +84,25 @@ def test_retile_and_autotune_keep_results(tmp_path, monkeypatch):
         assert inf["max_items_pts"] == k and inf["unit_points"] == u
         assert relmax(host(P.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
         assert relmax(host(P.matvec(v, precision=nlh.NLH_FP32)), y0f) < 1e-5
+    # launch shapes of the spread / interpolation kernels: same results
+    y64 = host(P.matvec(v, precision=nlh.NLH_FP64))
+    for arith, yref, tol in ((nlh.NLH_DF32, y0, 1e-12), (nlh.NLH_FP32, y0f, 1e-5),
+                             (nlh.NLH_FP64, y64, 1e-12)):
+        for sh in (1, 2, 0):
+            P.set_team(arith, sh)
+            assert P.info()["team"][arith] == sh
+            assert relmax(host(P.matvec(v, precision=arith)), yref) < tol, (arith, sh)
+    Q12 = make_plan(img, m=6, precision=6)          # 2m = 12 has its own shapes
+    z0 = host(Q12.matvec(v, precision=nlh.NLH_DF32))
+    for sh in (1, 2):
+        Q12.set_team(nlh.NLH_DF32, sh)
+        Q12.set_team(nlh.NLH_FP32, sh)
+        assert relmax(host(Q12.matvec(v, precision=nlh.NLH_DF32)), z0) < 1e-12
+        assert relmax(host(Q12.matvec(v, precision=nlh.NLH_FP32)), z0) < 1e-5
+    with pytest.raises(nlh.NLHError):
+        P.set_team(nlh.NLH_FP32, 3)
     res = P.autotune(reps=1)
+    assert all(t in (0, 1, 2) for t in res["team"]) and P.info()["team"] == res["team"]
     assert res["max_items_pts"] in (32, 64, 128, 256)
     assert res["unit_points"] in (256, 512, 1024, 2048) and res["ms"] > 0
     assert relmax(host(P.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
@@ -94,4 +112,5 @@ def test_retile_and_autotune_keep_results(tmp_path, monkeypatch):
     R = nlh.Plan.from_image(cuda(img), 1, raster_windows(1), 0.2, precision=7, autotune=True)
     assert R.info()["max_items_pts"] == first["max_items_pts"]
     assert R.info()["unit_points"] == first["unit_points"]
+    assert R.info()["team"] == first["team"]
     assert relmax(host(R.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12

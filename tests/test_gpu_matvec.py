@@ -207,3 +207,24 @@ def test_argument_errors():
         make_plan(img, n_os=48)                    # not a power of two
     with pytest.raises(nlh.NLHError):
         make_plan(img, M=5)
+
+
+def test_double_float_weights_without_fp64_path(img64):
+    """Plans without the FP64 path evaluate the window polynomials in
+    double-float arithmetic; their double-float operator agrees with the one
+    built from FP64-evaluated weights (a plan with both paths) to the
+    double-float rounding, and the FP32 operator to FP32 rounding."""
+    img, coords = img64
+    P5 = make_plan(img, precision=5)   # FP64 + double-float: FP64 Horner
+    P6 = make_plan(img, precision=6)   # FP32 + double-float: double-float Horner
+    v = random_vector(img.size, 23)
+    y5 = host(P5.matvec(cuda(v), op=2, alpha=0.5, precision=nlh.NLH_DF32))
+    y6 = host(P6.matvec(cuda(v), op=2, alpha=0.5, precision=nlh.NLH_DF32))
+    assert relmax(y6, y5) < 1e-11, relmax(y6, y5)
+    y32 = host(P6.matvec(cuda(v), op=2, alpha=0.5, precision=nlh.NLH_FP32))
+    assert relmax(y32, y5) < 1e-5
+    one = cuda(np.ones(img.size))
+    d = host(P6.matvec(one, op=0, precision=nlh.NLH_DF32))
+    L1 = host(P6.matvec(one, op=1, precision=nlh.NLH_FP32))
+    assert np.max(np.abs(L1)) < 1e-5 * np.max(d)
+    assert relmax(host(P6.degrees()), host(P5.degrees())) < 1e-12
