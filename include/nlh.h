@@ -86,8 +86,10 @@ typedef struct {
     int team[3];            /* launch shape of the spread / interpolation
                                kernels per NFFT arithmetic (index NLH_FP64,
                                NLH_FP32, NLH_DF32): 0 default, 1 and 2 the
-                               alternatives compiled for 2m = 8 and 12 (other
-                               widths use 0); results equal up to rounding */
+                               alternatives compiled for 2m = 8 and 12, 3 the
+                               tensor-core FP32 kernels (3xTF32 mma) for
+                               2m = 8; other combinations use 0.  Results
+                               equal up to the arithmetic's rounding        */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
@@ -129,7 +131,7 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
  * Synchronises `stream`. */
 nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream);
 
-/* Set the launch shape (0, 1, 2; see nlh_plan_desc.team) of the spread and
+/* Set the launch shape (0..3; see nlh_plan_desc.team) of the spread and
  * interpolation kernels of one NFFT arithmetic (NLH_FP64, NLH_FP32,
  * NLH_DF32).  Changes no result beyond rounding. */
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);

@@ -113,7 +113,8 @@ struct Plan {
     int32_t *perm = nullptr;
     int4 *items = nullptr;
     int4 *units = nullptr;
-    int64_t n_units = 0;
+    int64_t n_units = 0;          // host copy of the unit count (-1: on the device only)
+    int64_t units_cap = 0;        // capacity of `units` (an upper bound of the count)
     double *wts64 = nullptr;
     float *wts32 = nullptr;
     float *wtsdf = nullptr;       // double-float records: per dim 2m high then 2m low parts
@@ -135,10 +136,12 @@ struct Plan {
     SolveState *st = nullptr;     // device
     int *err = nullptr;           // device error word (bounded waits that gave up)
     int *unit_ctr = nullptr;      // device [2]: next unit of spread / interpolation
+    int *d_units = nullptr;       // device [1]: the unit count
     SolveState *st_host = nullptr; // pinned mirror
     double *red_host = nullptr;   // pinned, 3 * kRedBlocks residual partials
     std::map<int, cudaGraphExec_t> graphs;  // solve graphs (see solve.cu)
     cudaStream_t capture_stream = nullptr;
+    int device = 0;               // the device the plan was built on
     double *hist = nullptr;       // device, kMaxHist
     std::vector<void *> allocs;
     int64_t bytes = 0;
@@ -216,6 +219,7 @@ void retain_pool_memory();
 // Throws Failure{NLH_ERR_TIMEOUT} if a kernel recorded a bounded wait that
 // gave up (synchronises s).
 void check_device_error(Plan &P, cudaStream_t s);
+cudaStream_t take_capture_stream(int device);
 void plan_degrees(Plan &P, cudaStream_t s);
 // alpha_dev (optional): read alpha from device memory instead of `alpha`.
 void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,

@@ -105,7 +105,9 @@ struct UnitSmem {
     static constexpr int E = kTile + W2 - 1, E3 = E * E * E, PWP = padded_record<T, W2>();
     static constexpr size_t tile = align16(sizeof(T) * E3);
     static constexpr size_t stage = align16(sizeof(typename Num<T>::R) * kChunk * PWP);
-    static constexpr size_t team = 2 * stage + 2 * sizeof(uint64_t) + 16 + align16(sizeof(T) * kChunk);
+    // per team: two staging buffers, two mbarriers, a status word and a slot,
+    // and the per-warp point totals of a chunk (up to 4 warps per team)
+    static constexpr size_t team = 2 * stage + 2 * sizeof(uint64_t) + 16 + align16(sizeof(T) * kChunk * 4);
 };
 
 __device__ __forceinline__ void tile_origin(int tile, int n, int &tx0, int &ty0, int &tz0) {
@@ -387,7 +389,8 @@ struct UnitLayout {
 // input vector in sorted order.
 template <typename T, int W2, int NW, int TPB>
 __global__ void __launch_bounds__(32 * NW * TPB, 1)
-k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
+k_spread(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
+         int *__restrict__ unit_ctr,
          const int4 *__restrict__ items, const typename Num<T>::R *__restrict__ wts,
          const T *__restrict__ xs, typename Num<T>::G *__restrict__ grid, int n, int m,
          const int *__restrict__ done, int *__restrict__ err) {
@@ -420,7 +423,7 @@ k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
         if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
         __syncthreads();
         const int uidx = s_ctl[1];
-        if (uidx >= n_units || s_ctl[2]) break;
+        if (uidx >= *n_units_dev || s_ctl[2]) break;
         const int4 un = units[uidx];
         const int l = un.x, it0 = un.z, nit = un.w;
         int tx0, ty0, tz0;
@@ -512,7 +515,8 @@ k_spread(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
 // the warp so that lane j ends with point j's value.
 template <typename T, int W2, int NW, int TPB>
 __global__ void __launch_bounds__(32 * NW * TPB, 1)
-k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr,
+k_interp(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
+         int *__restrict__ unit_ctr,
          const int4 *__restrict__ items, const int *__restrict__ perm,
          const typename Num<T>::R *__restrict__ wts, const typename Num<T>::G *__restrict__ grid,
          double *__restrict__ Y, int n, int m, int64_t N, const int *__restrict__ done,
@@ -547,7 +551,7 @@ k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
         if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
         __syncthreads();
         const int uidx = s_ctl[1];
-        if (uidx >= n_units || s_ctl[2]) break;
+        if (uidx >= *n_units_dev || s_ctl[2]) break;
         const int4 un = units[uidx];
         const int l = un.x, it0 = un.z, nit = un.w;
         int tx0, ty0, tz0;
@@ -653,21 +657,329 @@ k_interp(const int4 *__restrict__ units, int n_units, int *__restrict__ unit_ctr
                 tot = tot + __shfl_xor_sync(0xffffffffu, tot, 8);
                 tot = tot + __shfl_xor_sync(0xffffffffu, tot, 16);
                 if (NW > 1) {
-                    if (warp == 0 && lane < 8) sred[lane] = tot;
-                    team_sync<NW>(team);
-#pragma unroll
-                    for (int w = 1; w < NW; ++w) {
-                        if (warp == w && lane < 8) sred[lane] += tot;
-                        team_sync<NW>(team);
-                    }
-                    tot = sred[lane & 7];
-                    team_sync<NW>(team);
+                    // each warp's totals of the chunk's points; summed once per chunk
+                    if (lane < 8) sred[warp * kChunk + g0 + lane] = tot;
+                } else {
+                    const int pidx = __shfl_sync(0xffffffffu, pcur, (g0 + lane) & 31);
+                    if (lane < 8 && g0 + lane < cn) Y[(int64_t)l * N + pidx] = (double)tot;
                 }
-                const int pidx = __shfl_sync(0xffffffffu, pcur, (g0 + lane) & 31);
-                if (warp == 0 && lane < 8 && g0 + lane < cn)
-                    Y[(int64_t)l * N + pidx] = (double)tot;
+            }
+            if (NW > 1) {
+                team_sync<NW>(team);
+                if (warp == 0 && lane < cn) {  // lane j holds point j's permutation entry
+                    T tot = sred[lane];
+#pragma unroll
+                    for (int w = 1; w < NW; ++w) tot = tot + sred[w * kChunk + lane];
+                    Y[(int64_t)l * N + pcur] = (double)tot;
+                }
             }
             team_sync<NW>(team);  // every read of buffer bsel (and sred) is done
+            cur = nxt;
+            pcur = pnxt;
+            bsel ^= 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core FP32 path
+// For 2m = 8 the FP32 stencil work of one item (one grid cell, P points) is a
+// dense contraction over a 64 x 8 block of the grid (rows (z, y), columns x):
+//   spread:  G[(z,y), x] += sum_p (v_p wz_p[z] wy_p[y]) wx_p[x]   (A: 64 x P, B: P x 8)
+//   interp:  C[(z,y), p]  = sum_x G[(z,y), x] wx_p[x],  y_p = sum wz wy C   (A: 64 x 8)
+// These kernels run it on the tensor cores with mma.sync m16n8k8 TF32 and
+// the 3xTF32 split (a = a_hi + a_lo, products hi*hi + hi*lo + lo*hi), which
+// keeps FP32 accuracy (~2^-22 relative per product, FP32 accumulation).
+// Rows are ordered so that m16 tile i holds z = 2i (rows 0-7) and z = 2i+1
+// (rows 8-15) with y = row % 8; a thread (group g = lane / 4) then owns
+// y = g and every z of its columns.
+__device__ __forceinline__ uint32_t tf32_hi(float a) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+    return r;
+}
+// a = hi + lo: hi keeps the top 10 mantissa bits (exact in TF32; a - hi is
+// then exact in FP32), lo is that remainder rounded to TF32.
+__device__ __forceinline__ void tf32_split(float a, uint32_t &hi, uint32_t &lo) {
+    hi = __float_as_uint(a) & 0xFFFFE000u;
+    lo = tf32_hi(a - __uint_as_float(hi));
+}
+// D += A B (m16n8k8, tf32 inputs, f32 accumulators)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// 3xTF32: D += Ahi Bhi + Ahi Blo + Alo Bhi
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4],
+                                           const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
+                                           uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+template <int TPB, int MINB>
+__global__ void __launch_bounds__(32 * TPB, MINB)
+k_spread_tc(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
+            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
+            const float *__restrict__ wts, const float *__restrict__ xs, float *__restrict__ grid,
+            int n, int m, const int *__restrict__ done, int *__restrict__ err) {
+    constexpr int W2 = 8, NW = 1;
+    using SM = UnitSmem<float, W2, TPB>;
+    using LY = UnitLayout<float, W2, TPB>;
+    constexpr int PWP = SM::PWP, E = SM::E, E3 = SM::E3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *S = reinterpret_cast<float *>(smem_raw);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
+    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
+    if (done && *done) return;
+    const int team = threadIdx.x / 32, lane = threadIdx.x % 32, tid = lane;
+    const int g = lane >> 2, t = lane & 3;
+    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
+    auto st = make_stager<float, W2, NW, TPB>(team_base, team, tid);
+    int *s_slot = const_cast<int *>(st.flag) + 1;
+    if (tid == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        mbar_fence_init();
+    }
+    if (threadIdx.x == 0) s_ctl[2] = 0;
+    const int msk = n - 1;
+    while (true) {
+        __syncthreads();  // previous unit fully flushed
+        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
+        __syncthreads();
+        const int uidx = s_ctl[1];
+        if (uidx >= *n_units_dev || s_ctl[2]) break;
+        const int4 un = units[uidx];
+        const int l = un.x, it0 = un.z, nit = un.w;
+        int tx0, ty0, tz0;
+        tile_origin(un.y, n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = 0.f;
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        if (threadIdx.x == 0) s_ctl[0] = TPB;
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][e] = 0.f;
+        ChunkCursor cur = make_cursor(s_items, team, nit);
+        float vcur = 0.f;
+        if (cur.valid()) {
+            st.issue(0, wts, cur);
+            if (lane < cur.cnt) vcur = xs[cur.start + lane];
+        }
+        int bsel = 0;
+        while (cur.valid()) {
+            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
+            float vnxt = 0.f;
+            if (nxt.valid()) {
+                st.issue(bsel ^ 1, wts, nxt);
+                if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
+            }
+            if (!st.wait(bsel, err)) {
+                st.drain(err);
+                s_ctl[2] = 1;
+                break;
+            }
+            const float *sw = st.buf(bsel);
+            const int cn = min(kChunk, cur.cnt - cur.c0);
+            for (int g0 = 0; g0 < cn; g0 += 8) {
+                // columns t and t + 4 of this 8-point group
+                const int p0 = g0 + t, p1 = g0 + t + 4;
+                const float v0 = __shfl_sync(0xffffffffu, vcur, p0);
+                const float v1 = __shfl_sync(0xffffffffu, vcur, p1 & 31);
+                const bool ok0 = p0 < cn, ok1 = p1 < cn;
+                const float *w0 = sw + p0 * PWP, *w1 = sw + (ok1 ? p1 : p0) * PWP;
+                const float s0 = ok0 ? v0 * w0[W2 + g] : 0.f;
+                const float s1 = ok1 ? v1 * w1[W2 + g] : 0.f;
+                // columns of points past the chunk are zero (the staging buffer
+                // beyond cn holds stale records)
+                const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 z0a = ok0 ? *reinterpret_cast<const float4 *>(w0 + 2 * W2) : zero4;
+                const float4 z0b = ok0 ? *reinterpret_cast<const float4 *>(w0 + 2 * W2 + 4) : zero4;
+                const float4 z1a = ok1 ? *reinterpret_cast<const float4 *>(w1 + 2 * W2) : zero4;
+                const float4 z1b = ok1 ? *reinterpret_cast<const float4 *>(w1 + 2 * W2 + 4) : zero4;
+                const float wz0[8] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+                const float wz1[8] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
+                // B: k = point (t, t + 4), n = x = g
+                uint32_t bh0, bl0, bh1, bl1;
+                tf32_split(ok0 ? w0[g] : 0.f, bh0, bl0);
+                tf32_split(ok1 ? w1[g] : 0.f, bh1, bl1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    uint32_t ah[4], al[4];
+                    tf32_split(s0 * wz0[2 * i], ah[0], al[0]);
+                    tf32_split(s0 * wz0[2 * i + 1], ah[1], al[1]);
+                    tf32_split(s1 * wz1[2 * i], ah[2], al[2]);
+                    tf32_split(s1 * wz1[2 * i + 1], ah[3], al[3]);
+                    mma_3xtf32(acc[i], ah, al, bh0, bh1, bl0, bl1);
+                }
+            }
+            if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
+                int lx0, ly0, lz0;
+                item_local(cur.local, lx0, ly0, lz0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float *row = S + ((lz0 + 2 * i + h) * E + (ly0 + g)) * E + lx0 + 2 * t;
+                        atomicAdd(&row[0], acc[i][2 * h]);
+                        atomicAdd(&row[1], acc[i][2 * h + 1]);
+                        acc[i][2 * h] = acc[i][2 * h + 1] = 0.f;
+                    }
+                }
+            }
+            __syncwarp();  // every read of buffer bsel is done before it is refilled
+            cur = nxt;
+            vcur = vnxt;
+            bsel ^= 1;
+        }
+        __syncthreads();
+        float *gl = grid + (int64_t)l * n * n * n;
+        for (int e = threadIdx.x; e < E3; e += blockDim.x) {
+            const float val = S[e];
+            if (val != 0.f) {
+                int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+                int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                    gz = (tz0 - m + 1 + ez) & msk;
+                atomicAdd(&gl[((int64_t)gz * n + gy) * n + gx], val);
+            }
+        }
+    }
+}
+
+template <int TPB, int MINB>
+__global__ void __launch_bounds__(32 * TPB, MINB)
+k_interp_tc(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
+            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
+            const int *__restrict__ perm, const float *__restrict__ wts,
+            const float *__restrict__ grid, double *__restrict__ Y, int n, int m, int64_t N,
+            const int *__restrict__ done, int *__restrict__ err) {
+    constexpr int W2 = 8, NW = 1;
+    using SM = UnitSmem<float, W2, TPB>;
+    using LY = UnitLayout<float, W2, TPB>;
+    constexpr int PWP = SM::PWP, E = SM::E, E3 = SM::E3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *S = reinterpret_cast<float *>(smem_raw);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
+    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
+    if (done && *done) return;
+    const int team = threadIdx.x / 32, lane = threadIdx.x % 32, tid = lane;
+    const int g = lane >> 2, t = lane & 3;
+    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
+    auto st = make_stager<float, W2, NW, TPB>(team_base, team, tid);
+    int *s_slot = const_cast<int *>(st.flag) + 1;
+    if (tid == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        mbar_fence_init();
+    }
+    if (threadIdx.x == 0) s_ctl[2] = 0;
+    const int msk = n - 1;
+    while (true) {
+        __syncthreads();  // previous unit done with the tile
+        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
+        __syncthreads();
+        const int uidx = s_ctl[1];
+        if (uidx >= *n_units_dev || s_ctl[2]) break;
+        const int4 un = units[uidx];
+        const int l = un.x, it0 = un.z, nit = un.w;
+        int tx0, ty0, tz0;
+        tile_origin(un.y, n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        if (threadIdx.x == 0) s_ctl[0] = TPB;
+        const float *gl = grid + (int64_t)l * n * n * n;
+        for (int e = threadIdx.x; e < E3; e += blockDim.x) {
+            int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+            int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                gz = (tz0 - m + 1 + ez) & msk;
+            S[e] = __ldg(&gl[((int64_t)gz * n + gy) * n + gx]);
+        }
+        __syncthreads();
+        ChunkCursor cur = make_cursor(s_items, team, nit);
+        if (cur.valid()) st.issue(0, wts, cur);
+        int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
+        uint32_t ah[4][4], al[4][4];  // the item's stencil, A = G[(z, y), x]
+        int bsel = 0;
+        while (cur.valid()) {
+            if (cur.c0 == 0) {
+                int lx0, ly0, lz0;
+                item_local(cur.local, lx0, ly0, lz0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float *r0 = S + ((lz0 + 2 * i) * E + (ly0 + g)) * E + lx0;
+                    const float *r1 = S + ((lz0 + 2 * i + 1) * E + (ly0 + g)) * E + lx0;
+                    tf32_split(r0[t], ah[i][0], al[i][0]);
+                    tf32_split(r1[t], ah[i][1], al[i][1]);
+                    tf32_split(r0[t + 4], ah[i][2], al[i][2]);
+                    tf32_split(r1[t + 4], ah[i][3], al[i][3]);
+                }
+            }
+            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
+            int pnxt = 0;
+            if (nxt.valid()) {
+                st.issue(bsel ^ 1, wts, nxt);
+                if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
+            }
+            if (!st.wait(bsel, err)) {
+                st.drain(err);
+                s_ctl[2] = 1;
+                break;
+            }
+            const float *sw = st.buf(bsel);
+            const int cn = min(kChunk, cur.cnt - cur.c0);
+            for (int g0 = 0; g0 < cn; g0 += 8) {
+                // B: k = x (t, t + 4), n = point g0 + g
+                const int pb = g0 + g;
+                const float *wb = sw + (pb < cn ? pb : g0) * PWP;
+                uint32_t bh0, bl0, bh1, bl1;
+                tf32_split(pb < cn ? wb[t] : 0.f, bh0, bl0);
+                tf32_split(pb < cn ? wb[t + 4] : 0.f, bh1, bl1);
+                float c[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    c[i][0] = c[i][1] = c[i][2] = c[i][3] = 0.f;
+                    mma_3xtf32(c[i], ah[i], al[i], bh0, bh1, bl0, bl1);
+                }
+                // this thread: y = g, z = 0..7, points q0 = g0 + 2t, q1 = q0 + 1
+                const int q0 = g0 + 2 * t, q1 = q0 + 1;
+                const float *w0 = sw + (q0 < cn ? q0 : g0) * PWP;
+                const float *w1 = sw + (q1 < cn ? q1 : g0) * PWP;
+                const float4 z0a = *reinterpret_cast<const float4 *>(w0 + 2 * W2);
+                const float4 z0b = *reinterpret_cast<const float4 *>(w0 + 2 * W2 + 4);
+                const float4 z1a = *reinterpret_cast<const float4 *>(w1 + 2 * W2);
+                const float4 z1b = *reinterpret_cast<const float4 *>(w1 + 2 * W2 + 4);
+                const float wz0[8] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+                const float wz1[8] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    s0 = fmaf(wz0[2 * i], c[i][0], s0);
+                    s0 = fmaf(wz0[2 * i + 1], c[i][2], s0);
+                    s1 = fmaf(wz1[2 * i], c[i][1], s1);
+                    s1 = fmaf(wz1[2 * i + 1], c[i][3], s1);
+                }
+                s0 *= w0[W2 + g];
+                s1 *= w1[W2 + g];
+                // sum over y = g: lanes 4 g + t with the same t
+#pragma unroll
+                for (int o = 4; o <= 16; o <<= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                }
+                const int pi0 = __shfl_sync(0xffffffffu, pcur, q0 & 31);
+                const int pi1 = __shfl_sync(0xffffffffu, pcur, q1 & 31);
+                if (g == 0) {
+                    if (q0 < cn) Y[(int64_t)l * N + pi0] = (double)s0;
+                    if (q1 < cn) Y[(int64_t)l * N + pi1] = (double)s1;
+                }
+            }
+            __syncwarp();  // every read of buffer bsel is done before it is refilled
             cur = nxt;
             pcur = pnxt;
             bsel ^= 1;
@@ -864,7 +1176,7 @@ static void launch_spread_interp_shape(Plan &P, bool spread, const typename Num<
                                  cudaStream_t s) {
     constexpr int NTH = 32 * NW * TPB;
     constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
-    if (P.n_units == 0) return;
+    if (P.units_cap == 0) return;
     static int blocks_spread = 0, blocks_interp = 0;  // per template instance
     if (blocks_spread == 0) {
         NLH_CUDA(cudaFuncSetAttribute(k_spread<T, W2, NW, TPB>,
@@ -882,16 +1194,58 @@ static void launch_spread_interp_shape(Plan &P, bool spread, const typename Num<
         blocks_spread = sms * std::max(1, a);
     }
     ProfRange pr(spread ? spread_class<T>() : interp_class<T>(), s);
-    const int nu = (int)P.n_units;
+    // grid bound: the unit count once known on the host, else its upper bound
+    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
+    if (nu == 0) return;
     if (spread) {
         const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
-        k_spread<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, nu, P.unit_ctr, P.items, wts, xs,
+        k_spread<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr, P.items, wts, xs,
                                                       grid, P.n, P.m, done, P.err);
     } else {
         const unsigned g = (unsigned)std::min<int64_t>(blocks_interp, nu);
-        k_interp<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, nu, P.unit_ctr + 1, P.items,
+        k_interp<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
                                                       P.perm, wts, grid, P.Y, P.n, P.m, P.N, done,
                                                       P.err);
+    }
+    NLH_CHECK_LAUNCH();
+}
+
+// The tensor-core FP32 kernels (2m = 8, one-warp teams, 4 teams per CTA,
+// registers capped for MINB resident CTAs per SM).
+template <int MINB>
+static void launch_spread_interp_tc(Plan &P, bool spread, const float *wts, float *grid,
+                                    const float *xs, const int *done, cudaStream_t s) {
+    constexpr int TPB = 4, NTH = 32 * TPB;
+    constexpr size_t smem = UnitLayout<float, 8, TPB>::bytes;
+    if (P.units_cap == 0) return;
+    static int blocks_spread = 0, blocks_interp = 0;
+    if (blocks_spread == 0) {
+        NLH_CUDA(cudaFuncSetAttribute(k_spread_tc<TPB, MINB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NLH_CUDA(cudaFuncSetAttribute(k_interp_tc<TPB, MINB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, a = 0, b = 0;
+        NLH_CUDA(cudaGetDevice(&dev));
+        NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spread_tc<TPB, MINB>, NTH,
+                                                               smem));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_tc<TPB, MINB>, NTH,
+                                                               smem));
+        blocks_interp = sms * std::max(1, b);
+        blocks_spread = sms * std::max(1, a);
+    }
+    ProfRange pr(spread ? NLH_K_SPREAD32 : NLH_K_INTERP32, s);
+    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
+    if (nu == 0) return;
+    if (spread) {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
+        k_spread_tc<TPB, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr, P.items, wts,
+                                                    xs, grid, P.n, P.m, done, P.err);
+    } else {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks_interp, nu);
+        k_interp_tc<TPB, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
+                                                    P.perm, wts, grid, P.Y, P.n, P.m, P.N, done,
+                                                    P.err);
     }
     NLH_CHECK_LAUNCH();
 }
@@ -905,13 +1259,17 @@ template <typename T> constexpr int arith_index() {
 // Team shape (warps per team NW, teams per CTA TPB) of the spread and
 // interpolation kernels: fewer accumulator lines per thread (larger teams)
 // against more independent teams per SM.  Shape 0 is the default; shapes 1
-// and 2 are compiled for the stencil widths of the workloads (2m = 8, 12)
-// and picked per arithmetic by the autotuner (plan.team[]).
+// and 2 are compiled for the stencil widths of the workloads (2m = 8, 12);
+// shape 3 is the tensor-core FP32 path for 2m = 8.  The autotuner picks one
+// per arithmetic (plan.team[]); other combinations fall back to shape 0.
 template <typename T, int W2>
 static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
                                  typename Num<T>::G *grid, const T *xs, const int *done,
                                  cudaStream_t s) {
     const int shape = P.team[arith_index<T>()];
+    if constexpr (W2 == 8 && std::is_same<T, float>::value) {
+        if (shape == 3) return launch_spread_interp_tc<5>(P, spread, wts, grid, xs, done, s);
+    }
     if constexpr (W2 == 8) {
         if (shape == 1) return launch_spread_interp_shape<T, W2, 2, 2>(P, spread, wts, grid, xs, done, s);
         if (shape == 2) return launch_spread_interp_shape<T, W2, 2, 4>(P, spread, wts, grid, xs, done, s);

@@ -28,16 +28,58 @@ void set_error(const char *fmt, ...) {
 }
 void clear_error() { g_err.clear(); }
 
+// Pinned host mirrors and capture streams cost a driver round trip (page
+// pinning, stream creation) that a plan made per image would pay every
+// time; plans take them from process-wide free lists and return them.
+namespace {
+struct HostPool {
+    std::mutex mu;
+    std::vector<SolveState *> st;
+    std::vector<double *> red;
+    std::map<int, std::vector<cudaStream_t>> streams;  // per device
+};
+HostPool &host_pool() {
+    static HostPool *p = new HostPool();  // kept to process exit
+    return *p;
+}
+}  // namespace
+
+void take_pinned(Plan &P) {
+    HostPool &hp = host_pool();
+    {
+        std::lock_guard<std::mutex> lk(hp.mu);
+        if (!hp.st.empty()) { P.st_host = hp.st.back(); hp.st.pop_back(); }
+        if (!hp.red.empty()) { P.red_host = hp.red.back(); hp.red.pop_back(); }
+    }
+    if (!P.st_host) NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
+    if (!P.red_host) NLH_CUDA(cudaMallocHost(&P.red_host, sizeof(double) * 3 * kRedBlocks));
+}
+
+cudaStream_t take_capture_stream(int device) {
+    HostPool &hp = host_pool();
+    {
+        std::lock_guard<std::mutex> lk(hp.mu);
+        auto &v = hp.streams[device];
+        if (!v.empty()) {
+            cudaStream_t s = v.back();
+            v.pop_back();
+            return s;
+        }
+    }
+    cudaStream_t s = nullptr;
+    NLH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    return s;
+}
+
 Plan::~Plan() {
     cudaStreamSynchronize(stream);
     for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
     for (void *ptr : allocs) cudaFreeAsync(ptr, stream);
-    if (st_host || red_host) {
-        cudaStreamSynchronize(stream);
-        if (st_host) cudaFreeHost(st_host);
-        if (red_host) cudaFreeHost(red_host);
-    }
-    if (capture_stream) cudaStreamDestroy(capture_stream);
+    HostPool &hp = host_pool();
+    std::lock_guard<std::mutex> lk(hp.mu);
+    if (st_host) hp.st.push_back(st_host);
+    if (red_host) hp.red.push_back(red_host);
+    if (capture_stream) hp.streams[device].push_back(capture_stream);
 }
 
 void retain_pool_memory() {
@@ -268,6 +310,18 @@ __global__ void k_scan_apply(const int *__restrict__ in, int64_t n, const int *_
         if (base + j < n) out[base + j] = run;
         run += vals[j];
     }
+}
+
+// out = exclusive scan of in, the total to d_total, no synchronisation.
+static void exclusive_scan_dev(const int *in, int *out, int64_t n, cudaStream_t s,
+                               int *tmp_sums, int *d_total) {
+    int nt = div_up(n, kScanTile);
+    k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, n, tmp_sums);
+    NLH_CHECK_LAUNCH();
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp_sums, nt, d_total);
+    NLH_CHECK_LAUNCH();
+    k_scan_apply<<<nt, kScanThreads, 0, s>>>(in, n, tmp_sums, out);
+    NLH_CHECK_LAUNCH();
 }
 
 // out = exclusive scan of in; returns the total (synchronises s).
@@ -535,43 +589,142 @@ __global__ void k_fill(double *__restrict__ x, int64_t n, double v) {
 }
 
 // Work units: consecutive items (tile-major order) of one window and one
-// tile, cut when the running point count would exceed kUnitPoints or the
+// tile, cut when the running point count would exceed unit_points or the
 // item count kUnitItems.  Units are then ordered by decreasing point count
-// so that the largest start first.  Built on the host from the item list
-// (a plan-time pass over n_items records).
-static void build_units(Plan &P, cudaStream_t s) {
-    std::vector<int4> items(P.n_items);
-    if (P.n_items)
-        NLH_CUDA(cudaMemcpyAsync(items.data(), P.items, sizeof(int4) * P.n_items,
-                                 cudaMemcpyDeviceToHost, s));
-    NLH_CUDA(cudaStreamSynchronize(s));
-    std::vector<std::pair<int, int4>> units;
-    int64_t i = 0;
-    while (i < P.n_items) {
-        const int l = items[i].x >> 16, tile = items[i].y;
-        int64_t j = i;
-        int pts = 0;
-        while (j < P.n_items && (items[j].x >> 16) == l && items[j].y == tile &&
-               j - i < kUnitItems && (j == i || pts + items[j].w <= P.unit_points)) {
-            pts += items[j].w;
-            ++j;
+// so that the largest start first (a counting sort on the size; the order
+// among units of one size is not fixed).  Built on the device, without a
+// host round trip: one thread walks each (window, tile) group of items; the
+// unit count stays in device memory (P.d_units[0]) for the persistent
+// kernels and reaches the host at the plan's next synchronisation.
+constexpr int kSizeBins = 4096;
+
+__device__ __forceinline__ bool same_group(const int4 &a, const int4 &b) {
+    return (a.x >> 16) == (b.x >> 16) && a.y == b.y;
+}
+
+// Count pass (uoff == nullptr): ucnt[i] = units of the group starting at
+// item i (0 elsewhere).  Emit pass: write them at uoff[i] and their sizes.
+__global__ void k_unit_walk(const int4 *__restrict__ items, int64_t n_items, int unit_points,
+                            const int *__restrict__ uoff, int *__restrict__ ucnt,
+                            int4 *__restrict__ units, int *__restrict__ sizes) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int4 first = items[i];
+        if (i > 0 && same_group(items[i - 1], first)) {
+            if (!uoff) ucnt[i] = 0;
+            continue;
         }
-        units.push_back({pts, make_int4(l, tile, (int)i, (int)(j - i))});
-        i = j;
+        int nu = 0;
+        int64_t j = i;
+        while (j < n_items && same_group(items[j], first)) {
+            const int64_t j0 = j;
+            int pts = 0;
+            while (j < n_items && same_group(items[j], first) && j - j0 < kUnitItems &&
+                   (j == j0 || pts + items[j].w <= unit_points)) {
+                pts += items[j].w;
+                ++j;
+            }
+            if (uoff) {
+                const int o = uoff[i] + nu;
+                units[o] = make_int4(first.x >> 16, first.y, (int)j0, (int)(j - j0));
+                sizes[o] = pts;
+            }
+            ++nu;
+        }
+        if (!uoff) ucnt[i] = nu;
     }
-    std::stable_sort(units.begin(), units.end(),
-                     [](const std::pair<int, int4> &a, const std::pair<int, int4> &b) {
-                         return a.first > b.first;
-                     });
-    std::vector<int4> u(units.size());
-    for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
-    P.n_units = (int64_t)u.size();
+}
+
+__global__ void k_size_hist(const int *__restrict__ sizes, const int *__restrict__ n_units,
+                            int *__restrict__ hist) {
+    const int n = *n_units;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&hist[min(sizes[i], kSizeBins - 1)], 1);
+}
+
+// off[b] = number of units in bins above b (descending order of size).
+__global__ void k_size_offsets(const int *__restrict__ hist, int *__restrict__ off) {
+    __shared__ int sh[32];
+    __shared__ int carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < kSizeBins; base += blockDim.x) {
+        const int b = kSizeBins - 1 - (base + (int)threadIdx.x);  // descending
+        const int v = hist[b];
+        const int inc = block_incl_scan(v, sh);
+        off[b] = carry_s + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_s += inc;
+        __syncthreads();
+    }
+}
+
+__global__ void k_size_scatter(const int4 *__restrict__ in, const int *__restrict__ sizes,
+                               const int *__restrict__ n_units, int *__restrict__ off,
+                               int4 *__restrict__ out) {
+    const int n = *n_units;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[atomicAdd(&off[min(sizes[i], kSizeBins - 1)], 1)] = in[i];
+}
+
+static void exclusive_scan_dev(const int *in, int *out, int64_t n, cudaStream_t s,
+                               int *tmp_sums, int *d_total);
+
+static void build_units(Plan &P, cudaStream_t s) {
+    const int64_t ni = P.n_items;
     if (P.units) P.release(P.units);
-    P.units = P.alloc<int4>(u.size());
-    if (!u.empty())
-        NLH_CUDA(cudaMemcpyAsync(P.units, u.data(), sizeof(int4) * u.size(),
-                                 cudaMemcpyHostToDevice, s));
-    NLH_CUDA(cudaStreamSynchronize(s));
+    P.units = P.alloc<int4>(std::max<int64_t>(ni, 1));
+    P.units_cap = ni;
+    if (!P.d_units) P.d_units = P.alloc<int>(1);
+    NLH_CUDA(cudaMemsetAsync(P.d_units, 0, sizeof(int), s));
+    if (ni == 0) return;
+    int *ucnt = nullptr, *uoff = nullptr, *sums = nullptr, *sizes = nullptr, *hist = nullptr,
+        *off = nullptr;
+    int4 *tmpu = nullptr;
+    std::vector<void *> tmp;
+    auto talloc = [&](auto **ptr, size_t bytes) {
+        NLH_CUDA(cudaMallocAsync((void **)ptr, std::max<size_t>(bytes, 4), s));
+        tmp.push_back(*ptr);
+    };
+    try {
+        talloc(&ucnt, sizeof(int) * ni);
+        talloc(&uoff, sizeof(int) * ni);
+        talloc(&sums, sizeof(int) * (div_up(ni, kScanTile) + 1));
+        talloc(&sizes, sizeof(int) * ni);
+        talloc(&tmpu, sizeof(int4) * ni);
+        talloc(&hist, sizeof(int) * kSizeBins);
+        talloc(&off, sizeof(int) * kSizeBins);
+        const int gb = (int)std::min<int64_t>(div_up(ni, 256), 152 * 8);
+        k_unit_walk<<<gb, 256, 0, s>>>(P.items, ni, P.unit_points, nullptr, ucnt, nullptr,
+                                       nullptr);
+        NLH_CHECK_LAUNCH();
+        exclusive_scan_dev(ucnt, uoff, ni, s, sums, P.d_units);
+        k_unit_walk<<<gb, 256, 0, s>>>(P.items, ni, P.unit_points, uoff, ucnt, tmpu, sizes);
+        NLH_CHECK_LAUNCH();
+        NLH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * kSizeBins, s));
+        k_size_hist<<<gb, 256, 0, s>>>(sizes, P.d_units, hist);
+        NLH_CHECK_LAUNCH();
+        k_size_offsets<<<1, 1024, 0, s>>>(hist, off);
+        NLH_CHECK_LAUNCH();
+        k_size_scatter<<<gb, 256, 0, s>>>(tmpu, sizes, P.d_units, off, P.units);
+        NLH_CHECK_LAUNCH();
+    } catch (...) {
+        for (void *ptr : tmp) cudaFreeAsync(ptr, s);
+        throw;
+    }
+    for (void *ptr : tmp) cudaFreeAsync(ptr, s);
+    P.n_units = -1;  // known on the device; read at the next synchronisation
+}
+
+// The host copy of the unit count (after the stream has been synchronised
+// or with this call's own synchronisation).
+static void fetch_unit_count(Plan &P, cudaStream_t s) {
+    int nu = 0;
+    if (P.d_units) {
+        NLH_CUDA(cudaMemcpyAsync(&nu, P.d_units, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NLH_CUDA(cudaStreamSynchronize(s));
+    }
+    P.n_units = nu;
 }
 
 // Re-split the plan's points into items of at most kmax points and units of
@@ -608,6 +761,7 @@ static void retile(Plan &P, int kmax, int unit_points, cudaStream_t s) {
     P.kmax = kmax;
     P.unit_points = unit_points;
     build_units(P, s);
+    fetch_unit_count(P, s);
 }
 
 static int ilog2(int n) {
@@ -705,6 +859,7 @@ void plan_degrees(Plan &P, cudaStream_t s) {
 
 static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *features,
                        cudaStream_t s) {
+    NLH_CUDA(cudaGetDevice(&P.device));
     P.N = desc.N;
     P.D = desc.D;
     P.L = desc.L;
@@ -717,7 +872,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
     P.unit_points = desc.unit_points > 0 ? desc.unit_points : kUnitPoints;
     for (int a = 0; a < 3; ++a) {
-        NLH_REQUIRE(desc.team[a] >= 0 && desc.team[a] <= 2, "nlh_plan_create: team[%d]=%d", a,
+        NLH_REQUIRE(desc.team[a] >= 0 && desc.team[a] <= 3, "nlh_plan_create: team[%d]=%d", a,
                     desc.team[a]);
         P.team[a] = desc.team[a];
     }
@@ -789,17 +944,16 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         k_cell_keys<<<gb, 256, 0, s>>>(features, N, P.D, L, d_win, d_center, P.scale, n, u, keys,
                                        hist);
         NLH_CHECK_LAUNCH();
-        int64_t tot = exclusive_scan(P, hist, start, ncells, s, sums, scal);
-        NLH_REQUIRE(tot == LN, "internal: cell histogram total %lld != L*N", (long long)tot);
+        exclusive_scan_dev(hist, start, ncells, s, sums, scal);
         P.perm = P.alloc<int32_t>(LN);
         NLH_CUDA(cudaMemcpyAsync(cnt, start, sizeof(int) * ncells, cudaMemcpyDeviceToDevice, s));
         k_scatter<<<gb, 256, 0, s>>>(keys, N, L, n3, cnt, P.perm);
         NLH_CHECK_LAUNCH();
         k_item_counts<<<gb, 256, 0, s>>>(hist, ncells, P.kmax, cnt, scal + 1);
         NLH_CHECK_LAUNCH();
-        P.n_items = exclusive_scan(P, cnt, ioff, ncells, s, sums, scal);
-        int occ = 0;
+        int occ = 0;  // read with the synchronisation of the scan below
         NLH_CUDA(cudaMemcpyAsync(&occ, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        P.n_items = exclusive_scan(P, cnt, ioff, ncells, s, sums, scal);
         P.items = P.alloc<int4>(P.n_items);
         k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n, P.kmax, P.items);
         NLH_CHECK_LAUNCH();
@@ -834,7 +988,6 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
                                             P.wtsdf);
         }
         NLH_CHECK_LAUNCH();
-        NLH_CUDA(cudaStreamSynchronize(s));
         P.occupied = occ;
     } catch (...) {
         for (void *ptr : tmp) cudaFreeAsync(ptr, s);
@@ -880,11 +1033,11 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.unit_ctr = P.alloc<int>(2);
     NLH_CUDA(cudaMemsetAsync(P.unit_ctr, 0, sizeof(int) * 2, s));
     P.hist = P.alloc<double>(kMaxHist);
-    NLH_CUDA(cudaMallocHost(&P.st_host, sizeof(SolveState)));
-    NLH_CUDA(cudaMallocHost(&P.red_host, sizeof(double) * 3 * kRedBlocks));
+    take_pinned(P);
     plan_tables(P, s);
     plan_degrees(P, s);
     check_device_error(P, s);
+    fetch_unit_count(P, s);
 }
 
 }  // namespace nlh
@@ -1047,7 +1200,7 @@ nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape) {
     clear_error();
     try {
         NLH_REQUIRE(plan, "nlh_plan_set_team: NULL plan");
-        NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 2,
+        NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 3,
                     "nlh_plan_set_team: arith=%d shape=%d", arith, shape);
         plan->team[arith] = shape;
         return NLH_OK;
@@ -1077,7 +1230,7 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
         NLH_CUDA(cudaEventCreate(&e1));
         const int kmaxes[] = {32, 64, 128, 256};
         const int unitpts[] = {256, 512, 1024, 2048};
-        const int nshapes = (P.W2 == 8 || P.W2 == 12) ? 3 : 1;
+        const int nshapes = (P.W2 == 8 || P.W2 == 12) ? 3 : 1;  // 4 for FP32 at 2m = 8
         double best = INFINITY;
         int bk = P.kmax, bu = P.unit_points;
         int bt[3] = {P.team[0], P.team[1], P.team[2]};
@@ -1089,7 +1242,8 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
                 for (int prec = 0; prec < 3; ++prec) {
                     if (!(mask & (prec == NLH_FP64 ? 1 : prec == NLH_FP32 ? 2 : 4))) continue;
                     double best_shape = INFINITY;
-                    for (int sh = 0; sh < nshapes; ++sh) {
+                    const int nsh = (prec == NLH_FP32 && P.W2 == 8) ? 4 : nshapes;
+                    for (int sh = 0; sh < nsh; ++sh) {
                         P.team[prec] = sh;
                         matvec(P, 0, prec, 0.0, P.t, P.q, nullptr, nullptr, s);  // warm
                         NLH_CUDA(cudaEventRecord(e0, s));

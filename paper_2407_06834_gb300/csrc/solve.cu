@@ -316,8 +316,7 @@ static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, b
     const int key = prec | (method << 2) | ((int)has_x0 << 4) | ((int)has_scale << 5);
     auto it = P.graphs.find(key);
     if (it != P.graphs.end()) return it->second;
-    if (!P.capture_stream)
-        NLH_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+    if (!P.capture_stream) P.capture_stream = take_capture_stream(P.device);
     cudaStream_t cs = P.capture_stream;
     cudaGraph_t top = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -1,0 +1,62 @@
+"""The 2048 x 2048 workload (N = 4,194,304; 5x5 reflect patches, L = 9
+windows with the last one zero-padded; M = 64, n_os = 128, m = 6) through
+the C ABI: sampled rows of Gamma_full v against the oracle's direct sums
+(within 10x the a-priori NFFT error estimate), the FP32 operator against
+the double-float one, and the mixed-precision deflated solve to the
+FP64-accurate relative residual 1e-6 for the three sigmas of the workload."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2407_06834_gb300.inputs import WORKLOADS, random_vector
+from gpu_helpers import cuda, host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2407_06834_gb300 import nlh  # noqa: E402
+
+WL = WORKLOADS["img2048"]
+
+
+@pytest.fixture(scope="module")
+def big():
+    img = WL.image()
+    return img, cuda(img)
+
+
+def test_sampled_rows_and_fp32(big):
+    img, f = big
+    P = nlh.Plan.from_image(f, WL.radius, WL.windows, 0.2, M=WL.M, n_os=WL.n_os, m=WL.m,
+                            precision=6)
+    info = P.info()
+    assert info["L"] == 9 and info["N"] == WL.N
+    v = random_vector(WL.N, 51)
+    ydf = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_DF32))
+    y32 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP32))
+    assert np.linalg.norm(y32 - ydf) / np.linalg.norm(ydf) < 1e-5
+    coords = orc.image_coords(img, WL.radius, WL.windows)
+    rows = np.sort(np.random.Generator(np.random.PCG64(52)).choice(WL.N, 24, replace=False))
+    ref = orc.gamma_full_rows(coords, 0.2, v, rows)
+    est = max(info["est_trunc_err"], info["est_alias_err"])
+    err = np.max(np.abs(ydf[rows] - ref)) / np.max(np.abs(ref))
+    assert err < 10 * est * np.abs(v).sum() / np.max(np.abs(ref)) + 1e-6, err
+
+
+@pytest.mark.parametrize("sigma", [0.1, 0.2, 0.4])
+def test_mixed_solve_2048(big, sigma):
+    img, f = big
+    P = nlh.Plan.from_image(f, WL.radius, WL.windows, sigma, M=WL.M, n_os=WL.n_os, m=WL.m,
+                            precision=6)
+    b = f.reshape(-1) * WL.alpha
+    res = P.solve(WL.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    assert res.info["status"] == 0 and res.info["rel_res_true"] <= 1e-6
+    # the FP64-accurate residual, recomputed independently of the solve
+    q = host(P.matvec(res.u, op=2, alpha=WL.alpha, precision=nlh.NLH_DF32))
+    bh = img.ravel() * WL.alpha
+    assert np.linalg.norm(bh - q) / np.linalg.norm(bh) <= 1.01e-6
+    u = host(res.u)
+    assert u.min() >= img.min() - 1e-3 and u.max() <= img.max() + 1e-3

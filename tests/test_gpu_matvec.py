@@ -228,3 +228,28 @@ def test_double_float_weights_without_fp64_path(img64):
     L1 = host(P6.matvec(one, op=1, precision=nlh.NLH_FP32))
     assert np.max(np.abs(L1)) < 1e-5 * np.max(d)
     assert relmax(host(P6.degrees()), host(P5.degrees())) < 1e-12
+
+
+@pytest.mark.parametrize("shape,kmax", [((64, 64), 0), ((37, 53), 7), ((16, 16), 0)])
+def test_fp32_tensor_core_kernels(shape, kmax):
+    """Launch shape 3 runs the FP32 spread / interpolation as 3xTF32 tensor-core
+    contractions (2m = 8): FP32 accuracy against the FP64 path, the Laplacian
+    invariants, and agreement with the CUDA-core FP32 kernels.  The 16 x 16
+    constant image puts every point into one cell (items of many chunks)."""
+    img = image(*shape) if shape != (16, 16) else np.full((16, 16), 0.3)
+    P = make_plan(img, precision=3, kmax=kmax)
+    v = random_vector(img.size, 61)
+    y64 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+    y32 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP32))
+    P.set_team(nlh.NLH_FP32, 3)
+    ytc = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP32))
+    assert relmax(ytc, y64) < 1e-5, relmax(ytc, y64)
+    assert relmax(ytc, y32) < 1e-5
+    one = cuda(np.ones(img.size))
+    d = host(P.matvec(one, op=0, precision=nlh.NLH_FP32))
+    L1 = host(P.matvec(one, op=1, precision=nlh.NLH_FP32))
+    assert np.max(np.abs(L1)) < 1e-5 * np.max(d)
+    # a mixed solve on the tensor-core inner operator reaches the tolerance
+    b = 0.5 * img.ravel()
+    r = P.solve(0.5, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    assert r.info["rel_res_true"] <= 1e-6
