@@ -113,6 +113,10 @@ SIGNATURES = {
     "nlh_net_adam": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                C.c_void_p]),
     "nlh_net_destroy": (C.c_int, [C.c_void_p]),
+    "nlh_bilevel_misfit": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_double), C.c_void_p]),
+    "nlh_bilevel_gradient_term": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.POINTER(C.c_double), C.c_void_p]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
@@ -331,6 +335,25 @@ def solve_batched(plans, alphas, bs, us=None, tol: float = 1e-6, maxit: int = 20
     st = load().nlh_solve_batched(n, hp, ha, hb, hu, C.byref(opts), infos, _stream_ptr(stream))
     _check(st, allow_not_converged=True)
     return us, [infos[i].as_dict() for i in range(n)]
+
+
+def bilevel_misfit(u, uc, r=None, stream=None) -> float:
+    """||u - uc||^2, and r = u - uc when given (nlh_bilevel_misfit)."""
+    n = u.numel()
+    sq = C.c_double(0)
+    _check(load().nlh_bilevel_misfit(n, _dptr(u, n), _dptr(uc, n),
+                                     None if r is None else _dptr(r, n), C.byref(sq),
+                                     _stream_ptr(stream)))
+    return sq.value
+
+
+def bilevel_gradient_term(p, f, u, stream=None) -> float:
+    """<p, f - u> (nlh_bilevel_gradient_term)."""
+    n = u.numel()
+    dot = C.c_double(0)
+    _check(load().nlh_bilevel_gradient_term(n, _dptr(p, n), _dptr(f, n), _dptr(u, n),
+                                            C.byref(dot), _stream_ptr(stream)))
+    return dot.value
 
 
 class Net:
