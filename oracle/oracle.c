@@ -174,6 +174,36 @@ void orc_degrees(const double *coords, long N, int L, double sigma, double *eta)
     free(ones);
 }
 
+/* The diagonal preconditioner P_b' of Sec. 4.3.3 (Eq. ANOVA_Norm_2_Prec):
+ *   (P_b')_ii^2 = (mu / L)^2 sum_l sum_{j != i} exp(-2 sigma^-2 ||W_l[f]_i - W_l[f]_j||^2)
+ *                 + (lambda + mu eta_i)^2,
+ * i.e. the first L (per-window) terms of the Pascal-simplex expansion of
+ * (Gamma o Gamma) 1 added to the square of P_a = lambda + mu eta. */
+void orc_pb_diag(const double *coords, long N, int L, double sigma, double lambda,
+                 double mu, double *P)
+{
+    double *eta = (double *)malloc(sizeof(double) * N);
+    orc_degrees(coords, N, L, sigma, eta);
+    double two_inv_s2 = 2.0 / (sigma * sigma);
+    double w = (mu / L) * (mu / L);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int l = 0; l < L; ++l) {
+            const double *ci = coords + ((long)l * N + i) * 3;
+            for (long j = 0; j < N; ++j) {
+                if (j == i) continue;
+                const double *cj = coords + ((long)l * N + j) * 3;
+                double d0 = ci[0] - cj[0], d1 = ci[1] - cj[1], d2 = ci[2] - cj[2];
+                acc += exp(-two_inv_s2 * (d0 * d0 + d1 * d1 + d2 * d2));
+            }
+        }
+        double pa = lambda + mu * eta[i];
+        P[i] = sqrt(w * acc + pa * pa);
+    }
+    free(eta);
+}
+
 /* y = A v = lambda v + mu (diag(eta) - Gamma) v, Eq. discretized-state. */
 void orc_A_apply(const double *coords, long N, int L, double sigma,
                  double lambda, double mu, const double *eta,
@@ -353,7 +383,8 @@ static void block2_prec(orc_sys *S, const double *r, double *z)
 /* Deflated (decoupled) CG of Sec. 4.1 / Sec. 4.3.2 / Sec. 5.4, in the
  * paper's coordinates: g = U^T b, x_1 = g_1 / lambda, CG on
  * B2 x_{2:n} = g_{2:n} preconditioned by pi_2(U^T P_a^-1 U) (precond = 1,
- * "P_{U,a}") or unpreconditioned (precond = 0, "I_U"); then u = U x.
+ * "P_{U,a}"), by pi_2(U^T P_b'^-1 U) (precond = 2, P_b' of Sec. 4.3.3) or
+ * unpreconditioned (precond = 0, "I_U"); then u = U x.
  * Stops when ||r|| <= tol ||b|| (r the CG residual of the second block,
  * whose norm equals ||b - A u|| because U is orthogonal and the first block
  * is solved exactly).  hist[k] = ||r_k|| / ||b|| for k = 0..iters.
@@ -376,7 +407,10 @@ int orc_pcg_deflated(const double *coords, long N, int L, double sigma,
                  (double *)malloc(sizeof(double) * N),
                  (double *)malloc(sizeof(double) * N)};
     orc_degrees(coords, N, L, sigma, eta);
-    for (long i = 0; i < N; ++i) P[i] = lambda + mu * eta[i];
+    if (precond == 2)
+        orc_pb_diag(coords, N, L, sigma, lambda, mu, P);
+    else
+        for (long i = 0; i < N; ++i) P[i] = lambda + mu * eta[i];
     if (precond) S.P = P;
 
     orc_Ut_apply(b, N, g);
@@ -416,7 +450,8 @@ int orc_pcg_deflated(const double *coords, long N, int L, double sigma,
 }
 
 /* CG / Jacobi-PCG in the original basis (Sec. 5.3, Table 2 with no
- * preconditioner and x0 = f; Sec. 5.4 "P_a"): precond 0 = I, 1 = P_a.
+ * preconditioner and x0 = f; Sec. 5.4 "P_a"): precond 0 = I, 1 = P_a,
+ * 2 = P_b' (Sec. 4.3.3).
  * x0 may be NULL (zero start).  Same stopping rule and history as above. */
 int orc_cg(const double *coords, long N, int L, double sigma, double lambda,
            double mu, const double *b, const double *x0, double tol, int maxit,
@@ -429,7 +464,10 @@ int orc_cg(const double *coords, long N, int L, double sigma, double lambda,
     double *p = (double *)malloc(sizeof(double) * N);
     double *q = (double *)malloc(sizeof(double) * N);
     orc_degrees(coords, N, L, sigma, eta);
-    for (long i = 0; i < N; ++i) P[i] = lambda + mu * eta[i];
+    if (precond == 2)
+        orc_pb_diag(coords, N, L, sigma, lambda, mu, P);
+    else
+        for (long i = 0; i < N; ++i) P[i] = lambda + mu * eta[i];
     for (long i = 0; i < N; ++i) u[i] = x0 ? x0[i] : 0.0;
     orc_A_apply(coords, N, L, sigma, lambda, mu, eta, u, q);
     for (long i = 0; i < N; ++i) r[i] = b[i] - q[i];

@@ -70,6 +70,7 @@ def _load():
             "orc_gamma_matvec": (None, [_dp, L, C.c_int, C.c_double, _dp, _dp]),
             "orc_gamma_dense": (None, [_dp, L, C.c_int, C.c_double, _dp]),
             "orc_degrees": (None, [_dp, L, C.c_int, C.c_double, _dp]),
+            "orc_pb_diag": (None, [_dp, L, C.c_int, C.c_double, C.c_double, C.c_double, _dp]),
             "orc_A_apply": (None, [_dp, L, C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]),
             "orc_gauss_fourier_coeff": (C.c_double, [C.c_double, C.c_double]),
             "orc_trig_kernel_1d": (C.c_double, [C.c_double, C.c_double, C.c_int]),
@@ -244,19 +245,30 @@ class SolveResult:
 
 
 def pcg_deflated(coords, sigma, lam, mu, b, tol=1e-6, maxit=200, precond=True):
-    """The paper's decoupled CG in U coordinates (P_{U,a} or I_U)."""
+    """The paper's decoupled CG in U coordinates: precond True / 1 = P_{U,a},
+    2 = with P_b' (Sec. 4.3.3), False / 0 = I_U."""
     coords = _f64(coords)
     L, N, _ = coords.shape
     u = np.empty(N)
     hist = np.zeros(maxit + 1)
     it = C.c_int(0)
     st = _load().orc_pcg_deflated(coords, N, L, sigma, lam, mu, _f64(b), tol, maxit,
-                                  1 if precond else 0, u, hist, C.byref(it))
+                                  int(precond), u, hist, C.byref(it))
     return SolveResult(u, hist, it.value, st)
 
 
+def pb_diag(coords, sigma, lam, mu):
+    """The diagonal of P_b' (Sec. 4.3.3, Eq. ANOVA_Norm_2_Prec)."""
+    coords = _f64(coords)
+    L, N, _ = coords.shape
+    P = np.empty(N)
+    _load().orc_pb_diag(coords, N, L, sigma, lam, mu, P)
+    return P
+
+
 def cg(coords, sigma, lam, mu, b, x0=None, tol=1e-6, maxit=200, precond=False):
-    """CG (precond False) or Jacobi-PCG with P_a (precond True), original basis."""
+    """CG (precond False / 0), Jacobi-PCG with P_a (True / 1) or with P_b'
+    (2, Sec. 4.3.3), original basis."""
     coords = _f64(coords)
     L, N, _ = coords.shape
     u = np.empty(N)
@@ -265,5 +277,5 @@ def cg(coords, sigma, lam, mu, b, x0=None, tol=1e-6, maxit=200, precond=False):
     x0a = None if x0 is None else _f64(x0)
     st = _load().orc_cg(coords, N, L, sigma, lam, mu, _f64(b),
                         None if x0a is None else x0a.ctypes.data_as(C.c_void_p),
-                        tol, maxit, 1 if precond else 0, u, hist, C.byref(it))
+                        tol, maxit, int(precond), u, hist, C.byref(it))
     return SolveResult(u, hist, it.value, st)
