@@ -343,10 +343,10 @@ def run_ours(args):
         Q.close()
     torch.cuda.synchronize()
     solve_s["plan_seconds"] = (time.perf_counter() - t0) / 3
-    for nm, ar in (("fp64", nlh.SOLVE_FP64), ("df32", nlh.SOLVE_DF32),
-                   ("mixed", nlh.SOLVE_MIXED)):
-        P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
-        r = P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
+    for nm, ar, pc in (("fp64", nlh.SOLVE_FP64, 0), ("df32", nlh.SOLVE_DF32, 0),
+                       ("mixed", nlh.SOLVE_MIXED, 0), ("mixed_pb", nlh.SOLVE_MIXED, 1)):
+        P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3, precond=pc)
+        r = P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3, precond=pc)
         solve_s[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
                        "rel_res_fp64": r.info["rel_res_true"]}
     # kernel-only matvec throughput

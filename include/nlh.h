@@ -140,7 +140,9 @@ nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
  * bit mask `precisions` (0 = all the plan built) for each tiling of a fixed
  * grid (max_items_pts in {32, 64, 128, 256} x unit_points in {256, 512, 1024,
  * 2048}) and, per arithmetic, each launch shape; leave the plan in the
- * tiling with the smallest sum over the arithmetics of their fastest shape,
+ * tiling with the smallest sum over the arithmetics of their fastest shape
+ * among 0-2 (shape 3 changes the FP32 rounding and thereby the mixed form's
+ * iteration counts, which this timing does not measure),
  * with those shapes; report it (any output pointer may be NULL; best_team
  * has 3 entries indexed like nlh_plan_desc.team) and its summed matvec time
  * in ms.  Synchronises `stream`. */
@@ -199,6 +201,12 @@ typedef struct {
                                the method's own start ((mean(b)/alpha) 1 for
                                the deflated methods, 0 otherwise), else start
                                there (info.x0_rejected); 0: use x0 as given */
+    int precond;            /* preconditioner of NLH_PCG_JACOBI and
+                               NLH_PCG_DEFLATED: 0 P_a = alpha + max(d-1, 0)
+                               (Jacobi), 1 P_b' = sqrt(P_a^2 + (d'-1)/L)
+                               with d' = Gamma_full 1 at sigma/sqrt(2)
+                               (Sec. 4.3.3, Eq. ANOVA_Norm_2_Prec); d' is
+                               computed once per plan and sigma           */
 } nlh_solve_opts;
 
 typedef struct {

@@ -106,6 +106,9 @@ struct Plan {
     int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 64;
     int unit_points = kUnitPoints;
     int team[3] = {0, 0, 0};  // spread / interpolation team shape per arithmetic
+    double *pb2 = nullptr;     // (d' - 1) / L for P_b' (d' = Gamma_full 1 at sigma / sqrt 2)
+    double pb2_sigma = -1.0;   // sigma pb2 was computed for
+    int pc_kind = 0;           // preconditioner of the current solve: 0 P_a, 1 P_b'
     double sigma = 0, fill = 0, scale = 0, R = 0, kb_beta = 0;
     int64_t n_items = 0, occupied = 0;
     std::vector<int32_t> windows;
@@ -214,6 +217,7 @@ __device__ __forceinline__ double reduce_partials(const double *parts, int npart
 
 // ---------------------------------------------------------------- host API (internal)
 void plan_tables(Plan &P, cudaStream_t s);
+void ensure_pb2(Plan &P, cudaStream_t s);
 // Keep freed pool memory in the process (set once).
 void retain_pool_memory();
 // Throws Failure{NLH_ERR_TIMEOUT} if a kernel recorded a bounded wait that

@@ -29,11 +29,13 @@ namespace nlh {
 __device__ __forceinline__ double *pq_parts(double *partials) { return partials + 4 * kRedBlocks; }
 
 // ------------------------------------------------------------------ kernels
-// pinv = 1 / (c o (alpha + max(d - 1, 0))) for Jacobi (eta = d - 1, the
-// exact diagonal 1 removed), or 1.  alpha is read from the solve state.
+// pinv = 1 / (c o P) with P the Jacobi diagonal P_a = alpha + max(d - 1, 0)
+// (eta = d - 1, the exact diagonal 1 removed), or with pb2 given the P_b'
+// of Sec. 4.3.3, P = sqrt(P_a^2 + pb2) (Eq. ANOVA_Norm_2_Prec with mu = 1);
+// or 1 without preconditioner.  alpha is read from the solve state.
 __global__ void k_pinv(const double *__restrict__ d, const double *__restrict__ c,
-                       const SolveState *__restrict__ st, int precond, int64_t N,
-                       double *__restrict__ pinv) {
+                       const double *__restrict__ pb2, const SolveState *__restrict__ st,
+                       int precond, int64_t N, double *__restrict__ pinv) {
     const double alpha = st->alpha;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -41,11 +43,28 @@ __global__ void k_pinv(const double *__restrict__ d, const double *__restrict__ 
         if (precond) {
             double eta = fmax(d[i] - 1.0, 0.0);
             double P = alpha + eta;
+            if (pb2) P = sqrt(P * P + pb2[i]);
             if (c) P *= c[i];
             v = 1.0 / P;
         }
         pinv[i] = v;
     }
+}
+
+__global__ void k_ones(double *__restrict__ x, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 1.0;
+}
+
+// pb2 = max(d' - 1, 0) / L: sum_l (Gamma_l o Gamma_l) 1 (zero diagonal) over
+// L^2, from d' = Gamma_full 1 at sigma / sqrt 2 (the per-window kernel
+// squared is the kernel at sigma / sqrt 2, and Gamma_full averages the L
+// per-window sums, each with its diagonal 1).
+__global__ void k_pb2(double *__restrict__ v, int64_t N, double inv_l) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = fmax(v[i] - 1.0, 0.0) * inv_l;
 }
 
 // r = rhs - q (q = A x0) or rhs; partials: sum r, sum rhs^2, sum rhs.
@@ -248,6 +267,33 @@ k_residual(const double *__restrict__ b, const double *__restrict__ q, int64_t N
 }
 
 // ------------------------------------------------------------------ host drivers
+// The P_b' term of the plan for its current sigma (computed once per sigma):
+// a degree matvec with the multiplier tables of sigma / sqrt 2 (the torus
+// map and the window weights do not depend on sigma), in the plan's most
+// accurate arithmetic.
+void ensure_pb2(Plan &P, cudaStream_t s) {
+    if (P.pb2 && P.pb2_sigma == P.sigma) return;
+    if (!P.pb2) P.pb2 = P.alloc<double>(P.N);
+    const double sig = P.sigma;
+    P.sigma = sig / std::sqrt(2.0);
+    try {
+        plan_tables(P, s);
+        k_ones<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N);
+        NLH_CHECK_LAUNCH();
+        const int prec = (P.precision & 1) ? NLH_FP64 : (P.precision & 4) ? NLH_DF32 : NLH_FP32;
+        matvec(P, 0, prec, 0.0, P.t, P.pb2, nullptr, nullptr, s);
+        k_pb2<<<kRedBlocks, kRedThreads, 0, s>>>(P.pb2, P.N, 1.0 / P.L);
+        NLH_CHECK_LAUNCH();
+    } catch (...) {
+        P.sigma = sig;
+        plan_tables(P, s);
+        throw;
+    }
+    P.sigma = sig;
+    plan_tables(P, s);
+    P.pb2_sigma = sig;
+}
+
 struct KrylovResult {
     int iters = 0;
     int status = 0;  // 0 ok, 1 not converged, -4 breakdown
@@ -273,7 +319,8 @@ static void enqueue_init(Plan &P, int prec, int method, bool has_x0, bool has_sc
     const int B = kRedBlocks, T = kRedThreads;
     const double *d = P.d64 ? P.d64 : (P.ddf ? P.ddf : P.d32);
     double *part2 = P.partials + 5 * kRedBlocks;
-    k_pinv<<<B, T, 0, s>>>(d, has_scale ? P.cbuf : nullptr, P.st, precond, N, P.pinv);
+    k_pinv<<<B, T, 0, s>>>(d, has_scale ? P.cbuf : nullptr, P.pc_kind == 1 ? P.pb2 : nullptr,
+                           P.st, precond, N, P.pinv);
     NLH_CHECK_LAUNCH();
     const double *qptr = nullptr;
     if (has_x0) {
@@ -313,7 +360,8 @@ static void enqueue_iteration(Plan &P, int prec, int method, unsigned long long 
 // the loop condition from the device-side convergence flag, so the solve
 // runs without any host round trip.  Graphs are cached per plan.
 static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, bool has_scale) {
-    const int key = prec | (method << 2) | ((int)has_x0 << 4) | ((int)has_scale << 5);
+    const int key = prec | (method << 2) | ((int)has_x0 << 4) | ((int)has_scale << 5) |
+                    (P.pc_kind << 6);
     auto it = P.graphs.find(key);
     if (it != P.graphs.end()) return it->second;
     if (!P.capture_stream) P.capture_stream = take_capture_stream(P.device);
@@ -468,6 +516,8 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                     "nlh_solve: tol=%g maxit=%d", opts->tol, opts->maxit);
         NLH_REQUIRE(opts->method >= NLH_CG && opts->method <= NLH_CG_DEFLATED,
                     "nlh_solve: method=%d", opts->method);
+        NLH_REQUIRE(opts->precond == 0 || opts->precond == 1, "nlh_solve: precond=%d",
+                    opts->precond);
         NLH_REQUIRE(opts->arith >= NLH_SOLVE_FP64 && opts->arith <= NLH_SOLVE_DF32,
                     "nlh_solve: arith=%d", opts->arith);
         Plan &P = *plan;
@@ -485,6 +535,8 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                         "nlh_solve: mixed solve needs the FP32 path and an FP64-accurate path");
         const int solve_prec = opts->arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32;
         const double *scale = opts->diag_scale;
+        P.pc_kind = opts->precond;
+        if (P.pc_kind == 1) ensure_pb2(P, s);
         // With x0_check a warm start is used only if its residual is below
         // that of the method's own start: (mean(b) / alpha) 1 for the
         // deflated methods, 0 for CG and Jacobi-PCG.
@@ -627,6 +679,8 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                     "nlh_solve_batched: tol=%g maxit=%d", opts->tol, opts->maxit);
         NLH_REQUIRE(opts->method >= NLH_CG && opts->method <= NLH_CG_DEFLATED,
                     "nlh_solve_batched: method=%d", opts->method);
+        NLH_REQUIRE(opts->precond == 0 || opts->precond == 1, "nlh_solve_batched: precond=%d",
+                    opts->precond);
         NLH_REQUIRE(opts->arith >= NLH_SOLVE_FP64 && opts->arith <= NLH_SOLVE_DF32,
                     "nlh_solve_batched: arith=%d", opts->arith);
         NLH_REQUIRE(opts->x0 == nullptr && opts->diag_scale == nullptr,
@@ -674,6 +728,8 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                 Plan &P = *plans[i];
                 cudaStream_t s = g_pool[gi % ns];
                 P.stream = s;
+                P.pc_kind = opts->precond;
+                if (P.pc_kind == 1) ensure_pb2(P, s);
                 const int accurate = (P.precision & 4) ? NLH_DF32 : NLH_FP64;
                 if (!mixed) {
                     const int prec = opts->arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32;

@@ -22,6 +22,7 @@ _lib = None
 
 NLH_OK, NLH_ERR_NOT_CONVERGED = 0, 1
 NLH_FP64, NLH_FP32, NLH_DF32 = 0, 1, 2
+PREC_PA, PREC_PB = 0, 1      # Jacobi P_a, and P_b' of Sec. 4.3.3
 CG, PCG_JACOBI, PCG_DEFLATED, CG_DEFLATED = 0, 1, 2, 3
 SOLVE_FP64, SOLVE_MIXED, SOLVE_DF32 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
@@ -51,7 +52,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("method", C.c_int),
                 ("arith", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
                 ("x0", C.c_void_p), ("diag_scale", C.c_void_p), ("hist", C.c_void_p),
-                ("hist_len", C.c_int), ("check_every", C.c_int), ("x0_check", C.c_int)]
+                ("hist_len", C.c_int), ("check_every", C.c_int), ("x0_check", C.c_int),
+                ("precond", C.c_int)]
 
 
 class NetBatch(C.Structure):
@@ -286,7 +288,7 @@ class Plan:
     def solve(self, alpha: float, b, tol: float = 1e-6, maxit: int = 200,
               method: int = PCG_DEFLATED, arith: int = SOLVE_FP64, inner_tol: float = 0.0,
               max_outer: int = 0, x0=None, diag_scale=None, u=None, check_every: int = 0,
-              x0_check: bool = False,
+              x0_check: bool = False, precond: int = 0,
               hist_len: int = 256, stream=None) -> SolveResult:
         torch = _torch()
         u = u if u is not None else torch.empty_like(b)
@@ -296,7 +298,7 @@ class Plan:
                          x0=None if x0 is None else _dptr(x0, self.N),
                          diag_scale=None if diag_scale is None else _dptr(diag_scale, self.N),
                          hist=hist.ctypes.data, hist_len=hist_len, check_every=check_every,
-                         x0_check=1 if x0_check else 0)
+                         x0_check=1 if x0_check else 0, precond=int(precond))
         info = SolveInfo()
         st = load().nlh_solve(self._h, float(alpha), _dptr(b, self.N), _dptr(u, self.N),
                               C.byref(opts), C.byref(info), _stream_ptr(stream))
@@ -319,7 +321,7 @@ class Plan:
 
 def solve_batched(plans, alphas, bs, us=None, tol: float = 1e-6, maxit: int = 200,
                   method: int = PCG_DEFLATED, arith: int = SOLVE_MIXED, inner_tol: float = 0.0,
-                  max_outer: int = 0, stream=None):
+                  max_outer: int = 0, precond: int = 0, stream=None):
     """Solve (alpha_i I + L_i) u_i = b_i for many plans at once (nlh_solve_batched)."""
     torch = _torch()
     n = len(plans)
@@ -330,7 +332,7 @@ def solve_batched(plans, alphas, bs, us=None, tol: float = 1e-6, maxit: int = 20
     hu = (C.c_void_p * n)(*[_dptr(u, p.N) for u, p in zip(us, plans)])
     opts = SolveOpts(tol=tol, maxit=maxit, method=method, arith=arith, inner_tol=inner_tol,
                      max_outer=max_outer, x0=None, diag_scale=None, hist=None, hist_len=0,
-                     check_every=0, x0_check=0)
+                     check_every=0, x0_check=0, precond=int(precond))
     infos = (SolveInfo * n)()
     st = load().nlh_solve_batched(n, hp, ha, hb, hu, C.byref(opts), infos, _stream_ptr(stream))
     _check(st, allow_not_converged=True)

@@ -222,3 +222,38 @@ def test_warm_start_screening(tight64):
     # without the check the paper's CG start (x0 = f) is used as given
     r = P.solve(ALPHA, cuda(b), tol=1e-6, method=nlh.CG, x0=cuda(img.ravel()))
     assert r.info["x0_rejected"] == 0
+
+
+def test_pb_preconditioner_matches_oracle(tight64):
+    """P_b' (Sec. 4.3.3): the deflated CG with P_b' follows the oracle's
+    U-coordinate CG with P_b' residual by residual; Jacobi-PCG with P_b' from
+    x0 = f follows the oracle's; the mixed form reaches the tolerance."""
+    img, coords, P = tight64
+    f = img.ravel()
+    b = ALPHA * f
+    res = P.solve(ALPHA, cuda(b), tol=1e-6, method=nlh.PCG_DEFLATED, precond=nlh.PREC_PB)
+    o = orc.pcg_deflated(coords, SIGMA, ALPHA, 1.0, b, tol=1e-6, maxit=200, precond=2)
+    assert res.info["status"] == 0 and res.info["iters"] == o.iters
+    np.testing.assert_allclose(res.hist, o.hist[:o.iters + 1], rtol=1e-7)
+    r2 = P.solve(ALPHA, cuda(b), tol=1e-6, maxit=400, method=nlh.PCG_JACOBI, x0=cuda(f),
+                 precond=nlh.PREC_PB)
+    o2 = orc.cg(coords, SIGMA, ALPHA, 1.0, b, x0=f, tol=1e-6, maxit=400, precond=2)
+    assert abs(r2.info["iters"] - o2.iters) <= 1
+    n = min(r2.info["iters"], o2.iters) + 1
+    np.testing.assert_allclose(r2.hist[:n], o2.hist[:n], rtol=1e-6)
+    # P_b' and P_a need comparable iteration counts (Table 3)
+    ra = P.solve(ALPHA, cuda(b), tol=1e-6, method=nlh.PCG_DEFLATED)
+    assert abs(ra.info["iters"] - res.info["iters"]) <= max(2, ra.info["iters"] // 2)
+    # after a change of sigma the P_b' term is recomputed
+    P.set_sigma(0.3)
+    r3 = P.solve(ALPHA, cuda(b), tol=1e-6, method=nlh.PCG_DEFLATED, precond=nlh.PREC_PB)
+    o3 = orc.pcg_deflated(coords, 0.3, ALPHA, 1.0, b, tol=1e-6, maxit=200, precond=2)
+    P.set_sigma(SIGMA)
+    assert r3.info["iters"] == o3.iters
+    np.testing.assert_allclose(r3.hist, o3.hist[:o3.iters + 1], rtol=1e-7)
+    Pm = make_plan(img, precision=6)
+    rm = Pm.solve(ALPHA, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3,
+                  precond=nlh.PREC_PB)
+    assert rm.info["rel_res_true"] <= 1e-6
+    with pytest.raises(nlh.NLHError):
+        P.solve(ALPHA, cuda(b), precond=2)
