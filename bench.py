@@ -566,6 +566,9 @@ def run_bilevel(args):
     res = B.learn(bounds=(1e-2, 1e6), xatol=1e-3)
     j0 = float(np.mean([np.sum((c - n) ** 2) for c, n in pairs]))
     _, g = B.objective_and_gradient(res.alpha)
+    joint = B.learn_alpha_theta(res.alpha, 0.2, bounds_alpha=(1e-2, 1e6),
+                                bounds_sigma=(0.1, 0.4))
+    joint.pop("history")
     B.close()
     print(json.dumps({
         "metric": "bilevel learning of alpha: seconds (8 pairs of 256x256, Brent, mixed solves)",
@@ -573,6 +576,7 @@ def run_bilevel(args):
         "alpha": res.alpha, "j": res.j, "j_noisy": j0, "evaluations": res.evaluations,
         "lower_level_solves": res.solves, "cg_iters_per_solve": res.cg_iters_mean,
         "gradient_at_alpha": g, "plans_seconds": t_plans,
+        "joint_alpha_theta": joint,
         "history": res.history,
         "config": {"workload": "8 synthetic pairs (seeds 1-8) 256x256, 3x3 reflect patches, "
                                "L=3, sigma=0.2, Lambda=[1e-2, 1e6], tol 1e-8"}}), flush=True)

@@ -63,6 +63,7 @@ class Bilevel:
         self.r = [torch.empty_like(f) for f in self.f]
         self.solves = 0
         self.cg_iters = 0
+        self.sigma = sigma
 
     @property
     def T(self) -> int:
@@ -115,6 +116,55 @@ class Bilevel:
         return LearnResult(float(math.exp(res.x)), float(res.fun), int(res.nfev),
                            time.perf_counter() - t0, n_s,
                            (self.cg_iters - c0) / max(1, n_s), hist)
+
+    def set_sigma(self, sigma: float):
+        """Kernel width of every lower-level system (multiplier tables and
+        degrees; the torus map and the window weights are kept)."""
+        for P in self.plans:
+            P.set_sigma(sigma)
+        self.sigma = sigma
+
+    def learn_alpha_theta(self, alpha0: float, sigma0: float, bounds_alpha=(1e-3, 1e3),
+                          bounds_sigma=(0.05, 1.0), rel_step: float = 1e-4,
+                          maxiter: int = 50) -> dict:
+        """Joint learning of (alpha, theta = sigma^-2) (Sec. 5.5) with
+        L-BFGS-B over (log alpha, log theta): dj/dalpha by the adjoint
+        solves, dj/dtheta by a central difference in log theta (the paper
+        used two-point differences for both)."""
+        from scipy.optimize import minimize
+        torch = _torch()
+        evals = []
+        s0, c0 = self.solves, self.cg_iters
+
+        def fg(z):
+            la, lt = float(z[0]), float(z[1])
+            a, th = math.exp(la), math.exp(lt)
+            self.set_sigma(th ** -0.5)
+            j, ga = self.objective_and_gradient(a)
+            h = rel_step
+            self.set_sigma(math.exp(lt + h) ** -0.5)
+            jp = self.objective(a)
+            self.set_sigma(math.exp(lt - h) ** -0.5)
+            jm = self.objective(a)
+            self.set_sigma(th ** -0.5)
+            evals.append((a, th ** -0.5, j))
+            return j, np.array([ga * a, (jp - jm) / (2 * h)])
+
+        lt_b = (math.log(bounds_sigma[1] ** -2), math.log(bounds_sigma[0] ** -2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = minimize(fg, np.array([math.log(alpha0), math.log(sigma0 ** -2)]), jac=True,
+                       method="L-BFGS-B",
+                       bounds=[(math.log(bounds_alpha[0]), math.log(bounds_alpha[1])), lt_b],
+                       options={"maxiter": maxiter, "ftol": 1e-12, "gtol": 1e-8})
+        torch.cuda.synchronize()
+        a, th = math.exp(res.x[0]), math.exp(res.x[1])
+        self.set_sigma(th ** -0.5)
+        return {"alpha": a, "sigma": th ** -0.5, "theta": th, "j": float(res.fun),
+                "iterations": int(res.nit), "evaluations": len(evals),
+                "seconds": time.perf_counter() - t0, "solves": self.solves - s0,
+                "cg_iters_mean": (self.cg_iters - c0) / max(1, self.solves - s0),
+                "history": evals}
 
     def close(self):
         for P in self.plans:

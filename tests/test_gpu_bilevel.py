@@ -79,3 +79,22 @@ def test_reduction_argument_errors():
     r = torch.empty_like(x)
     assert nlh.bilevel_misfit(x + 2, x, r) == pytest.approx(16.0)
     assert torch.all(r == 2)
+
+
+def test_joint_alpha_theta_matches_oracle(problem):
+    """Joint (alpha, theta = sigma^-2) learning (Sec. 5.5): L-BFGS-B with the
+    adjoint alpha-derivative and a central difference in log theta, on the
+    GPU and in the oracle, from the same start; sigma is kept in [0.15, 0.5],
+    where the tight NFFT parameters stay below 1e-9."""
+    B, (Ls, fs, ucs), pairs = problem
+    coords = [orc.image_coords(noisy, 1, raster_windows(1)) for _, noisy in pairs]
+    try:
+        res = B.learn_alpha_theta(30.0, SIGMA, bounds_sigma=(0.15, 0.5))
+        ao, so, jo = obl.learn_alpha_theta(coords, fs, ucs, 30.0, SIGMA, bounds_sigma=(0.15, 0.5))
+        assert res["j"] == pytest.approx(jo, rel=1e-6)
+        assert res["alpha"] == pytest.approx(ao, rel=1e-3)
+        assert res["sigma"] == pytest.approx(so, rel=1e-3)
+        j_alpha_only = obl.objective_and_gradient(Ls, fs, ucs, 30.0)[0]
+        assert res["j"] <= j_alpha_only * (1 + 1e-9)
+    finally:
+        B.set_sigma(SIGMA)

@@ -60,3 +60,22 @@ def test_brent_minimiser_is_stationary(pairs):
     assert abs(g) * a < 1e-3 * abs(jl - j)
     for b in (lo, hi, a * 0.9, a * 1.1):
         assert j <= bilevel.objective_and_gradient(Ls, fs, ucs, b)[0]
+
+
+def test_joint_learning_improves_on_alpha_alone():
+    """The joint (alpha, theta) minimum is no worse than the alpha-only one
+    at the initial sigma, and stationary in alpha."""
+    ucs, fs, coords = [], [], []
+    for seed in (3, 4):
+        clean, noisy = synthetic_image(10, 10, seed)
+        ucs.append(clean.ravel())
+        fs.append(noisy.ravel())
+        coords.append(orc.image_coords(noisy, 1, raster_windows(1)))
+    Ls = bilevel.laplacians(coords, 0.1)
+    a1, j1, _ = bilevel.learn_alpha(Ls, fs, ucs, bounds=(1e-3, 1e3), xatol=1e-8)
+    a2, s2, j2 = bilevel.learn_alpha_theta(coords, fs, ucs, a1, 0.1, bounds_sigma=(0.05, 0.5))
+    assert j2 <= j1 * (1 + 1e-9)
+    assert 0.05 <= s2 <= 0.5
+    _, g = bilevel.objective_and_gradient(bilevel.laplacians(coords, s2), fs, ucs, a2)
+    if 1.1e-3 < a2 < 1e3 / 1.1:
+        assert abs(g * a2) < 1e-3 * j2
