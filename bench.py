@@ -477,14 +477,17 @@ def learned_leg(args, dev):
 
 
 def matvec_case(args):
-    """Small profiling case: plan (both precisions) + 2 matvecs per precision."""
+    """Small profiling case: one 512x512 plan with all three arithmetics and
+    the autotuned launch shapes of the bench step (FP32: default; double-
+    float: 2 warps x 4 teams), then 2 matvecs per arithmetic."""
     import torch
 
     from paper_2407_06834_gb300 import nlh
     wl = WORKLOADS[args.workload]
     img = torch.as_tensor(wl.image(), device="cuda")
     P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                            n_os=wl.n_os, m=wl.m, precision=7)
+                            n_os=wl.n_os, m=wl.m, precision=7, max_items_pts=128,
+                            unit_points=512, team=(0, 0, 2))
     x = torch.randn(wl.N, dtype=torch.float64, device="cuda")
     for prec in (nlh.NLH_FP64, nlh.NLH_FP32, nlh.NLH_DF32):
         for _ in range(2):

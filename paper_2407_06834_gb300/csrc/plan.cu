@@ -8,6 +8,7 @@
 #include "df32.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -456,12 +457,15 @@ static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &co
     throw Failure{NLH_ERR_ARG};
 }
 
+// The 2m weights of one dim are 2m independent Horner chains; a compile-time
+// 2m lets them advance in lockstep (instruction-level parallelism across
+// the dependent multiply-add steps).
+template <int W2>
 __global__ void k_weights(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
-                          int L, int m, int K, const double *__restrict__ coef, int rec64,
-                          int rec32, double *__restrict__ w64, float *__restrict__ w32,
+                          int L, int K, const double *__restrict__ coef, int rec64, int rec32,
+                          double *__restrict__ w64, float *__restrict__ w32,
                           float *__restrict__ wdf) {
     __shared__ double sc[16 * kMaxPolyCoef];
-    const int W2 = 2 * m;
     for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
     __syncthreads();
     const int64_t total = (int64_t)L * N;
@@ -473,16 +477,20 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
         for (int t = 0; t < 3; ++t) {
             double ut = up[t];
             double y = 2.0 * (ut - floor(ut)) - 1.0;
+            double w[W2];
+#pragma unroll
+            for (int j = 0; j < W2; ++j) w[j] = sc[j * K + K - 1];
+            for (int q = K - 2; q >= 0; --q)
+#pragma unroll
+                for (int j = 0; j < W2; ++j) w[j] = fma(w[j], y, sc[j * K + q]);
+#pragma unroll
             for (int j = 0; j < W2; ++j) {
-                const double *a = sc + j * K;
-                double w = a[K - 1];
-                for (int q = K - 2; q >= 0; --q) w = fma(w, y, a[q]);
-                if (w64) w64[sidx * rec64 + t * W2 + j] = w;
-                if (w32) w32[sidx * rec32 + t * W2 + j] = (float)w;
+                if (w64) w64[sidx * rec64 + t * W2 + j] = w[j];
+                if (w32) w32[sidx * rec32 + t * W2 + j] = (float)w[j];
                 if (wdf) {  // double-float record: per dim 2m high parts, then 2m low parts
-                    const float hi = (float)w;
+                    const float hi = (float)w[j];
                     wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
-                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = (float)(w - (double)hi);
+                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = (float)(w[j] - (double)hi);
                 }
             }
         }
@@ -499,11 +507,11 @@ __global__ void k_weights(const int *__restrict__ perm, const double *__restrict
 // for the double-float records, their rounded high parts for the FP32
 // records.  GB300 runs FP32 ~59x faster than FP64, so this is several times
 // faster than the FP64 Horner above.
+template <int W2>
 __global__ void k_weights_df(const int *__restrict__ perm, const double *__restrict__ u,
-                             int64_t N, int L, int m, int K, const float2 *__restrict__ coef,
+                             int64_t N, int L, int K, const float2 *__restrict__ coef,
                              int rec32, float *__restrict__ w32, float *__restrict__ wdf) {
     __shared__ float2 sc[16 * kMaxPolyCoef];
-    const int W2 = 2 * m;
     for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
     __syncthreads();
     const int64_t total = (int64_t)L * N;
@@ -515,13 +523,18 @@ __global__ void k_weights_df(const int *__restrict__ perm, const double *__restr
         for (int t = 0; t < 3; ++t) {
             const double ut = up[t];
             const df32 y(2.0 * (ut - floor(ut)) - 1.0);
+            df32 w[W2];
+#pragma unroll
+            for (int j = 0; j < W2; ++j) w[j] = df32(sc[j * K + K - 1].x, sc[j * K + K - 1].y);
+            for (int q = K - 2; q >= 0; --q)
+#pragma unroll
+                for (int j = 0; j < W2; ++j)
+                    w[j] = w[j] * y + df32(sc[j * K + q].x, sc[j * K + q].y);
+#pragma unroll
             for (int j = 0; j < W2; ++j) {
-                const float2 *a = sc + j * K;
-                df32 w(a[K - 1].x, a[K - 1].y);
-                for (int q = K - 2; q >= 0; --q) w = w * y + df32(a[q].x, a[q].y);
                 // renormalise (Fast2Sum; |lo| is a few ulps of hi at most)
-                const float hi = __fadd_rn(w.hi, w.lo);
-                const float lo = __fsub_rn(w.lo, __fsub_rn(hi, w.hi));
+                const float hi = __fadd_rn(w[j].hi, w[j].lo);
+                const float lo = __fsub_rn(w[j].lo, __fsub_rn(hi, w[j].hi));
                 if (w32) w32[sidx * rec32 + t * W2 + j] = hi;
                 if (wdf) {
                     wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
@@ -588,50 +601,78 @@ __global__ void k_fill(double *__restrict__ x, int64_t n, double v) {
         x[i] = v;
 }
 
-// Work units: consecutive items (tile-major order) of one window and one
-// tile, cut when the running point count would exceed unit_points or the
-// item count kUnitItems.  Units are then ordered by decreasing point count
-// so that the largest start first (a counting sort on the size; the order
-// among units of one size is not fixed).  Built on the device, without a
-// host round trip: one thread walks each (window, tile) group of items; the
-// unit count stays in device memory (P.d_units[0]) for the persistent
-// kernels and reaches the host at the plan's next synchronisation.
+// Work units: runs of consecutive items (tile-major order) of one window and
+// one tile.  An item belongs to the unit given by the bucket of its point
+// offset inside the (window, tile) group (unit_points points per bucket) and
+// of its item index inside the group (kUnitItems per bucket); a unit may
+// exceed unit_points by its last item.  Units are then ordered by
+// decreasing point count so that the largest start first (a counting sort
+// on the size; the order among units of one size is not fixed).  All on the
+// device, in data-parallel passes: the unit count stays in device memory
+// (P.d_units[0]) for the persistent kernels and reaches the host at the
+// plan's next synchronisation.
 constexpr int kSizeBins = 4096;
 
-__device__ __forceinline__ bool same_group(const int4 &a, const int4 &b) {
-    return (a.x >> 16) == (b.x >> 16) && a.y == b.y;
+// (window, tile) group of an item; ntiles = tiles per window
+__device__ __forceinline__ int group_key(const int4 &it, int ntiles) {
+    return (it.x >> 16) * ntiles + it.y;
 }
 
-// Count pass (uoff == nullptr): ucnt[i] = units of the group starting at
-// item i (0 elsewhere).  Emit pass: write them at uoff[i] and their sizes.
-__global__ void k_unit_walk(const int4 *__restrict__ items, int64_t n_items, int unit_points,
-                            const int *__restrict__ uoff, int *__restrict__ ucnt,
-                            int4 *__restrict__ units, int *__restrict__ sizes) {
+// pts[i] = point count of item i; first[g] = min item index of group g.
+__global__ void k_item_pts(const int4 *__restrict__ items, int64_t n_items, int ntiles,
+                           int *__restrict__ pts, int *__restrict__ first) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int4 first = items[i];
-        if (i > 0 && same_group(items[i - 1], first)) {
-            if (!uoff) ucnt[i] = 0;
-            continue;
-        }
-        int nu = 0;
-        int64_t j = i;
-        while (j < n_items && same_group(items[j], first)) {
-            const int64_t j0 = j;
-            int pts = 0;
-            while (j < n_items && same_group(items[j], first) && j - j0 < kUnitItems &&
-                   (j == j0 || pts + items[j].w <= unit_points)) {
-                pts += items[j].w;
-                ++j;
-            }
-            if (uoff) {
-                const int o = uoff[i] + nu;
-                units[o] = make_int4(first.x >> 16, first.y, (int)j0, (int)(j - j0));
-                sizes[o] = pts;
-            }
-            ++nu;
-        }
-        if (!uoff) ucnt[i] = nu;
+        const int4 it = items[i];
+        pts[i] = it.w;
+        if (i == 0 || group_key(items[i - 1], ntiles) != group_key(it, ntiles))
+            first[group_key(it, ntiles)] = (int)i;
+    }
+}
+
+// brk[i] = 1 where item i starts a unit (a new group, or a new point or item
+// bucket inside the group).
+__device__ __forceinline__ long long unit_bucket(int64_t i, const int4 *items, const int *pre,
+                                                 const int *first, int ntiles, int unit_points) {
+    const int g0 = first[group_key(items[i], ntiles)];
+    const long long pb = (pre[i] - pre[g0]) / unit_points;
+    const long long ib = (i - g0) / kUnitItems;
+    return pb * 1048576ll + ib;
+}
+
+__global__ void k_unit_breaks(const int4 *__restrict__ items, int64_t n_items, int ntiles,
+                              const int *__restrict__ pre, const int *__restrict__ first,
+                              int unit_points, int *__restrict__ brk) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int b = 1;
+        if (i > 0 && group_key(items[i - 1], ntiles) == group_key(items[i], ntiles))
+            b = unit_bucket(i - 1, items, pre, first, ntiles, unit_points) !=
+                unit_bucket(i, items, pre, first, ntiles, unit_points);
+        brk[i] = b;
+    }
+}
+
+// start[uid[i]] = i at each unit start (uid = exclusive scan of brk).
+__global__ void k_unit_starts(const int *__restrict__ brk, const int *__restrict__ uid,
+                              int64_t n_items, int *__restrict__ start) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (brk[i]) start[uid[i]] = (int)i;
+}
+
+// Unit u covers items start[u] .. start[u+1]-1 (or to the end).
+__global__ void k_unit_emit(const int4 *__restrict__ items, int64_t n_items,
+                            const int *__restrict__ start, const int *__restrict__ pre,
+                            const int *__restrict__ n_units, int4 *__restrict__ units,
+                            int *__restrict__ sizes) {
+    const int nu = *n_units;
+    const int total = pre[n_items - 1] + items[n_items - 1].w;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+        const int i0 = start[u];
+        const int i1 = u + 1 < nu ? start[u + 1] : (int)n_items;
+        units[u] = make_int4(items[i0].x >> 16, items[i0].y, i0, i1 - i0);
+        sizes[u] = (i1 < n_items ? pre[i1] : total) - pre[i0];
     }
 }
 
@@ -678,8 +719,11 @@ static void build_units(Plan &P, cudaStream_t s) {
     if (!P.d_units) P.d_units = P.alloc<int>(1);
     NLH_CUDA(cudaMemsetAsync(P.d_units, 0, sizeof(int), s));
     if (ni == 0) return;
-    int *ucnt = nullptr, *uoff = nullptr, *sums = nullptr, *sizes = nullptr, *hist = nullptr,
-        *off = nullptr;
+    const int nt = P.n / kTile, nt3 = nt * nt * nt;
+    const int64_t ngroups = (int64_t)P.L * nt3;
+    int *pts = nullptr, *pre = nullptr, *first = nullptr, *brk = nullptr, *uid = nullptr,
+        *sums = nullptr, *sizes = nullptr, *hist = nullptr, *off = nullptr, *tot = nullptr,
+        *start = nullptr;
     int4 *tmpu = nullptr;
     std::vector<void *> tmp;
     auto talloc = [&](auto **ptr, size_t bytes) {
@@ -687,19 +731,28 @@ static void build_units(Plan &P, cudaStream_t s) {
         tmp.push_back(*ptr);
     };
     try {
-        talloc(&ucnt, sizeof(int) * ni);
-        talloc(&uoff, sizeof(int) * ni);
+        talloc(&pts, sizeof(int) * ni);
+        talloc(&pre, sizeof(int) * ni);
+        talloc(&first, sizeof(int) * ngroups);
+        talloc(&brk, sizeof(int) * ni);
+        talloc(&uid, sizeof(int) * ni);
+        talloc(&start, sizeof(int) * ni);
         talloc(&sums, sizeof(int) * (div_up(ni, kScanTile) + 1));
         talloc(&sizes, sizeof(int) * ni);
         talloc(&tmpu, sizeof(int4) * ni);
         talloc(&hist, sizeof(int) * kSizeBins);
         talloc(&off, sizeof(int) * kSizeBins);
+        talloc(&tot, sizeof(int));
         const int gb = (int)std::min<int64_t>(div_up(ni, 256), 152 * 8);
-        k_unit_walk<<<gb, 256, 0, s>>>(P.items, ni, P.unit_points, nullptr, ucnt, nullptr,
-                                       nullptr);
+        k_item_pts<<<gb, 256, 0, s>>>(P.items, ni, nt3, pts, first);
         NLH_CHECK_LAUNCH();
-        exclusive_scan_dev(ucnt, uoff, ni, s, sums, P.d_units);
-        k_unit_walk<<<gb, 256, 0, s>>>(P.items, ni, P.unit_points, uoff, ucnt, tmpu, sizes);
+        exclusive_scan_dev(pts, pre, ni, s, sums, tot);
+        k_unit_breaks<<<gb, 256, 0, s>>>(P.items, ni, nt3, pre, first, P.unit_points, brk);
+        NLH_CHECK_LAUNCH();
+        exclusive_scan_dev(brk, uid, ni, s, sums, P.d_units);
+        k_unit_starts<<<gb, 256, 0, s>>>(brk, uid, ni, start);
+        NLH_CHECK_LAUNCH();
+        k_unit_emit<<<gb, 256, 0, s>>>(P.items, ni, start, pre, P.d_units, tmpu, sizes);
         NLH_CHECK_LAUNCH();
         NLH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * kSizeBins, s));
         k_size_hist<<<gb, 256, 0, s>>>(sizes, P.d_units, hist);
@@ -971,8 +1024,21 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         if (P.precision & 2) P.wts32 = P.alloc<float>((size_t)LN * rec32);
         if (P.precision & 4) P.wtsdf = P.alloc<float>((size_t)LN * 6 * P.W2);
         if (P.precision & 1) {
-            k_weights<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_coef, rec64, rec32, P.wts64,
-                                         P.wts32, P.wtsdf);
+            auto fp64 = [&](auto w2) {
+                constexpr int W = decltype(w2)::value;
+                k_weights<W><<<gb, 256, 0, s>>>(P.perm, u, N, L, K, d_coef, rec64, rec32, P.wts64,
+                                                P.wts32, P.wtsdf);
+            };
+            switch (P.W2) {
+                case 4: fp64(std::integral_constant<int, 4>()); break;
+                case 6: fp64(std::integral_constant<int, 6>()); break;
+                case 8: fp64(std::integral_constant<int, 8>()); break;
+                case 10: fp64(std::integral_constant<int, 10>()); break;
+                case 12: fp64(std::integral_constant<int, 12>()); break;
+                case 14: fp64(std::integral_constant<int, 14>()); break;
+                case 16: fp64(std::integral_constant<int, 16>()); break;
+                default: NLH_REQUIRE(false, "internal: stencil width %d", P.W2);
+            }
         } else {
             std::vector<float2> cdf(coef.size());
             for (size_t e = 0; e < coef.size(); ++e) {
@@ -984,8 +1050,21 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
             tmp.push_back(d_cdf);
             NLH_CUDA(cudaMemcpyAsync(d_cdf, cdf.data(), sizeof(float2) * cdf.size(),
                                      cudaMemcpyHostToDevice, s));
-            k_weights_df<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.m, K, d_cdf, rec32, P.wts32,
-                                            P.wtsdf);
+            auto dfw = [&](auto w2) {
+                constexpr int W = decltype(w2)::value;
+                k_weights_df<W><<<gb, 256, 0, s>>>(P.perm, u, N, L, K, d_cdf, rec32, P.wts32,
+                                                   P.wtsdf);
+            };
+            switch (P.W2) {
+                case 4: dfw(std::integral_constant<int, 4>()); break;
+                case 6: dfw(std::integral_constant<int, 6>()); break;
+                case 8: dfw(std::integral_constant<int, 8>()); break;
+                case 10: dfw(std::integral_constant<int, 10>()); break;
+                case 12: dfw(std::integral_constant<int, 12>()); break;
+                case 14: dfw(std::integral_constant<int, 14>()); break;
+                case 16: dfw(std::integral_constant<int, 16>()); break;
+                default: NLH_REQUIRE(false, "internal: stencil width %d", P.W2);
+            }
         }
         NLH_CHECK_LAUNCH();
         P.occupied = occ;
