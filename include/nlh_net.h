@@ -113,6 +113,23 @@ nlh_status nlh_net_loss_grad(nlh_net net, const nlh_net_batch *batch, double *lo
 nlh_status nlh_net_adam(nlh_net net, double lr, double beta1, double beta2, double eps,
                         void *stream);
 
+/* Engine of the 3x3 forward and input-gradient convolutions (implicit
+ * GEMMs, bf16 operands, f32 accumulation):
+ *   NLH_NET_ENGINE_TCGEN05  (default) 5th-generation tensor cores, the
+ *                           accumulator in tensor memory;
+ *   NLH_NET_ENGINE_MMA_SYNC warp-level mma.sync (register accumulators).
+ * Both sum the same products per 32-channel chunk; results agree to f32
+ * rounding order.  Errors: NLH_ERR_ARG. */
+enum { NLH_NET_ENGINE_MMA_SYNC = 0, NLH_NET_ENGINE_TCGEN05 = 1 };
+nlh_status nlh_net_set_engine(nlh_net net, int engine);
+nlh_status nlh_net_get_engine(nlh_net net, int *engine);
+
+/* Synchronise `stream` and report NLH_ERR_TIMEOUT if a bounded wait inside
+ * a tensor-core kernel gave up since the last check (the outputs of the
+ * calls in between are then invalid; the word is cleared).  The synchronous
+ * calls (get_params, get_grads, loss_grad with a loss pointer) check too. */
+nlh_status nlh_net_check(nlh_net net, void *stream);
+
 /* Free the network (NULL is a no-op). */
 nlh_status nlh_net_destroy(nlh_net net);
 

@@ -22,6 +22,11 @@
 //                    same GEMM with the taps mirrored (input = out - offset)
 //                    and Wd, f32 out, optionally split into two tensors at a
 //                    channel boundary (the two parts of a concatenation).
+//   k_conv3x3_tc<BN> the same forward / input-gradient GEMM on tcgen05 (the
+//                    default engine): M runs over the zero-padded image's
+//                    pixels, so one staged band of 130 pixels serves the
+//                    three horizontal taps of a row offset; the accumulator
+//                    is in tensor memory, read back with tcgen05.ld.
 //   k_conv3x3_wgrad  weight gradient dW[co][tap][ci] = sum_p dZ[p][co]
 //                    X[p + off(tap)][ci]: M = cout, N = 32 input channels of
 //                    one tap, K = pixels split across CTAs, both operands
@@ -31,9 +36,10 @@
 //                    average-pool backward from the coarser level, upsample
 //                    backward from the finer level), masked by y > 0, to
 //                    bf16, with the bias gradient reduced on the fly.
-//   k_input_planes, k_avgpool2, k_sample_stats, k_head_fwd, k_loss_grad,
+//   k_input_planes, k_avgpool2, k_stats_partial / k_stats_final, k_head_fwd, k_loss_grad,
 //   k_head_bwd, k_adam, k_pack_weights, k_sub.
 #include "common.cuh"
+#include "async_copy.cuh"
 #include "../../include/nlh_net.h"
 
 #include <cuda_bf16.h>
@@ -132,6 +138,7 @@ __device__ __forceinline__ const bf16 *src_ptr(const Src &s, int b, int y, int x
 struct ConvArgs {
     Src src;
     const bf16 *w;      // [n][9][cin], cin = c1 + c2
+    const bf16 *wt;     // the same weights as [9][cin / 32][4][n][8] (tcgen05 engine)
     const float *bias;  // [n] or nullptr
     int relu;
     int sign;           // +1: input pixel = output + offset; -1: output - offset
@@ -272,6 +279,267 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a) {
             }
         }
     }
+}
+
+// ------------------------------------- forward / input gradient on tcgen05
+// The same convolution as an implicit GEMM on the 5th-generation tensor
+// cores, with the M dimension running over the pixels of the zero-padded
+// image (rows of W + 2: one zero column on each side; the two padding
+// outputs of each row are computed and dropped).  In that indexing the
+// three horizontal taps of one row offset dy read the same 130 consecutive
+// padded pixels, shifted by 0, 1, 2: a CTA stages one such band per
+// (dy, 32-channel block) with cp.async (zero-filled outside the image) and
+// issues 3 taps x 2 (K = 16) tcgen05.mma (kind::f16, bf16 x bf16 -> f32)
+// from it, the tap shift being a 16-byte offset of the operand's start
+// address.  The weights come pre-packed in that operand layout (one
+// contiguous run of BN rows per tap and K group), fetched by one thread as
+// 12 bulk copies per stage completing on the stage's weight mbarrier.
+// Operands sit in the no-swizzle K-major canonical layout: rows of 8
+// channels (16 B) consecutive within a K group, 8-row groups 128 B apart
+// (SBO), K groups one band (or one weight tile) apart (LBO).  One
+// thread issues the MMAs and commits each stage to its mbarrier, which
+// releases the stage for the next refill; the 128 x BN f32 accumulator
+// lives in tensor memory (BN columns per CTA) and the epilogue reads it
+// with tcgen05.ld, one pixel per thread.  Every wait is bounded (the
+// kernel then records NLH_ERR_TIMEOUT, skips its stores and still frees
+// its tensor memory).
+// Two stages (load of chunk k + 1 overlapping the MMAs of chunk k): the
+// small footprint keeps 3 (BN 128) to 7 (BN 32) CTAs on an SM, which hides
+// the load latency better than a deeper pipeline with fewer CTAs (measured:
+// 2 stages 1.23 ms, 3 stages 1.35 ms, 4 stages 1.78 ms for the forward pass
+// of 16 images of 256 x 256).
+constexpr int kTcStages = 2;
+constexpr int kBandRows = kBM + 2;  // 128 outputs + one halo pixel each side
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < kMbarSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bytes of one pipeline stage: the band (4 K groups of 130 rows) and the
+// three taps' weight tiles (each 4 K groups of BN rows).
+template <int BN> struct TcTile {
+    static constexpr int A_BYTES = 4 * kBandRows * 16;  // 8320
+    static constexpr int B_TAP = BN * kBK * 2;
+    static constexpr int STAGE = A_BYTES + 3 * B_TAP;
+    static constexpr int SMEM = kTcStages * STAGE + 128;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv3x3_tc(ConvArgs a, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using T = TcTile<BN>;
+    constexpr uint32_t KA = kBandRows * 16, KB = (BN / 8) * 128;  // K-group strides
+    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(kBM >> 4) << 24);
+    // bars: MMA commits per stage; wbars: weight bulk copies per stage
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTcStages * T::STAGE);
+    uint64_t *wbars = bars + kTcStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(wbars + kTcStages);
+    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Wp = a.W + 2;
+    const int64_t Pp = (int64_t)a.B * a.H * Wp;  // padded pixels
+    const int64_t q0 = (int64_t)blockIdx.x * kBM;
+    const int n0 = blockIdx.y * BN;
+    const int cin = a.src.c1 + a.src.c2;
+    const int kcb = cin / kBK;
+    const int nk = 3 * kcb;  // chunks: (band dy, channel block)
+
+    if (tid == 0) {
+        for (int st = 0; st < kTcStages; ++st) {
+            mbar_init(bars + st, 1);
+            mbar_init(wbars + st, 1);
+        }
+        mbar_fence_init();
+        *s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    // band rows of this thread: i = tid and (tid < 2) i = 128 + tid; row i
+    // holds the padded pixel q0 - 1 + i shifted by the band's dy
+    int rb[2], ry[2], rx[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t sidx = q0 - 1 + tid + h * kBM;
+        rb[h] = -1;
+        if (sidx >= 0 && sidx < Pp && (h == 0 || tid < 2)) {
+            const int64_t r = sidx / Wp;
+            const int xp = (int)(sidx - r * Wp);
+            rb[h] = (int)(r / a.H);
+            ry[h] = (int)(r - (int64_t)rb[h] * a.H);
+            rx[h] = xp - 1;  // -1 and W are the padding columns
+        }
+    }
+    int w_issued = 0;  // thread 0: chunks whose weight copies were issued
+    auto load = [&](int stage, int kc) {
+        const int band = kc / kcb, cb = kc - band * kcb;
+        const int dy = band - 1;  // input row offset of the band
+        const int c0 = cb * kBK;
+        const uint32_t sa = smem_u32(smem + stage * T::STAGE);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && tid >= 2) break;
+            const int i = tid + h * kBM;
+            const bf16 *p = rb[h] >= 0 ? src_ptr(a.src, rb[h], ry[h] + dy, rx[h], a.H, a.W, c0)
+                                       : nullptr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cp_async16(sa + q * KA + i * 16, p ? p + 8 * q : a.w, p != nullptr);
+        }
+        // weights of the band's three taps (input offset (dy, dx) is tap
+        // (sign dy + 1) * 3 + (sign dx + 1)): the packed layout holds each
+        // (tap, channel block, K group) as n rows of 16 B, so the BN rows
+        // of this CTA are one contiguous bulk copy, 12 per chunk
+        if (tid == 0) {
+            ++w_issued;
+            unsigned char *dst = smem + stage * T::STAGE + T::A_BYTES;
+            mbar_arrive_expect_tx(wbars + stage, 12u * BN * 16u);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int tap = (a.sign * dy + 1) * 3 + (a.sign * (t - 1) + 1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bf16 *wp = a.wt + ((((int64_t)tap * kcb + cb) * 4 + q) * a.n + n0) * 8;
+                    bulk_copy_g2s(dst + t * T::B_TAP + q * KB, wp, BN * 16, wbars + stage);
+                }
+            }
+        }
+    };
+
+    bool ok = true;
+    int w_waited = 0;  // thread 0: chunks whose weight copies have landed
+#pragma unroll
+    for (int st = 0; st < kTcStages - 1; ++st) {
+        if (st < nk) load(st, st);
+        cp_commit();
+    }
+    for (int kc = 0; kc < nk; ++kc) {
+        const int stage = kc % kTcStages;
+        cp_wait<kTcStages - 2>();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && ok) {
+            if (tc_wait(wbars + stage, (kc / kTcStages) & 1))
+                w_waited = kc + 1;
+            else
+                ok = false;
+        }
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + stage * T::STAGE);
+            const uint32_t sb = sa + T::A_BYTES;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    // output row m reads band row m + t (tap dx = t - 1)
+                    const uint64_t da = tc_desc(sa + ks * 2 * KA + t * 16, KA, 128);
+                    const uint64_t db = tc_desc(sb + t * T::B_TAP + ks * 2 * KB, KB, 128);
+                    const uint32_t acc = (kc > 0 || t > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(bars + stage))
+                : "memory");
+        }
+        // refill the stage of chunk kc - 1 once its MMAs have read it
+        const int nx = kc + kTcStages - 1;
+        if (nx < nk) {
+            if (kc >= 1 && ok) {
+                const int c = kc - 1;
+                if (!tc_wait(bars + (c % kTcStages), (c / kTcStages) & 1)) ok = false;
+            }
+            if (ok) load(nx % kTcStages, nx);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    // drain: the commits not yet waited for (the last chunk's covers every
+    // MMA issued before it; the others are consumed so no arrival is left)
+    for (int c = nk - kTcStages > 0 ? nk - kTcStages : 0; c < nk && ok; ++c)
+        if (!tc_wait(bars + (c % kTcStages), (c / kTcStages) & 1)) ok = false;
+    if (tid == 0 && !ok) {
+        // after a failed wait: let the weight copies still in flight land
+        // (bounded) before the shared memory is released
+        for (int c = w_waited; c < w_issued; ++c)
+            if (!tc_wait(wbars + (c % kTcStages), (c / kTcStages) & 1)) break;
+    }
+    if (!ok) atomicExch(s_fail, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool failed = *s_fail != 0;
+    if (failed && tid == 0 && err) atomicExch(err, (int)NLH_ERR_TIMEOUT);
+
+    // epilogue: accumulator row (= padded pixel q0 + 32 warp + lane) per thread
+    const int64_t qm = q0 + warp * 32 + lane;
+    int64_t mm = -1;  // unpadded output pixel, or -1 (padding column / past the end)
+    if (qm < Pp) {
+        const int64_t r = qm / Wp;
+        const int xp = (int)(qm - r * Wp);
+        if (xp >= 1 && xp <= a.W) mm = r * a.W + (xp - 1);
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (failed || mm < 0) continue;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            v[j] = __uint_as_float(r[j]);
+            if (a.bias) v[j] += a.bias[n0 + c0 + j];
+            if (a.relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        const int n = n0 + c0;
+        if (a.ybf) {
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16_rn(v[j]);
+            uint4 *dst = reinterpret_cast<uint4 *>(a.ybf + mm * a.n + n);
+            dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+            dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+        } else {
+            float *dst = n < a.n1 ? a.y1 + mm * a.n1 + n : a.y2 + mm * (a.n - a.n1) + (n - a.n1);
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
 // ----------------------------------------------------------- weight gradient
@@ -575,29 +843,52 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
     return r;
 }
 
+// Partial sums of image b over the slice blockIdx.x of gridDim.x:
+// part[3 (b G + g) + {0, 1, 2}] = sum (f - K), sum (f - K)^2, sum e0^2, with
+// the shift K = f[b][0] (so that the variance below does not cancel).
+constexpr int kStatsMaxSlices = 64;
 __global__ void __launch_bounds__(kElemThreads)
-k_sample_stats(const double *__restrict__ f, const double *__restrict__ e0, int HW, Scalars sc,
-               double *__restrict__ stats) {
+k_stats_partial(const double *__restrict__ f, const double *__restrict__ e0, int HW,
+                double *__restrict__ part) {
     __shared__ double sh[kElemThreads];
-    const int b = blockIdx.x;
+    const int b = blockIdx.y, G = gridDim.x;
     const double *fb = f + (int64_t)b * HW;
-    double a = 0.0;
-    for (int i = threadIdx.x; i < HW; i += blockDim.x) a += fb[i];
-    const double mean = block_sum_d(a, sh) / HW;
-    a = 0.0;
-    double e = 0.0;
-    for (int i = threadIdx.x; i < HW; i += blockDim.x) {
-        const double d = sc.alpha[b] * (fb[i] - mean);
-        a += d * d;
-        if (e0) e += e0[(int64_t)b * HW + i] * e0[(int64_t)b * HW + i];
+    const double K = fb[0];
+    double s1 = 0.0, s2 = 0.0, se = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += G * blockDim.x) {
+        const double d = fb[i] - K;
+        s1 += d;
+        s2 = fma(d, d, s2);
+        if (e0) se = fma(e0[(int64_t)b * HW + i], e0[(int64_t)b * HW + i], se);
     }
-    const double nu = block_sum_d(a, sh);
-    const double ne = block_sum_d(e, sh);
+    s1 = block_sum_d(s1, sh);
+    s2 = block_sum_d(s2, sh);
+    se = block_sum_d(se, sh);
     if (threadIdx.x == 0) {
-        stats[3 * b] = mean;
-        stats[3 * b + 1] = nu > 0.0 ? nu : 1e-300;
-        stats[3 * b + 2] = ne > 0.0 ? ne : 1e-300;
+        double *o = part + 3 * ((int64_t)b * G + blockIdx.x);
+        o[0] = s1, o[1] = s2, o[2] = se;
     }
+}
+
+// One block per image sums the G partials in a fixed order:
+// stats[3b] = mean(f) = K + S1 / HW,
+// stats[3b+1] = ||alpha (f - mean f)||^2 = alpha^2 (S2 - S1^2 / HW),
+// stats[3b+2] = ||e0||^2 (the residual of the deflated start and the norm
+// of the preconditioner term's target).
+__global__ void k_stats_final(const double *__restrict__ f, const double *__restrict__ part, int G,
+                              int HW, Scalars sc, double *__restrict__ stats) {
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double s1 = 0.0, s2 = 0.0, se = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double *o = part + 3 * ((int64_t)b * G + g);
+        s1 += o[0], s2 += o[1], se += o[2];
+    }
+    const double mean = f[(int64_t)b * HW] + s1 / HW;
+    const double nu = sc.alpha[b] * sc.alpha[b] * (s2 - s1 * s1 / HW);
+    stats[3 * b] = mean;
+    stats[3 * b + 1] = nu > 0.0 ? nu : 1e-300;
+    stats[3 * b + 2] = se > 0.0 ? se : 1e-300;
 }
 
 // Loss and its gradient with respect to the head outputs (see nlh_net.h).
@@ -715,9 +1006,20 @@ struct PackTable {
     int64_t woff[16], wfoff[16], wdoff[16], start[17];
 };
 
-// theta -> Wf[cout][9][cinp] and Wd[cinp][9][cout] (bf16; zero padding).
+// theta -> Wf[cout][9][cinp] and Wd[cinp][9][cout] (bf16; zero padding),
+// and both again in the tcgen05 layout.
+// The tcgen05 engine's copies: a GEMM weight w[n][9][k] (forward: n =
+// cout, k = cinp; input gradient: n = cinp, k = cout) as
+// [9][k / 32][4][n][8], element (n, tap, kk) at
+// ((tap (k / 32) + kk / 32) 4 + (kk % 32) / 8) n 8 + n 8 + kk % 8.
+__device__ __forceinline__ int64_t tc_pack_index(int n, int tap, int kk, int N, int K) {
+    return (((int64_t)tap * (K / 32) + kk / 32) * 4 + (kk % 32) / 8) * N * 8 + (int64_t)n * 8 +
+           kk % 8;
+}
+
 __global__ void k_pack_weights(const float *__restrict__ theta, PackTable t, bf16 *__restrict__ wf,
-                               bf16 *__restrict__ wd) {
+                               bf16 *__restrict__ wd, bf16 *__restrict__ wtf,
+                               bf16 *__restrict__ wtd) {
     const int64_t total = t.start[t.nl];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -733,6 +1035,8 @@ __global__ void k_pack_weights(const float *__restrict__ theta, PackTable t, bf1
         const bf16 b = __float2bfloat16_rn(val);
         wf[t.wfoff[l] + loc] = b;
         wd[t.wdoff[l] + ((int64_t)ci * 9 + tap) * t.cout[l] + co] = b;
+        wtf[t.wfoff[l] + tc_pack_index(co, tap, ci, t.cout[l], cinp)] = b;
+        wtd[t.wdoff[l] + tc_pack_index(ci, tap, co, cinp, t.cout[l])] = b;
     }
 }
 
@@ -777,9 +1081,11 @@ struct nlh_net_s {
     std::vector<LayerDesc> layers;  // 3x3 layers then the head
     int64_t n_params = 0, wf_total = 0;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wf = nullptr, *wd = nullptr;
+    bf16 *wf = nullptr, *wd = nullptr, *wtf = nullptr, *wtd = nullptr;
     bool packed = false;
     int adam_t = 0;
+    int engine = NLH_NET_ENGINE_TCGEN05;
+    int *err = nullptr;  // device error word of the bounded tensor-core waits
     // workspace of the current batch shape
     int B = 0, H = 0, W = 0;
     bool has_grad_ws = false;
@@ -787,7 +1093,7 @@ struct nlh_net_s {
     std::vector<Level> lv;
     float2 *o = nullptr, *dout = nullptr;
     float *T1 = nullptr, *T2 = nullptr;
-    double *stats = nullptr, *loss = nullptr;
+    double *stats = nullptr, *stats_part = nullptr, *loss = nullptr;
     std::vector<void *> ws;
     netk::PackTable pack{};
 
@@ -800,6 +1106,9 @@ struct nlh_net_s {
         cudaFree(v);
         cudaFree(wf);
         cudaFree(wd);
+        cudaFree(wtf);
+        cudaFree(wtd);
+        cudaFree(err);
     }
     void free_ws() {
         for (void *p : ws) cudaFree(p);
@@ -841,6 +1150,7 @@ static void net_ensure_ws(nlh_net_s &N, int B, int H, int W, bool grad, cudaStre
     }
     N.o = N.wsalloc<float2>(P0);
     N.stats = N.wsalloc<double>(3 * netk::kMaxBatch);
+    N.stats_part = N.wsalloc<double>(3 * netk::kMaxBatch * netk::kStatsMaxSlices);
     if (grad) {
         N.dout = N.wsalloc<float2>(P0);
         N.dz = N.wsalloc<bf16>(P0 * N.ch(0));
@@ -858,9 +1168,44 @@ static void net_ensure_ws(nlh_net_s &N, int B, int H, int W, bool grad, cudaStre
 
 static void net_pack(nlh_net_s &N, cudaStream_t s) {
     if (N.packed) return;
-    netk::k_pack_weights<<<grid_for(N.wf_total, 256), 256, 0, s>>>(N.theta, N.pack, N.wf, N.wd);
+    netk::k_pack_weights<<<grid_for(N.wf_total, 256), 256, 0, s>>>(N.theta, N.pack, N.wf, N.wd,
+                                                                  N.wtf, N.wtd);
     NLH_CHECK_LAUNCH();
     N.packed = true;
+}
+
+// Launch the forward / input-gradient implicit GEMM a with the net's
+// engine; BN (output channels per CTA) is the widest of 128, 64, 32 that
+// divides n, does not straddle the split n1 and still gives two CTAs per SM.
+static void launch_conv(nlh_net_s &N, const netk::ConvArgs &a, int n1, cudaStream_t s) {
+    const int64_t P = (int64_t)a.B * a.H * a.W;
+    const int mt = (int)((P + netk::kBM - 1) / netk::kBM);
+    auto launch = [&](auto bn) {
+        constexpr int BN = decltype(bn)::value;
+        if (N.engine == NLH_NET_ENGINE_TCGEN05) {
+            // M runs over the padded pixels; tensor memory: BN columns per
+            // CTA, and the shared-memory footprint keeps at most 512 / BN
+            // CTAs on an SM, so allocations never wait
+            const int64_t Pp = (int64_t)a.B * a.H * (a.W + 2);
+            const int mtp = (int)((Pp + netk::kBM - 1) / netk::kBM);
+            const int smem = netk::TcTile<BN>::SMEM;
+            NLH_CUDA(cudaFuncSetAttribute(netk::k_conv3x3_tc<BN>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            netk::k_conv3x3_tc<BN><<<dim3(mtp, a.n / BN), netk::kConvThreads, smem, s>>>(a, N.err);
+        } else {
+            const int smem = netk::kStages * (netk::kBM + BN) * netk::kBK * 2;
+            NLH_CUDA(cudaFuncSetAttribute(netk::k_conv3x3<BN>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            netk::k_conv3x3<BN><<<dim3(mt, a.n / BN), netk::kConvThreads, smem, s>>>(a);
+        }
+        NLH_CHECK_LAUNCH();
+    };
+    if (a.n % 128 == 0 && n1 % 128 == 0 && (int64_t)mt * (a.n / 128) >= 2 * kSMs)
+        launch(std::integral_constant<int, 128>());
+    else if (a.n % 64 == 0 && n1 % 64 == 0 && (int64_t)mt * (a.n / 64) >= 2 * kSMs)
+        launch(std::integral_constant<int, 64>());
+    else
+        launch(std::integral_constant<int, 32>());
 }
 
 // y = conv3x3(src) with layer li's weights: forward (bias, ReLU, bf16 out).
@@ -871,28 +1216,14 @@ static void conv_fwd(nlh_net_s &N, int li, netk::Src src, int B, int H, int W, b
     netk::ConvArgs a{};
     a.src = src;
     a.w = N.wf + L.wfoff;
+    a.wt = N.wtf + L.wfoff;
     a.bias = N.theta + L.boff;
     a.relu = 1;
     a.sign = 1;
     a.B = B, a.H = H, a.W = W;
     a.n = L.cout;
     a.ybf = y;
-    const int64_t P = (int64_t)B * H * W;
-    const int mt = (int)((P + netk::kBM - 1) / netk::kBM);
-    auto launch = [&](auto bn) {
-        constexpr int BN = decltype(bn)::value;
-        const int smem = netk::kStages * (netk::kBM + BN) * netk::kBK * 2;
-        NLH_CUDA(cudaFuncSetAttribute(netk::k_conv3x3<BN>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        netk::k_conv3x3<BN><<<dim3(mt, a.n / BN), netk::kConvThreads, smem, s>>>(a);
-        NLH_CHECK_LAUNCH();
-    };
-    if (a.n % 128 == 0 && (int64_t)mt * (a.n / 128) >= 2 * kSMs)
-        launch(std::integral_constant<int, 128>());
-    else if (a.n % 64 == 0 && (int64_t)mt * (a.n / 64) >= 2 * kSMs)
-        launch(std::integral_constant<int, 64>());
-    else
-        launch(std::integral_constant<int, 32>());
+    launch_conv(N, a, 0, s);
 }
 
 // Input gradient of layer li: dz [P][cout] -> float [P][cinp], split at n1.
@@ -902,6 +1233,7 @@ static void conv_dgrad(nlh_net_s &N, int li, const bf16 *dz, int B, int H, int W
     netk::ConvArgs a{};
     a.src = netk::Src{dz, L.cout, 0, nullptr, 0};
     a.w = N.wd + L.wdoff;
+    a.wt = N.wtd + L.wdoff;
     a.bias = nullptr;
     a.relu = 0;
     a.sign = -1;
@@ -911,23 +1243,7 @@ static void conv_dgrad(nlh_net_s &N, int li, const bf16 *dz, int B, int H, int W
     a.y1 = y1;
     a.n1 = n1;
     a.y2 = y2;
-    const int64_t P = (int64_t)B * H * W;
-    const int mt = (int)((P + netk::kBM - 1) / netk::kBM);
-    auto launch = [&](auto bn) {
-        constexpr int BN = decltype(bn)::value;
-        const int smem = netk::kStages * (netk::kBM + BN) * netk::kBK * 2;
-        NLH_CUDA(cudaFuncSetAttribute(netk::k_conv3x3<BN>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        netk::k_conv3x3<BN><<<dim3(mt, a.n / BN), netk::kConvThreads, smem, s>>>(a);
-        NLH_CHECK_LAUNCH();
-    };
-    // BN must not straddle the split n1 (multiples of 32 always work)
-    if (a.n % 128 == 0 && n1 % 128 == 0 && (int64_t)mt * (a.n / 128) >= 2 * kSMs)
-        launch(std::integral_constant<int, 128>());
-    else if (a.n % 64 == 0 && n1 % 64 == 0 && (int64_t)mt * (a.n / 64) >= 2 * kSMs)
-        launch(std::integral_constant<int, 64>());
-    else
-        launch(std::integral_constant<int, 32>());
+    launch_conv(N, a, n1, s);
 }
 
 static void conv_wgrad(nlh_net_s &N, int li, netk::Src src, const bf16 *dz, int B, int H, int W,
@@ -1021,9 +1337,17 @@ static void net_forward(nlh_net_s &N, const nlh_net_batch &b, double *u0, double
         x = L.D;
         cx = N.ch(l);
     }
-    netk::k_sample_stats<<<B, netk::kElemThreads, 0, s>>>(
-        b.f, e0_for_stats, H * W, make_scalars(b), N.stats);
-    NLH_CHECK_LAUNCH();
+    {
+        // about two blocks per SM over the batch, at least 2048 pixels each
+        const int HW = H * W;
+        int G = std::min<int>((2 * kSMs + B - 1) / B, (HW + 2047) / 2048);
+        G = std::max(1, std::min(G, netk::kStatsMaxSlices));
+        netk::k_stats_partial<<<dim3(G, B), netk::kElemThreads, 0, s>>>(b.f, e0_for_stats, HW,
+                                                                        N.stats_part);
+        NLH_CHECK_LAUNCH();
+        netk::k_stats_final<<<B, 32, 0, s>>>(b.f, N.stats_part, G, HW, make_scalars(b), N.stats);
+        NLH_CHECK_LAUNCH();
+    }
     const LayerDesc &Hd = N.layers.back();
     if (N.base == 32)
         netk::k_head_fwd<32><<<grid_for(P0, 256), 256, 0, s>>>(x, P0, H * W, N.theta + Hd.woff,
@@ -1090,6 +1414,18 @@ static nlh_net_s *checked(nlh_net net) {
     return net;
 }
 
+// After a synchronisation: throw NLH_ERR_TIMEOUT (and clear the word) if a
+// tensor-core wait gave up since the last check.
+static void take_error(nlh_net_s &N) {
+    int e = 0;
+    NLH_CUDA(cudaMemcpy(&e, N.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        NLH_CUDA(cudaMemset(N.err, 0, sizeof(int)));
+        set_error("net: a bounded tensor-core wait gave up; results of the call are invalid");
+        throw Failure{NLH_ERR_TIMEOUT};
+    }
+}
+
 extern "C" {
 
 nlh_status nlh_net_create(int base, int levels, nlh_net *out) {
@@ -1144,10 +1480,14 @@ nlh_status nlh_net_create(int base, int levels, nlh_net *out) {
         NLH_CUDA(cudaMalloc(&N->v, sizeof(float) * N->n_params));
         NLH_CUDA(cudaMalloc(&N->wf, sizeof(bf16) * N->wf_total));
         NLH_CUDA(cudaMalloc(&N->wd, sizeof(bf16) * N->wf_total));
+        NLH_CUDA(cudaMalloc(&N->wtf, sizeof(bf16) * N->wf_total));
+        NLH_CUDA(cudaMalloc(&N->wtd, sizeof(bf16) * N->wf_total));
         NLH_CUDA(cudaMemset(N->theta, 0, sizeof(float) * N->n_params));
         NLH_CUDA(cudaMemset(N->grad, 0, sizeof(float) * N->n_params));
         NLH_CUDA(cudaMemset(N->m, 0, sizeof(float) * N->n_params));
         NLH_CUDA(cudaMemset(N->v, 0, sizeof(float) * N->n_params));
+        NLH_CUDA(cudaMalloc(&N->err, sizeof(int)));
+        NLH_CUDA(cudaMemset(N->err, 0, sizeof(int)));
         *out = N;
         return NLH_OK;
     } catch (Failure &f) {
@@ -1207,6 +1547,7 @@ static nlh_status copy_out(nlh_net net, bool grads, float *dst, int64_t count) {
         NLH_REQUIRE(dst && count == N->n_params, "nlh_net_get_%s: expected %lld floats",
                     grads ? "grads" : "params", (long long)N->n_params);
         NLH_CUDA(cudaDeviceSynchronize());
+        take_error(*N);
         NLH_CUDA(cudaMemcpy(dst, grads ? N->grad : N->theta, sizeof(float) * count,
                             cudaMemcpyDeviceToHost));
         return NLH_OK;
@@ -1284,6 +1625,7 @@ nlh_status nlh_net_loss_grad(nlh_net net, const nlh_net_batch *batch, double *lo
         if (loss) {
             NLH_CUDA(cudaMemcpyAsync(loss, N->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
             NLH_CUDA(cudaStreamSynchronize(s));
+            take_error(*N);
         }
         return NLH_OK;
     } catch (Failure &f) {
@@ -1308,6 +1650,43 @@ nlh_status nlh_net_adam(nlh_net net, double lr, double beta1, double beta2, doub
             (float)c2);
         NLH_CHECK_LAUNCH();
         N->packed = false;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_net_set_engine(nlh_net net, int engine) {
+    clear_error();
+    try {
+        nlh_net_s *N = checked(net);
+        NLH_REQUIRE(engine == NLH_NET_ENGINE_MMA_SYNC || engine == NLH_NET_ENGINE_TCGEN05,
+                    "nlh_net_set_engine: engine must be 0 (mma.sync) or 1 (tcgen05)");
+        N->engine = engine;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_net_get_engine(nlh_net net, int *engine) {
+    clear_error();
+    try {
+        nlh_net_s *N = checked(net);
+        NLH_REQUIRE(engine, "nlh_net_get_engine: engine is NULL");
+        *engine = N->engine;
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_net_check(nlh_net net, void *stream) {
+    clear_error();
+    try {
+        nlh_net_s *N = checked(net);
+        NLH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        take_error(*N);
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;

@@ -114,6 +114,9 @@ SIGNATURES = {
                                     C.c_void_p]),
     "nlh_net_adam": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                C.c_void_p]),
+    "nlh_net_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
+    "nlh_net_get_engine": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "nlh_net_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nlh_net_destroy": (C.c_int, [C.c_void_p]),
     "nlh_bilevel_misfit": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_double), C.c_void_p]),
@@ -377,6 +380,23 @@ class Net:
             a, b, k = C.c_int(), C.c_int(), C.c_int()
             _check(load().nlh_net_layer(h, i, C.byref(a), C.byref(b), C.byref(k)))
             self.layers.append((a.value, b.value, k.value))
+
+    ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
+
+    @property
+    def engine(self) -> int:
+        """Engine of the 3x3 convolutions: 1 = tcgen05 (default), 0 = mma.sync."""
+        e = C.c_int()
+        _check(load().nlh_net_get_engine(self._h, C.byref(e)))
+        return e.value
+
+    @engine.setter
+    def engine(self, value: int) -> None:
+        _check(load().nlh_net_set_engine(self._h, int(value)))
+
+    def check(self, stream=None) -> None:
+        """Synchronise and raise if a bounded tensor-core wait gave up."""
+        _check(load().nlh_net_check(self._h, _stream_ptr(stream)))
 
     def shapes(self):
         """(cout, k, cin) per layer, the order of the parameter vector."""
