@@ -232,6 +232,17 @@ void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Reflect padding of the patch features (Sec. 5): index -1 maps to 1 and
+// n to n - 2 (repeatedly, for radii beyond the image).
+__device__ __forceinline__ int reflect_index(int i, int n) {
+    if (n == 1) return 0;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * (n - 1) - i;
+    }
+    return i;
+}
+
 // Values per padded weight record (a multiple of 16 bytes).
 inline int record_len(int W2, int elem_bytes) {
     return ((3 * W2 * elem_bytes + 15) / 16) * 16 / elem_bytes;

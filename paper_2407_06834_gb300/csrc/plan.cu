@@ -96,14 +96,6 @@ void retain_pool_memory() {
 }
 
 // ------------------------------------------------------------------ features
-__device__ __forceinline__ int reflect_index(int i, int n) {
-    if (n == 1) return 0;
-    while (i < 0 || i >= n) {
-        if (i < 0) i = -i;
-        if (i >= n) i = 2 * (n - 1) - i;
-    }
-    return i;
-}
 
 // Patch features (Sec. 5): one thread per (pixel, patch dim).
 __global__ void k_patch_features(const double *__restrict__ img, int n1, int n2,

@@ -122,6 +122,8 @@ SIGNATURES = {
                                      C.POINTER(C.c_double), C.c_void_p]),
     "nlh_bilevel_gradient_term": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.POINTER(C.c_double), C.c_void_p]),
+    "nlh_mis_windows": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
@@ -176,6 +178,14 @@ def _stream_ptr(stream=None) -> int:
     return int(st.cuda_stream)
 
 
+def _iptr(t) -> int:
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous int32 CUDA tensor")
+    return int(t.data_ptr())
+
+
 def _dptr(t, n: Optional[int] = None) -> int:
     torch = _torch()
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -195,6 +205,28 @@ def patch_features(image, radius: int, pad: str = "reflect", stream=None):
     _check(load().nlh_patch_features(_dptr(image), n1, n2, radius, 1 if pad == "reflect" else 0,
                                      _dptr(out), _stream_ptr(stream)))
     return out
+
+
+def mis_windows(image, radius: int, pad: str = "reflect", bins: int = 64, want_counts=False,
+                stream=None):
+    """Feature windows ranked by mutual information (include/nlh_mis.h).
+
+    Returns (mis, windows, counts): mis a CUDA float64 tensor of the D
+    scores, windows an int32 (L, 3) host array for Plan, counts the CUDA
+    int32 (D, bins, bins) joint histograms or None."""
+    torch = _torch()
+    n1, n2 = image.shape
+    D = (2 * radius + 1) ** 2
+    L = -(-D // 3)
+    mis = torch.empty(D, dtype=torch.float64, device=image.device)
+    win = torch.empty((L, 3), dtype=torch.int32, device=image.device)
+    cnt = (torch.empty((D, bins, bins), dtype=torch.int32, device=image.device)
+           if want_counts else None)
+    _check(load().nlh_mis_windows(_dptr(image), n1, n2, int(radius),
+                                  1 if pad == "reflect" else 0, int(bins), _dptr(mis),
+                                  _iptr(win), None if cnt is None else _iptr(cnt),
+                                  _stream_ptr(stream)))
+    return mis, win.cpu().numpy(), cnt
 
 
 @dataclass
