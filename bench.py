@@ -72,6 +72,14 @@ def parse():
                     help="batched bilevel sweep: 64 (sigma, alpha) solves on 8 uneven images")
     ap.add_argument("--matvec-case", action="store_true",
                     help="profiling case: one plan, then 2 matvecs per NFFT precision; no JSON")
+    ap.add_argument("--net-case", action="store_true",
+                    help="profiling case: 2 x (forward + loss/gradient) of the network on 16 "
+                         "images of 256x256; no JSON")
+    ap.add_argument("--net-engine", type=int, default=1,
+                    help="--net-case convolution engine: 1 tcgen05, 0 mma.sync")
+    ap.add_argument("--mis-case", action="store_true",
+                    help="profiling case: window selection by mutual information, 2048x2048, "
+                         "5x5 patches, 4 calls; no JSON")
     return ap.parse_args()
 
 
@@ -366,6 +374,7 @@ def run_ours(args):
     pinfo = P.info()
     P.close()
     learned_out = None if args.no_learned or world > 1 else learned_leg(args, dev)
+    mis_out = None if world > 1 or rank != 0 else mis_leg(dev)
 
     if rank != 0:
         if world > 1:
@@ -402,6 +411,7 @@ def run_ours(args):
         "roofline": roof,
         "kernel_ms": prof,
         "learned": learned_out,
+        "mis_windows": mis_out,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -476,6 +486,43 @@ def learned_leg(args, dev):
     return out
 
 
+def mis_leg(dev):
+    """Window selection by mutual information (Sec. 5), a setup step once
+    per image: device time of nlh_mis_windows (64 bins, reflect padding) at
+    512^2 with 3x3 patches and 2048^2 with 5x5 patches, the oracle timed on
+    the 512^2 case on the host, and whether the windows agree there."""
+    import torch
+
+    from oracle import mis as omis
+    from paper_2407_06834_gb300 import nlh
+    from paper_2407_06834_gb300.inputs import synthetic_image
+    out = {}
+    for n, rho in ((512, 1), (2048, 2)):
+        img_h = synthetic_image(n, n, 0)[1]
+        img = torch.as_tensor(img_h, device=dev)
+        for _ in range(3):
+            nlh.mis_windows(img, rho, "reflect", 64)
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(20):
+            _, w, _ = nlh.mis_windows(img, rho, "reflect", 64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 20
+        D = (2 * rho + 1) ** 2
+        row = {"ms": ms, "gfeatures_per_s": n * n * D / ms / 1e6, "windows": w.tolist()}
+        if n == 512:
+            t0 = time.perf_counter()
+            _, w_ref = omis.mis_windows(img_h, rho, "reflect", 64)
+            row["oracle_seconds"] = time.perf_counter() - t0
+            row["oracle_kind"] = "oracle/mis.py: numpy, one thread (patch extraction OpenMP)"
+            row["windows_match_oracle"] = bool((w == w_ref).all())
+        out["%dx%d_%dx%d" % (n, n, 2 * rho + 1, 2 * rho + 1)] = row
+    return out
+
+
 def matvec_case(args):
     """Small profiling case: one 512x512 plan with all three arithmetics and
     the autotuned launch shapes of the bench step (FP32: default; double-
@@ -494,6 +541,40 @@ def matvec_case(args):
             P.matvec(x, op=2, precision=prec, alpha=wl.alpha)
     torch.cuda.synchronize()
     P.close()
+
+
+def net_case(args):
+    """Small profiling case of the learned leg's network: 2 x (forward +
+    loss and gradient) on 16 synthetic 256x256 images."""
+    import torch
+
+    from paper_2407_06834_gb300 import learned
+    from paper_2407_06834_gb300.inputs import synthetic_image
+    net = learned.new_net(seed=0)
+    net.engine = args.net_engine
+    B = 16
+    f = torch.as_tensor(np.stack([synthetic_image(256, 256, i)[1] for i in range(B)]),
+                        device="cuda")
+    sig, alp = [0.2] * B, [0.5] * B
+    ustar, deg = f.clone(), torch.full_like(f, 2.0)
+    for _ in range(2):
+        net.forward(f, sig, alp)
+        net.loss_grad(f, sig, alp, ustar, deg=deg, want_loss=False)
+    net.check()
+    net.close()
+
+
+def mis_case(args):
+    """Small profiling case: 4 calls of nlh_mis_windows on a 2048x2048 image
+    with 5x5 reflect-padded patches and 64 bins."""
+    import torch
+
+    from paper_2407_06834_gb300 import nlh
+    from paper_2407_06834_gb300.inputs import synthetic_image
+    img = torch.as_tensor(synthetic_image(2048, 2048, 0)[1], device="cuda")
+    for _ in range(4):
+        nlh.mis_windows(img, 2, "reflect", 64)
+    torch.cuda.synchronize()
 
 
 def run_sweep(args):
@@ -593,6 +674,10 @@ def main():
         run_sweep(args)
     elif args.matvec_case:
         matvec_case(args)
+    elif args.net_case:
+        net_case(args)
+    elif args.mis_case:
+        mis_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
