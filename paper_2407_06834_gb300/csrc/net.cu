@@ -27,6 +27,11 @@
 //                    pixels, so one staged band of 130 pixels serves the
 //                    three horizontal taps of a row offset; the accumulator
 //                    is in tensor memory, read back with tcgen05.ld.
+//   k_conv3x3_wgrad_tc<MT> the weight gradient on tcgen05 (the default
+//                    engine): M = output channels, N = 32 input channels,
+//                    K = padded pixels, both operands MN-major, the input
+//                    band shared by the three horizontal taps as in the
+//                    forward kernel; split K with f32 atomics.
 //   k_conv3x3_wgrad  weight gradient dW[co][tap][ci] = sum_p dZ[p][co]
 //                    X[p + off(tap)][ci]: M = cout, N = 32 input channels of
 //                    one tap, K = pixels split across CTAs, both operands
@@ -663,6 +668,198 @@ __global__ void __launch_bounds__(BMW * 2) k_conv3x3_wgrad(WgradArgs a) {
         }
 }
 
+// Weight gradient on tcgen05.  dW[co][tap][ci] = sum_p dZ[p][co] X[p + off][ci]
+// as a GEMM with M = output channels (MT = 64 or 128 per CTA), N = 32 input
+// channels, K = pixels, both operands read MN-major (idesc transpose bits):
+// A = dZ as planes of 8 channels [co / 8][pixel][8], B = the same 130-pixel
+// band of the input as the forward kernel ([ci / 8][band row][8]), so that
+// the three horizontal taps of the CTA's row offset dy are the band shifted
+// by 0, 1, 2 rows (16-byte steps of the start address).  K runs over the
+// zero-padded image's pixels, 128 per chunk (dZ is zero-filled at the
+// padding).  Three accumulators (one per tap, 32 columns each) in tensor
+// memory; after the CTA's chunks the epilogue adds them to the canonical
+// gradient with f32 atomics (split K).  With MT = 64 the accumulator row r
+// sits in lane (r / 16) 32 + r % 16.  Descriptors: LBO = stride between
+// K-direction core matrices (128 B), SBO = stride between M/N-direction
+// ones (one plane).  Grid: x = pixel split, y = (input block) * 3 + dy + 1,
+// z = block of MT output channels.
+constexpr int kWgChunk = 128;  // padded pixels per K chunk
+
+template <int MT> struct WgTile {
+    static constexpr int A_BYTES = MT * kWgChunk * 2;
+    static constexpr int B_BYTES = 4 * kBandRows * 16;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int SMEM = kTcStages * STAGE + 128;
+};
+
+template <int MT>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv3x3_wgrad_tc(WgradArgs a, int n_chunks,
+                                                                      int chunks_per_split,
+                                                                      int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using T = WgTile<MT>;
+    constexpr uint32_t SBO_A = kWgChunk * 16, SBO_B = kBandRows * 16;
+    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                               ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+    const int ch0 = blockIdx.x * chunks_per_split;
+    const int nch = min(n_chunks, ch0 + chunks_per_split) - ch0;
+    if (nch <= 0) return;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTcStages * T::STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + kTcStages);
+    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Wp = a.W + 2;
+    const int64_t Pp = (int64_t)a.B * a.H * Wp;
+    const int cb = blockIdx.y / 3, dy = (int)(blockIdx.y % 3) - 1;
+    const int c0 = cb * 32;
+    const int co0 = blockIdx.z * MT;
+    const int co_groups = min(MT, a.n - co0) / 8;  // loaded planes; the rest stay zero
+
+    // zero both stages once (planes beyond the layer's channels stay zero)
+    for (int i = tid; i < kTcStages * T::STAGE / 16; i += kConvThreads)
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int st = 0; st < kTcStages; ++st) mbar_init(bars + st, 1);
+        mbar_fence_init();
+        *s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+            smem_u32(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    auto load = [&](int stage, int c) {
+        const int64_t q0 = (int64_t)(ch0 + c) * kWgChunk;
+        const uint32_t sa = smem_u32(smem + stage * T::STAGE);
+        const uint32_t sb = sa + T::A_BYTES;
+        // A: dZ of padded pixel q0 + tid (zero at the padding and past the end)
+        {
+            const int64_t q = q0 + tid;
+            const bf16 *p = nullptr;
+            if (q < Pp) {
+                const int64_t r = q / Wp;
+                const int xp = (int)(q - r * Wp);
+                if (xp >= 1 && xp <= a.W) p = a.dz + (r * a.W + (xp - 1)) * a.n + co0;
+            }
+            for (int g = 0; g < co_groups; ++g)
+                cp_async16(sa + g * SBO_A + tid * 16, p ? p + 8 * g : a.dz, p != nullptr);
+        }
+        // B: band rows i = tid and (tid < 2) 128 + tid: padded pixel
+        // q0 - 1 + i shifted by dy rows
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && tid >= 2) break;
+            const int i = tid + h * kConvThreads;
+            const int64_t sidx = q0 - 1 + i;
+            const bf16 *p = nullptr;
+            if (sidx >= 0 && sidx < Pp) {
+                const int64_t r = sidx / Wp;
+                const int xp = (int)(sidx - r * Wp);
+                const int b = (int)(r / a.H), y = (int)(r - (int64_t)b * a.H);
+                p = src_ptr(a.src, b, y + dy, xp - 1, a.H, a.W, c0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cp_async16(sb + q * SBO_B + i * 16, p ? p + 8 * q : a.dz, p != nullptr);
+        }
+    };
+
+    bool ok = true;
+#pragma unroll
+    for (int st = 0; st < kTcStages - 1; ++st) {
+        if (st < nch) load(st, st);
+        cp_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int stage = c % kTcStages;
+        cp_wait<kTcStages - 2>();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + stage * T::STAGE);
+            const uint32_t sb = sa + T::A_BYTES;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+#pragma unroll
+                for (int ks = 0; ks < kWgChunk / 16; ++ks) {
+                    // tap dx = t - 1 reads band row k + t for pixel k
+                    const uint64_t da = tc_desc(sa + ks * 256, 128, SBO_A);
+                    const uint64_t db = tc_desc(sb + t * 16 + ks * 256, 128, SBO_B);
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                            tmem + (uint32_t)(t * 32)),
+                        "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(bars + stage))
+                : "memory");
+        }
+        // refill the stage of chunk c - 1 once its MMAs have read it
+        const int nx = c + kTcStages - 1;
+        if (nx < nch) {
+            if (c >= 1 && ok) {
+                const int w = c - 1;
+                if (!tc_wait(bars + (w % kTcStages), (w / kTcStages) & 1)) ok = false;
+            }
+            if (ok) load(nx % kTcStages, nx);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    for (int w = nch - kTcStages > 0 ? nch - kTcStages : 0; w < nch && ok; ++w)
+        if (!tc_wait(bars + (w % kTcStages), (w / kTcStages) & 1)) ok = false;
+    if (!ok) atomicExch(s_fail, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool failed = *s_fail != 0;
+    if (failed && tid == 0 && err) atomicExch(err, (int)NLH_ERR_TIMEOUT);
+
+    // epilogue: accumulator row of this lane (MT = 64: lanes 0..15 of each warp)
+    const int row = MT == 128 ? warp * 32 + lane : (lane < 16 ? warp * 16 + lane : -1);
+    const int co = co0 + row;
+    const bool live = !failed && row >= 0 && co < a.n;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int tap = (dy + 1) * 3 + t;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 32 + h * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!live) continue;
+            float *dst = a.dw + ((int64_t)co * 9 + tap) * a.cin_real;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int ci = c0 + h * 16 + j;
+                if (ci < a.cin_real) atomicAdd(dst + ci, __uint_as_float(r[j]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 // ------------------------------------------------------ elementwise kernels
 struct Scalars {
     float ls[kMaxBatch], la[kMaxBatch];  // ln sigma, ln alpha per image
@@ -1256,6 +1453,32 @@ static void conv_wgrad(nlh_net_s &N, int li, netk::Src src, const bf16 *dz, int 
     a.n = L.cout;
     a.cin_real = L.cin;
     a.dw = N.grad + L.woff;
+    if (N.engine == NLH_NET_ENGINE_TCGEN05) {
+        // K chunks of 128 padded pixels; about 8 CTAs per SM over the grid,
+        // at least 2 chunks per CTA
+        const int64_t Pp = (int64_t)B * H * (W + 2);
+        const int n_chunks = (int)((Pp + netk::kWgChunk - 1) / netk::kWgChunk);
+        const int gy = 3 * (L.cinp / 32);
+        auto launch = [&](auto mt) {
+            constexpr int MT = decltype(mt)::value;
+            const int gz = (L.cout + MT - 1) / MT;
+            int64_t splits = (8 * kSMs + (int64_t)gy * gz - 1) / ((int64_t)gy * gz);
+            splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n_chunks + 1) / 2));
+            const int cps = (int)((n_chunks + splits - 1) / splits);
+            splits = (n_chunks + cps - 1) / cps;
+            const int smem = netk::WgTile<MT>::SMEM;
+            NLH_CUDA(cudaFuncSetAttribute(netk::k_conv3x3_wgrad_tc<MT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            netk::k_conv3x3_wgrad_tc<MT><<<dim3((unsigned)splits, gy, gz), netk::kConvThreads,
+                                           smem, s>>>(a, n_chunks, cps, N.err);
+            NLH_CHECK_LAUNCH();
+        };
+        if (L.cout >= 128)
+            launch(std::integral_constant<int, 128>());
+        else
+            launch(std::integral_constant<int, 64>());
+        return;
+    }
     const int64_t P = (int64_t)B * H * W;
     const int bmw = L.cout % 64 == 0 ? 64 : 32;
     const int gy = 9 * (L.cinp / 32), gz = L.cout / bmw;
