@@ -420,6 +420,18 @@ static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, b
 // when check_every > 0), x_out = solution (or += when accumulate), and a
 // copy of the device state to the pinned mirror.  krylov_collect reads it
 // after the stream has been synchronised.
+// Relative tolerance of the inner FP32 solve of one refinement step, from
+// the current FP64-accurate relative residual rel: a step whose remaining
+// reduction is within reach (tol / (2 rel) >= max(inner / 4, 1e-4), 1e-4
+// being about where the FP32 operator's rounding stops a solve) runs to
+// exactly that reduction, capped at 0.1, so that it is the last step; any
+// other step runs to the caller's inner tolerance.
+static double inner_tolerance(double inner, double tol, double rel) {
+    const double need = 0.5 * tol / rel;
+    if (need >= std::max(0.25 * inner, 1e-4)) return std::min(need, 0.1);
+    return inner;
+}
+
 static void krylov_launch(Plan &P, int prec, double alpha, const double *rhs, const double *x0,
                           double *x_out, int accumulate, double tol, int maxit, int method,
                           const double *scale, int check_every, cudaStream_t s) {
@@ -607,7 +619,8 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 int outer = 0;
                 st = 1;
                 while (rel > opts->tol && outer < max_outer) {
-                    krylov_launch(P, NLH_FP32, alpha, P.rhs, nullptr, u, 1, inner, opts->maxit,
+                    krylov_launch(P, NLH_FP32, alpha, P.rhs, nullptr, u, 1,
+                                  inner_tolerance(inner, opts->tol, rel), opts->maxit,
                                   opts->method, scale, ce, s);
                     residual_launch(P, accurate, alpha, b, u, P.rhs, s);
                     NLH_CUDA(cudaStreamSynchronize(s));
@@ -742,8 +755,9 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                         NLH_CUDA(cudaMemcpyAsync(P.rhs, b[i], sizeof(double) * P.N,
                                                  cudaMemcpyDeviceToDevice, s));
                     }
-                    krylov_launch(P, NLH_FP32, alphas[i], P.rhs, nullptr, u[i], 1, inner,
-                                  opts->maxit, opts->method, nullptr, 0, s);
+                    krylov_launch(P, NLH_FP32, alphas[i], P.rhs, nullptr, u[i], 1,
+                                  inner_tolerance(inner, opts->tol, rel[i]), opts->maxit,
+                                  opts->method, nullptr, 0, s);
                     residual_launch(P, accurate, alphas[i], b[i], u[i], P.rhs, s);
                 }
                 active.push_back({(int)gi, i});
@@ -766,6 +780,7 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                     inf[i].matvecs_fp32 += kr.matvecs;
                     inf[i].matvecs_fp64 += 1;
                     inf[i].rel_res = r;
+                    rel[i] = r;
                     if (kr.status == -4) {
                         status[i] = -4;
                         done[i] = 1;
