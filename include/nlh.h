@@ -127,13 +127,17 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
 /* Re-split the plan's sorted points into work items of at most
  * max_items_pts points (all of one grid cell) and work units of at most
  * unit_points points (one CTA each), in place.  Changes only the
- * decomposition of the work, never the result beyond rounding.
- * Synchronises `stream`. */
+ * decomposition of the work, never the result beyond rounding.  The
+ * degrees are recomputed in the new summation order (so that L 1 = 0 holds
+ * to rounding), cached solve graphs are dropped and recaptured by the next
+ * solve.  Synchronises `stream`. */
 nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream);
 
 /* Set the launch shape (0..3; see nlh_plan_desc.team) of the spread and
  * interpolation kernels of one NFFT arithmetic (NLH_FP64, NLH_FP32,
- * NLH_DF32).  Changes no result beyond rounding. */
+ * NLH_DF32).  Changes no result beyond rounding.  A change of shape drops
+ * the cached solve graphs and recomputes the degrees on the stream of the
+ * plan's last call, which it synchronises. */
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
 
 /* Autotuner: time `reps` matvecs (0 = 3) of every NFFT arithmetic in the
@@ -145,7 +149,8 @@ nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
  * iteration counts, which this timing does not measure),
  * with those shapes; report it (any output pointer may be NULL; best_team
  * has 3 entries indexed like nlh_plan_desc.team) and its summed matvec time
- * in ms.  Synchronises `stream`. */
+ * in ms.  Like nlh_plan_retile it recomputes the degrees and drops cached
+ * solve graphs.  Synchronises `stream`. */
 nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_kmax,
                              int *best_unit_points, int *best_team, double *best_ms,
                              void *stream);

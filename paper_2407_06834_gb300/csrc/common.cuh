@@ -225,6 +225,8 @@ void retain_pool_memory();
 void check_device_error(Plan &P, cudaStream_t s);
 cudaStream_t take_capture_stream(int device);
 void plan_degrees(Plan &P, cudaStream_t s);
+// Destroy the cached solve graphs (after a change of tiling or launch shape).
+void drop_graphs(Plan &P);
 // alpha_dev (optional): read alpha from device memory instead of `alpha`.
 void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
             double *partials, const int *done, cudaStream_t s,

@@ -83,6 +83,15 @@ Plan::~Plan() {
     if (capture_stream) hp.streams[device].push_back(capture_stream);
 }
 
+// Destroy the plan's cached solve graphs (they hold the work-item and unit
+// arrays and the kernels' launch shapes); the next solve captures afresh.
+void drop_graphs(Plan &P) {
+    if (P.graphs.empty()) return;
+    NLH_CUDA(cudaStreamSynchronize(P.stream));
+    for (auto &kv : P.graphs) cudaGraphExecDestroy(kv.second);
+    P.graphs.clear();
+}
+
 void retain_pool_memory() {
     static std::once_flag once;
     std::call_once(once, [] {
@@ -777,6 +786,7 @@ static void fetch_unit_count(Plan &P, cudaStream_t s) {
 // recovered on the host (items of one cell are consecutive and contiguous
 // in sorted order) and cut again; no re-sort, no new weights.
 static void retile(Plan &P, int kmax, int unit_points, cudaStream_t s) {
+    drop_graphs(P);
     std::vector<int4> items(P.n_items);
     if (P.n_items)
         NLH_CUDA(cudaMemcpyAsync(items.data(), P.items, sizeof(int4) * P.n_items,
@@ -1260,6 +1270,9 @@ nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, vo
         cudaStream_t s = (cudaStream_t)stream;
         plan->stream = s;
         retile(*plan, max_items_pts, unit_points, s);
+        // degrees in the new summation order (L 1 = 0 to rounding again)
+        plan_degrees(*plan, s);
+        plan->pb2_sigma = -1.0;
         NLH_CUDA(cudaStreamSynchronize(s));
         return NLH_OK;
     } catch (Failure &f) {
@@ -1273,7 +1286,15 @@ nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape) {
         NLH_REQUIRE(plan, "nlh_plan_set_team: NULL plan");
         NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 3,
                     "nlh_plan_set_team: arith=%d shape=%d", arith, shape);
-        plan->team[arith] = shape;
+        if (plan->team[arith] != shape) {
+            // new summation order: drop the captured solve graphs and
+            // recompute the degrees (on the plan's last stream)
+            drop_graphs(*plan);
+            plan->team[arith] = shape;
+            plan_degrees(*plan, plan->stream);
+            plan->pb2_sigma = -1.0;
+            NLH_CUDA(cudaStreamSynchronize(plan->stream));
+        }
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;
@@ -1345,6 +1366,8 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
         cudaEventDestroy(e1);
         retile(P, bk, bu, s);
         for (int a = 0; a < 3; ++a) P.team[a] = bt[a];
+        plan_degrees(P, s);
+        P.pb2_sigma = -1.0;
         check_device_error(P, s);
         if (best_kmax) *best_kmax = bk;
         if (best_unit_points) *best_unit_points = bu;

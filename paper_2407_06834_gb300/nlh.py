@@ -268,7 +268,17 @@ class Plan:
         self.L = win.shape[0]
         if autotune and not tuned:
             from . import autotune as _at
-            _at.tune_and_record(self, stream=stream)
+            hit = None
+            if nfft_eps > 0.0:
+                # the class (n_os, m) is known only now: apply a cached result
+                inf = self.info()
+                hit = _at.lookup(inf["n_os"], inf["m"], self.L, N)
+            if hit:
+                self.retile(hit["max_items_pts"], hit["unit_points"], stream=stream)
+                for arith, shape in enumerate(hit.get("team", (0, 0, 0))):
+                    self.set_team(arith, shape)
+            else:
+                _at.tune_and_record(self, stream=stream)
 
     @classmethod
     def from_image(cls, image, radius: int, windows, sigma: float, pad: str = "reflect",

@@ -114,3 +114,32 @@ def test_retile_and_autotune_keep_results(tmp_path, monkeypatch):
     assert R.info()["unit_points"] == first["unit_points"]
     assert R.info()["team"] == first["team"]
     assert relmax(host(R.matvec(v, precision=nlh.NLH_DF32)), y0) < 1e-12
+
+
+def test_retile_and_team_after_a_solve_keep_the_plan_consistent():
+    """Changing the tiling or a launch shape after solves have captured
+    their graphs: the graphs are recaptured (same iterates up to rounding)
+    and the degrees follow the new summation order (L 1 = 0 to rounding)."""
+    from gpu_helpers import cuda, host, make_plan
+    from paper_2407_06834_gb300.inputs import synthetic_image
+    _, img = synthetic_image(96, 80, 4)
+    P = make_plan(img, precision=6)
+    b = cuda(img.reshape(-1) * 0.5)
+    r0 = P.solve(0.5, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    ones = cuda(np.ones(img.size))
+    for step in range(3):
+        if step == 0:
+            P.retile(32, 256)
+        elif step == 1:
+            P.set_team(nlh.NLH_DF32, 2)
+        else:
+            P.retile(128, 1024)
+        r = P.solve(0.5, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+        assert r.info["rel_res_true"] <= 1e-6
+        assert abs(r.info["iters"] - r0.info["iters"]) <= 1
+        np.testing.assert_allclose(host(r.u), host(r0.u), rtol=0, atol=2e-4 * np.abs(host(r0.u)).max())
+        for prec in (nlh.NLH_FP32, nlh.NLH_DF32):
+            l1 = host(P.matvec(ones, op=1, precision=prec))
+            d = host(P.degrees())
+            assert np.abs(l1).max() <= (1e-4 if prec == nlh.NLH_FP32 else 1e-9) * d.max()
+    P.close()
