@@ -68,4 +68,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Test hook (include/nlh_selftest.h): poll an mbarrier that nothing
+// completes with the non-blocking test_wait, 2^20 times, then record
+// NLH_ERR_TIMEOUT in *err as a library kernel's bounded wait does.
+__global__ void k_selftest_wait_nothing(int *err);
+
 }  // namespace nlh

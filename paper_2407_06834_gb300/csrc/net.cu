@@ -46,6 +46,7 @@
 #include "common.cuh"
 #include "async_copy.cuh"
 #include "../../include/nlh_net.h"
+#include "../../include/nlh_selftest.h"
 
 #include <cuda_bf16.h>
 
@@ -1910,6 +1911,18 @@ nlh_status nlh_net_check(nlh_net net, void *stream) {
         nlh_net_s *N = checked(net);
         NLH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
         take_error(*N);
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
+nlh_status nlh_selftest_net_timeout(nlh_net net, void *stream) {
+    clear_error();
+    try {
+        nlh_net_s *N = checked(net);
+        k_selftest_wait_nothing<<<1, 32, 0, (cudaStream_t)stream>>>(N->err);
+        NLH_CHECK_LAUNCH();
         return NLH_OK;
     } catch (Failure &f) {
         return f.st;

@@ -124,6 +124,8 @@ SIGNATURES = {
                                             C.POINTER(C.c_double), C.c_void_p]),
     "nlh_mis_windows": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nlh_selftest_plan_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nlh_selftest_net_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
