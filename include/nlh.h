@@ -140,6 +140,20 @@ nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, vo
  * plan's last call, which it synchronises. */
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
 
+/* Interpolation kernel of every NFFT arithmetic (Sec. 3, the NFFT
+ * evaluation at the points):
+ *   NLH_INTERP_POINTS (default) one point per lane: a warp takes 32
+ *       consecutive sorted points of a work unit and each lane sums its
+ *       point's (2m)^3 stencil from the tile staged in shared memory;
+ *   NLH_INTERP_TEAMS  the team kernel of nlh_plan_desc.team: threads own
+ *       (y, z) stencil rows and each point's sum is reduced across lanes.
+ * (The tensor-core FP32 shape 3 keeps its own interpolation.)  Results
+ * agree to the arithmetic's rounding.  A change drops the cached solve
+ * graphs and recomputes the degrees on the stream of the plan's last call,
+ * which it synchronises.  Errors: NLH_ERR_ARG. */
+enum { NLH_INTERP_POINTS = 0, NLH_INTERP_TEAMS = 1 };
+nlh_status nlh_plan_set_interp(nlh_plan plan, int kind);
+
 /* Autotuner: time `reps` matvecs (0 = 3) of every NFFT arithmetic in the
  * bit mask `precisions` (0 = all the plan built) for each tiling of a fixed
  * grid (max_items_pts in {32, 64, 128, 256} x unit_points in {256, 512, 1024,

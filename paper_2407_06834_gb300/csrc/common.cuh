@@ -105,7 +105,8 @@ struct Plan {
     int64_t N = 0;
     int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 64;
     int unit_points = kUnitPoints;
-    int team[3] = {0, 0, 0};  // spread / interpolation team shape per arithmetic
+    int team[3] = {0, 0, 0};   // spread / interpolation team shape per arithmetic
+    int interp_kind = 0;       // NLH_INTERP_POINTS or NLH_INTERP_TEAMS
     double *pb2 = nullptr;     // (d' - 1) / L for P_b' (d' = Gamma_full 1 at sigma / sqrt 2)
     double pb2_sigma = -1.0;   // sigma pb2 was computed for
     int pc_kind = 0;           // preconditioner of the current solve: 0 P_a, 1 P_b'

@@ -259,6 +259,10 @@ template <typename T, int W2> struct Line {
     }
     __device__ __forceinline__ T get(int a) const { return v[a]; }
     __device__ __forceinline__ void set(int a, T x) { v[a] = x; }
+    __device__ __forceinline__ void load_cells(const T *row) {  // 2m consecutive cells
+#pragma unroll
+        for (int a = 0; a < W2; ++a) v[a] = row[a];
+    }
 };
 
 template <int W2> struct Line<float, W2> {
@@ -298,6 +302,11 @@ template <int W2> struct Line<float, W2> {
         asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v[a / 2]));
         if (a & 1) hi = x; else lo = x;
         asm("mov.b64 %0, {%1, %2};" : "=l"(v[a / 2]) : "f"(lo), "f"(hi));
+    }
+    __device__ __forceinline__ void load_cells(const float *row) {  // 2m consecutive cells
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a)
+            asm("mov.b64 %0, {%1, %2};" : "=l"(v[a]) : "f"(row[2 * a]), "f"(row[2 * a + 1]));
     }
 };
 
@@ -345,6 +354,14 @@ template <int W2> struct Line<df32, W2> {
         if (a & 1) { h1 = x.hi; l1 = x.lo; } else { h0 = x.hi; l0 = x.lo; }
         h[a / 2] = pk_make(h0, h1);
         l[a / 2] = pk_make(l0, l1);
+    }
+    __device__ __forceinline__ void load_cells(const df32 *row) {  // 2m consecutive cells
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) {
+            const df32 c0 = row[2 * a], c1 = row[2 * a + 1];
+            h[a] = pk_make(c0.hi, c1.hi);
+            l[a] = pk_make(c0.lo, c1.lo);
+        }
     }
 };
 
@@ -679,6 +696,138 @@ k_interp(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
             bsel ^= 1;
         }
     }
+}
+
+template <typename T> constexpr int interp_class() {
+    return sizeof(T) == 4 ? NLH_K_INTERP32 : (Num<T>::kParts == 2 ? NLH_K_INTERPDF : NLH_K_INTERP64);
+}
+template <typename T> constexpr int interp_class_pl() { return interp_class<T>(); }
+
+// ------------------------------------------------- interpolation, points on lanes
+// The same interpolation with one point per lane: a warp takes 32
+// consecutive (sorted) points of the unit, each lane finds its point's cell
+// among the unit's items (binary search on the first sorted positions),
+// holds its weight record in registers and evaluates
+//   y = sum_z wz[z] (wx . t_z),  t_z[x] = sum_y wy[y] S[z][y][x]
+// over its stencil in the staged tile region, with no cross-lane reduction
+// (consecutive points mostly share a cell, so their tile rows are the same
+// addresses).  Written straight to Y in pixel order.
+constexpr int kPlThreads = 256;
+
+template <typename T, int W2>
+__global__ void __launch_bounds__(kPlThreads)
+k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
+            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
+            const int *__restrict__ perm, const typename Num<T>::R *__restrict__ wts,
+            const typename Num<T>::G *__restrict__ grid, double *__restrict__ Y, int n, int m,
+            int64_t N, const int *__restrict__ done) {
+    using R = typename Num<T>::R;
+    using G = typename Num<T>::G;
+    using SM = UnitSmem<T, W2, 1>;
+    constexpr int E = SM::E, E3 = SM::E3, PWP = SM::PWP;
+    static_assert((PWP * sizeof(R)) % 16 == 0, "records are whole 16-byte words");
+    constexpr int RW = PWP * (int)sizeof(R) / 16;  // 16-byte words per record
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + SM::tile);
+    int *s_ctl = reinterpret_cast<int *>(s_items + kUnitItems);
+    if (done && *done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int msk = n - 1;
+    while (true) {
+        __syncthreads();  // previous unit done with the tile
+        if (threadIdx.x == 0) s_ctl[0] = atomicAdd(unit_ctr, 1);
+        __syncthreads();
+        const int uidx = s_ctl[0];
+        if (uidx >= *n_units_dev) break;
+        const int4 un = units[uidx];
+        const int l = un.x, it0 = un.z, nit = un.w;
+        int tx0, ty0, tz0;
+        tile_origin(un.y, n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        const G *g = grid + (int64_t)l * n * n * n;
+        {
+            constexpr int UNR = 8;
+            for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
+                G vals[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int e = base + u * blockDim.x;
+                    vals[u] = G(0);
+                    if (e < E3) {
+                        const int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
+                        const int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
+                                  gz = (tz0 - m + 1 + ez) & msk;
+                        vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int e = base + u * blockDim.x;
+                    if (e < E3) S[e] = T(vals[u]);
+                }
+            }
+        }
+        __syncthreads();
+        const int first = s_items[0].z;
+        const int total = s_items[nit - 1].z + s_items[nit - 1].w - first;
+        for (int p = warp * 32 + lane; p - lane < total; p += nwarp * 32) {
+            if (p >= total) continue;
+            const int sp = first + p;
+            int lo = 0, hi = nit - 1;  // the last item starting at or before sp
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_items[mid].z <= sp) lo = mid; else hi = mid - 1;
+            }
+            int lx0, ly0, lz0;
+            item_local(s_items[lo].x, lx0, ly0, lz0);
+            R rec[PWP];
+            {
+                const uint4 *src = reinterpret_cast<const uint4 *>(wts + (int64_t)sp * PWP);
+#pragma unroll
+                for (int k = 0; k < RW; ++k) reinterpret_cast<uint4 *>(rec)[k] = __ldg(src + k);
+            }
+            Line<T, W2> wx, t, h;
+            wx.load(rec_line<T, W2>(rec, 0));
+            T acc = T(0);
+#pragma unroll
+            for (int z = 0; z < W2; ++z) {
+                t.zero();
+#pragma unroll
+                for (int y = 0; y < W2; ++y) {
+                    h.load_cells(S + ((lz0 + z) * E + (ly0 + y)) * E + lx0);
+                    t.axpy(rec_val<T, W2>(rec, 1, y), h);
+                }
+                acc = fma(rec_val<T, W2>(rec, 2, z), wx.dot(t), acc);
+            }
+            Y[(int64_t)l * N + perm[sp]] = (double)acc;
+        }
+    }
+}
+
+template <typename T, int W2>
+static void launch_interp_pl(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
+                             const int *done, cudaStream_t s) {
+    constexpr size_t smem = UnitSmem<T, W2, 1>::tile + sizeof(int4) * kUnitItems + 16;
+    if (P.units_cap == 0) return;
+    static int blocks = 0;
+    if (blocks == 0) {
+        NLH_CUDA(cudaFuncSetAttribute(k_interp_pl<T, W2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, b = 0;
+        NLH_CUDA(cudaGetDevice(&dev));
+        NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_pl<T, W2>,
+                                                               kPlThreads, smem));
+        blocks = sms * std::max(1, b);
+    }
+    ProfRange pr(interp_class_pl<T>(), s);
+    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
+    if (nu == 0) return;
+    const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
+    k_interp_pl<T, W2><<<g, kPlThreads, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
+                                                   P.perm, wts, grid, P.Y, P.n, P.m, P.N, done);
+    NLH_CHECK_LAUNCH();
 }
 
 // ------------------------------------------------------------------ tensor-core FP32 path
@@ -1166,9 +1315,7 @@ k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restr
 template <typename T> constexpr int spread_class() {
     return sizeof(T) == 4 ? NLH_K_SPREAD32 : (Num<T>::kParts == 2 ? NLH_K_SPREADDF : NLH_K_SPREAD64);
 }
-template <typename T> constexpr int interp_class() {
-    return sizeof(T) == 4 ? NLH_K_INTERP32 : (Num<T>::kParts == 2 ? NLH_K_INTERPDF : NLH_K_INTERP64);
-}
+
 
 template <typename T, int W2, int NW, int TPB>
 static void launch_spread_interp_shape(Plan &P, bool spread, const typename Num<T>::R *wts,
@@ -1267,6 +1414,10 @@ static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R 
                                  typename Num<T>::G *grid, const T *xs, const int *done,
                                  cudaStream_t s) {
     const int shape = P.team[arith_index<T>()];
+    // interpolation: points on lanes unless the plan asks for the team kernel
+    // (or the tensor-core FP32 shape, which has its own)
+    if (!spread && P.interp_kind == NLH_INTERP_POINTS && shape != 3)
+        return launch_interp_pl<T, W2>(P, wts, grid, done, s);
     if constexpr (W2 == 8 && std::is_same<T, float>::value) {
         if (shape == 3) return launch_spread_interp_tc<5>(P, spread, wts, grid, xs, done, s);
     }

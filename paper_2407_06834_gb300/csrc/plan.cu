@@ -1280,6 +1280,25 @@ nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, vo
     }
 }
 
+nlh_status nlh_plan_set_interp(nlh_plan plan, int kind) {
+    clear_error();
+    try {
+        NLH_REQUIRE(plan, "nlh_plan_set_interp: NULL plan");
+        NLH_REQUIRE(kind == NLH_INTERP_POINTS || kind == NLH_INTERP_TEAMS,
+                    "nlh_plan_set_interp: kind=%d", kind);
+        if (plan->interp_kind != kind) {
+            drop_graphs(*plan);
+            plan->interp_kind = kind;
+            plan_degrees(*plan, plan->stream);
+            plan->pb2_sigma = -1.0;
+            NLH_CUDA(cudaStreamSynchronize(plan->stream));
+        }
+        return NLH_OK;
+    } catch (Failure &f) {
+        return f.st;
+    }
+}
+
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape) {
     clear_error();
     try {

@@ -25,6 +25,7 @@ NLH_FP64, NLH_FP32, NLH_DF32 = 0, 1, 2
 PREC_PA, PREC_PB = 0, 1      # Jacobi P_a, and P_b' of Sec. 4.3.3
 CG, PCG_JACOBI, PCG_DEFLATED, CG_DEFLATED = 0, 1, 2, 3
 SOLVE_FP64, SOLVE_MIXED, SOLVE_DF32 = 0, 1, 2
+INTERP_POINTS, INTERP_TEAMS = 0, 1
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
                 -4: "ERR_BREAKDOWN", -5: "ERR_TIMEOUT"}
 
@@ -93,6 +94,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.c_void_p]),
     "nlh_plan_set_team": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "nlh_plan_set_interp": (C.c_int, [C.c_void_p, C.c_int]),
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
@@ -313,6 +315,10 @@ class Plan:
 
     def set_team(self, arith: int, shape: int):
         _check(load().nlh_plan_set_team(self._h, int(arith), int(shape)))
+
+    def set_interp(self, kind: int):
+        """Interpolation kernel: INTERP_POINTS (default) or INTERP_TEAMS."""
+        _check(load().nlh_plan_set_interp(self._h, int(kind)))
 
     def degrees(self, out=None, stream=None):
         """d = Gamma_full 1 in pixel order (nlh_plan_get_degrees)."""

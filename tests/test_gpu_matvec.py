@@ -253,3 +253,29 @@ def test_fp32_tensor_core_kernels(shape, kmax):
     b = 0.5 * img.ravel()
     r = P.solve(0.5, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
     assert r.info["rel_res_true"] <= 1e-6
+
+
+@pytest.mark.parametrize("m,shape,kmax", [(4, (64, 64), 0), (6, (37, 53), 0), (3, (16, 24), 7)])
+def test_interpolation_kernels_agree(m, shape, kmax):
+    """Points-on-lanes (default) and team interpolation: the same sums in
+    another order, for every arithmetic; ragged images, small work items."""
+    img = image(*shape, seed=m)
+    P = make_plan(img, M=32, n_os=64, m=m, precision=7, kmax=kmax)
+    v = cuda(random_vector(img.size, 5 + m))
+    ys = {}
+    for kind in (nlh.INTERP_POINTS, nlh.INTERP_TEAMS):
+        P.set_interp(kind)
+        for prec in (nlh.NLH_FP64, nlh.NLH_FP32, nlh.NLH_DF32):
+            ys[kind, prec] = host(P.matvec(v, op=0, precision=prec))
+    a, b = nlh.INTERP_POINTS, nlh.INTERP_TEAMS
+    assert relmax(ys[a, nlh.NLH_FP64], ys[b, nlh.NLH_FP64]) < 1e-13
+    assert relmax(ys[a, nlh.NLH_DF32], ys[b, nlh.NLH_DF32]) < 1e-12
+    assert relmax(ys[a, nlh.NLH_FP32], ys[b, nlh.NLH_FP32]) < 1e-5
+    assert relmax(ys[a, nlh.NLH_FP32], ys[a, nlh.NLH_FP64]) < 1e-5
+    # L 1 = 0 to rounding with the degrees recomputed for the kernel in use
+    ones = cuda(np.ones(img.size))
+    l1 = host(P.matvec(ones, op=1, precision=nlh.NLH_DF32))
+    assert np.abs(l1).max() < 1e-9 * host(P.degrees()).max()
+    with pytest.raises(nlh.NLHError):
+        P.set_interp(2)
+    P.close()
