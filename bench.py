@@ -52,6 +52,16 @@ NCU_TRAFFIC_IMG512 = {"spread32": 81.82e6, "interp32": 84.27e6,
                       "spread_df32": 163.74e6, "interp_df32": 161.53e6}
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the
+    profiling fallback of 6.8 TB/s."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,11 +320,22 @@ def run_ours(args):
         else:
             ach, peak = 2.0 * updates / avg_s / 1e12, FP32_PEAK_TFLOPS
             src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        # the same launch against the HBM roofline: algorithmic bytes per
+        # point-window = one weight record + one permutation entry + one FP64
+        # value (interpolation output / spreading input of the FP64-side
+        # vectors); 108 B FP32, 204 B double-float at m = 4, as ncu measures
+        rec_bytes = 3 * W2 * (8 if dom.endswith(("64", "df32")) else 4)
+        alg_bytes = float(N * L) * (((rec_bytes + 15) // 16) * 16 + 4 + 8)
+        hbm_peak = measured_hbm_gbs()
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "traffic_note": "ncu DRAM read+write bytes per launch, 512x512 capture"
                 if traffic else None,
-                "mean_launch_ms": avg_s * 1e3, "peak_source": src}
+                "mean_launch_ms": avg_s * 1e3, "peak_source": src,
+                "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / avg_s / 1e9,
+                        "peak_gbs": hbm_peak,
+                        "frac": (alg_bytes / avg_s / 1e9 / hbm_peak) if hbm_peak else None,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
     elif dom:
         roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": None, "unit": "GB/s",
                 "frac": None, "traffic": None}
