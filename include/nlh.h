@@ -147,7 +147,8 @@ nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
  *       point's (2m)^3 stencil from the tile staged in shared memory;
  *   NLH_INTERP_TEAMS  the team kernel of nlh_plan_desc.team: threads own
  *       (y, z) stencil rows and each point's sum is reduced across lanes.
- * (The tensor-core FP32 shape 3 keeps its own interpolation.)  Results
+ * (The tensor-core FP32 shape 3 keeps its own interpolation; stencil widths
+ * 2m other than 8 and 12 always use the team kernel.)  Results
  * agree to the arithmetic's rounding.  A change drops the cached solve
  * graphs and recomputes the degrees on the stream of the plan's last call,
  * which it synchronises.  Errors: NLH_ERR_ARG. */

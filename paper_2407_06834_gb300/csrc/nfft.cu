@@ -789,16 +789,25 @@ k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
             }
             Line<T, W2> wx, t, h;
             wx.load(rec_line<T, W2>(rec, 0));
-            T acc = T(0);
+            T wy[W2], wz[W2];
 #pragma unroll
+            for (int j = 0; j < W2; ++j) {
+                wy[j] = rec_val<T, W2>(rec, 1, j);
+                wz[j] = rec_val<T, W2>(rec, 2, j);
+            }
+            T acc = T(0);
+            // the z loop stays rolled (the unrolled y loop is the work; a
+            // fully unrolled stencil made the compile many minutes long)
+#pragma unroll 1
             for (int z = 0; z < W2; ++z) {
                 t.zero();
+                const T *srow = S + ((lz0 + z) * E + ly0) * E + lx0;
 #pragma unroll
                 for (int y = 0; y < W2; ++y) {
-                    h.load_cells(S + ((lz0 + z) * E + (ly0 + y)) * E + lx0);
-                    t.axpy(rec_val<T, W2>(rec, 1, y), h);
+                    h.load_cells(srow + y * E);
+                    t.axpy(wy[y], h);
                 }
-                acc = fma(rec_val<T, W2>(rec, 2, z), wx.dot(t), acc);
+                acc = fma(wz[z], wx.dot(t), acc);
             }
             Y[(int64_t)l * N + perm[sp]] = (double)acc;
         }
@@ -1423,9 +1432,14 @@ static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R 
                                  cudaStream_t s) {
     const int shape = P.team[arith_index<T>()];
     // interpolation: points on lanes unless the plan asks for the team kernel
-    // (or the tensor-core FP32 shape, which has its own)
-    if (!spread && P.interp_kind == NLH_INTERP_POINTS && shape != 3)
-        return launch_interp_pl<T, W2>(P, wts, grid, done, s);
+    // (or the tensor-core FP32 shape, which has its own).  Compiled for the
+    // stencil widths of the workloads (2m = 8, 12): its fully unrolled
+    // stencil makes every further width a long compile; other widths run
+    // the team kernel.
+    if constexpr (W2 == 8 || W2 == 12) {
+        if (!spread && P.interp_kind == NLH_INTERP_POINTS && shape != 3)
+            return launch_interp_pl<T, W2>(P, wts, grid, done, s);
+    }
     if constexpr (W2 == 8 && std::is_same<T, float>::value) {
         if (shape == 3) return launch_spread_interp_tc<5>(P, spread, wts, grid, xs, done, s);
     }

@@ -308,3 +308,50 @@ def test_what_the_trained_network_gains(trained):
             # atomic grid sums in the mixed form's inner solves
             assert abs(x0_only.info["iters"] - plain.info["iters"]) <= 1, rows
     print("sigma, alpha, plain iters, x0-only iters, x0 rejected, full iters, fallback:", rows)
+
+
+@pytest.mark.parametrize("engine", [nlh.Net.ENGINE_TCGEN05, nlh.Net.ENGINE_MMA_SYNC])
+def test_base64_forward_matches_bf16_oracle(engine):
+    """64 base channels: 512-channel bottom layers, several output-channel
+    tiles per convolution (and per weight-gradient CTA grid)."""
+    levels, B, H, W = 4, 1, 16, 24
+    net = nlh.Net(64, levels)
+    th = net_init(net.shapes(), 21)
+    nh = 2 * 64 + 2
+    th[-nh:-2] *= 100.0
+    net.set_params(th)
+    net.engine = engine
+    th = th.astype(np.float64)
+    f = _images(B, H, W, seed=4)
+    sig, alp = np.array([0.3]), np.array([0.7])
+    u0, scale = net.forward(cuda(f), sig, alp)
+    o0 = host(u0) - f.mean(axis=(1, 2))[:, None, None]
+    ob, _, _ = unet.forward(th, f, sig, alp, 64, levels, bf16=True)
+    oe, _, _ = unet.forward(th, f, sig, alp, 64, levels, bf16=False)
+    rms = lambda a: np.sqrt(np.mean(a ** 2))
+    eb = rms(ob[..., 0] - oe[..., 0])
+    assert 0 < eb < 3e-2 * rms(oe[..., 0])
+    assert rms(o0 - ob[..., 0]) <= 1.5 * eb and rms(o0 - oe[..., 0]) <= 2.5 * eb
+
+
+def test_base64_engines_agree_on_gradients():
+    levels, B, H, W = 4, 2, 64, 64
+    net = nlh.Net(64, levels)
+    th = net_init(net.shapes(), 22)
+    th[-130:-2] *= 100.0
+    net.set_params(th)
+    f, ustar, e0, r0, deg = _loss_inputs(B, H, W, 23)
+    sig, alp = np.array([0.2, 0.5]), np.array([0.5, 2.0])
+    g = {}
+    for eng in (nlh.Net.ENGINE_MMA_SYNC, nlh.Net.ENGINE_TCGEN05):
+        net.engine = eng
+        net.loss_grad(cuda(f), sig, alp, cuda(ustar), e0=cuda(e0), r0=cuda(r0), deg=cuda(deg),
+                      beta=0.3)
+        net.check()
+        g[eng] = net.grads().astype(np.float64)
+    off = 0
+    for L in unet.layers(64, levels):
+        n = L.cout * L.k * L.k * L.cin + L.cout
+        da, db = g[0][off:off + n], g[1][off:off + n]
+        assert np.linalg.norm(db - da) <= 5e-2 * np.linalg.norm(da) + 1e-30, L.name
+        off += n
