@@ -3,8 +3,9 @@
  *
  * The paper has no learned component (its solver is the deflated,
  * diagonally preconditioned CG of Sec. 4.3.2); this part adds one in front
- * of that solver and keeps the plain solver as the fallback and the judge of
- * the final residual (nlh_solve's x0 and diag_scale).
+ * of that solver and keeps the plain solver as the fallback, with the final
+ * residual always checked by the FP64-accurate operator (nlh_solve's x0 and
+ * diag_scale).
  *
  * The network, for B images of H x W pixels (H, W multiples of
  * 2^(levels-1)):
