@@ -714,8 +714,8 @@ template <typename T> constexpr int interp_class_pl() { return interp_class<T>()
 // addresses).  Written straight to Y in pixel order.
 constexpr int kPlThreads = 256;
 
-template <typename T, int W2, int NTH = kPlThreads>
-__global__ void __launch_bounds__(NTH)
+template <typename T, int W2, int NTH = kPlThreads, int MINB = 1>
+__global__ void __launch_bounds__(NTH, MINB)
 k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
             int *__restrict__ unit_ctr, const int4 *__restrict__ items,
             const int *__restrict__ perm, const typename Num<T>::R *__restrict__ wts,
@@ -814,19 +814,19 @@ k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
     }
 }
 
-template <typename T, int W2, int NTH>
+template <typename T, int W2, int NTH, int MINB = 1>
 static void launch_interp_pl_n(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
                                const int *done, cudaStream_t s) {
     constexpr size_t smem = UnitSmem<T, W2, 1>::tile + sizeof(int4) * kUnitItems + 16;
     if (P.units_cap == 0) return;
     static int blocks = 0;
     if (blocks == 0) {
-        NLH_CUDA(cudaFuncSetAttribute(k_interp_pl<T, W2, NTH>,
+        NLH_CUDA(cudaFuncSetAttribute(k_interp_pl<T, W2, NTH, MINB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, sms = 0, b = 0;
         NLH_CUDA(cudaGetDevice(&dev));
         NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_pl<T, W2, NTH>, NTH,
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_pl<T, W2, NTH, MINB>, NTH,
                                                                smem));
         blocks = sms * std::max(1, b);
     }
@@ -834,17 +834,20 @@ static void launch_interp_pl_n(Plan &P, const typename Num<T>::R *wts, typename 
     const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
     if (nu == 0) return;
     const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
-    k_interp_pl<T, W2, NTH><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
+    k_interp_pl<T, W2, NTH, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
                                                  P.perm, wts, grid, P.Y, P.n, P.m, P.N, done);
     NLH_CHECK_LAUNCH();
 }
 
 // 256 threads per CTA measured best for the double-float kernel at 512^2
-// (0.286 ms against 0.340 ms with 128 and 0.353 ms with 512).
+// (0.286 ms against 0.340 ms with 128 and 0.353 ms with 512, uncapped).
 template <typename T, int W2>
 static void launch_interp_pl(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
                              const int *done, cudaStream_t s) {
-    launch_interp_pl_n<T, W2, kPlThreads>(P, wts, grid, done, s);
+    // double-float at 2m = 8: registers capped for 3 CTAs per SM (no spills;
+    // whole matvecs at 512^2 0.722 -> 0.627 ms against the uncapped 2 CTAs)
+    constexpr int MINB = (std::is_same<T, df32>::value && W2 == 8) ? 3 : 1;
+    launch_interp_pl_n<T, W2, kPlThreads, MINB>(P, wts, grid, done, s);
 }
 
 // ------------------------------------------------------------------ tensor-core FP32 path
