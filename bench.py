@@ -48,8 +48,8 @@ FP64_PEAK_TFLOPS = 1.25
 DF32_FLOP_PER_UPDATE = 15
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/k_nfft_fp32_df32_img512.md (512 x 512 workload); None elsewhere.
-NCU_TRAFFIC_IMG512 = {"spread32": 81.82e6, "interp32": 84.08e6,
-                      "spread_df32": 163.74e6, "interp_df32": 161.84e6}
+NCU_TRAFFIC_IMG512 = {"spread32": 80.39e6, "interp32": 81.26e6,
+                      "spread_df32": 160.22e6, "interp_df32": 159.31e6}
 
 
 def measured_hbm_gbs():
