@@ -844,9 +844,13 @@ static void launch_interp_pl_n(Plan &P, const typename Num<T>::R *wts, typename 
 template <typename T, int W2>
 static void launch_interp_pl(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
                              const int *done, cudaStream_t s) {
-    // double-float at 2m = 8: registers capped for 3 CTAs per SM (no spills;
-    // whole matvecs at 512^2 0.722 -> 0.627 ms against the uncapped 2 CTAs)
-    constexpr int MINB = (std::is_same<T, df32>::value && W2 == 8) ? 3 : 1;
+    // Registers capped by launch bounds (no spills in any instance):
+    //  double-float, 2m = 8: 3 CTAs per SM instead of 2 (whole matvecs at
+    //    512^2 0.722 -> 0.627 ms);
+    //  FP32 and double-float, 2m = 12: 2 CTAs per SM instead of 1 (whole
+    //    matvecs at 2048^2, 5x5 patches: 20.75 -> 17.97 ms and 81.4 -> 75.0 ms).
+    constexpr bool f64 = std::is_same<T, double>::value;
+    constexpr int MINB = (std::is_same<T, df32>::value && W2 == 8) ? 3 : (W2 == 12 && !f64) ? 2 : 1;
     launch_interp_pl_n<T, W2, kPlThreads, MINB>(P, wts, grid, done, s);
 }
 
