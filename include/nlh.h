@@ -43,6 +43,16 @@ typedef enum {
 
 typedef struct nlh_plan_s *nlh_plan;
 
+/* Sum over ranks of a plan that holds a range of the windows (Sec. 3: the
+ * ANOVA kernel is the mean of L independent per-window Gauss transforms, so
+ * ranks holding disjoint window ranges each compute a share of
+ * Gamma_full x and one sum over the ranks completes it).  Called on the
+ * host, at enqueue time, with the device FP64 vector buf of length n and
+ * the stream of the current call; it must enqueue on that stream an
+ * in-place sum of buf over all ranks (e.g. an NCCL all-reduce) and return.
+ * ctx is the plan description's reduce_ctx. */
+typedef void (*nlh_reduce_fn)(double *buf, int64_t n, void *stream, void *ctx);
+
 /* NFFT arithmetic of a matvec.  NLH_DF32 carries every value as an
  * unevaluated sum of two floats (about 46-48 significant bits) so that the
  * FP64-accurate operator runs on the FP32 pipes; its grids and FFTs are FP64. */
@@ -83,19 +93,31 @@ typedef struct {
                                truncation and window errors are <= nfft_eps;
                                M, n_os, torus_fill are then ignored          */
     int unit_points;        /* points per work unit (one CTA), 0 = 512       */
-    int team[3];            /* launch shape of the spread / interpolation
-                               kernels per NFFT arithmetic (index NLH_FP64,
-                               NLH_FP32, NLH_DF32): 0 default, 1 and 2 the
-                               alternatives compiled for 2m = 8 and 12, 3 the
-                               tensor-core FP32 kernels (3xTF32 mma) for
-                               2m = 8; other combinations use 0.  Results
-                               equal up to the arithmetic's rounding        */
+    int team[3];            /* launch shape of the spreading kernel per NFFT
+                               arithmetic (index NLH_FP64, NLH_FP32,
+                               NLH_DF32): 0 default, 1 and 2 the
+                               alternatives compiled for 2m = 8 and 12;
+                               other combinations use 0.  Results equal up
+                               to the arithmetic's rounding                 */
+    int window_first;       /* with window_count > 0: the plan holds windows */
+    int window_count;       /* window_first .. window_first + window_count - 1
+                               of the L listed (0: all).  The torus map is
+                               taken over all L windows and sums are
+                               normalised by L, so plans of complementary
+                               ranges add up to the plan of all windows      */
+    nlh_reduce_fn reduce;   /* range plans: NULL, or the sum over ranks.
+                               With it every op of nlh_matvec, the degrees
+                               and the solves are those of all L windows;
+                               without it only op 0 (the range's share of
+                               Gamma_full x) is defined                      */
+    void *reduce_ctx;       /* passed to reduce                              */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
  * the affine map onto the torus x~ = s (x - c_l) with c_l the per-window
  * midrange and s = torus_fill / (largest per-dim range), the sort of the
- * points by grid cell, the per-point window weights, the Fourier multiplier
+ * points by grid cell with each point's offset inside its cell (the window
+ * weights are evaluated from it in every matvec), the Fourier multiplier
  * tables and the degrees d = Gamma_full 1 (one matvec per precision built).
  *   features  device, N x D FP64 row-major (e.g. from nlh_patch_features).
  * Synchronises `stream`.  Errors: NLH_ERR_ARG, NLH_ERR_OOM, NLH_ERR_CUDA. */
@@ -120,6 +142,7 @@ typedef struct {
     int64_t n_units;                 /* work units (one CTA each)            */
     int max_items_pts, unit_points;  /* current tiling of the work           */
     int team[3];                     /* current launch shapes (see desc)     */
+    int window_first, window_count;  /* the plan's window range              */
 } nlh_plan_info;
 
 nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
@@ -133,35 +156,18 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);
  * solve.  Synchronises `stream`. */
 nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, void *stream);
 
-/* Set the launch shape (0..3; see nlh_plan_desc.team) of the spread and
- * interpolation kernels of one NFFT arithmetic (NLH_FP64, NLH_FP32,
- * NLH_DF32).  Changes no result beyond rounding.  A change of shape drops
- * the cached solve graphs and recomputes the degrees on the stream of the
- * plan's last call, which it synchronises. */
+/* Set the launch shape (0..2; see nlh_plan_desc.team) of the spreading
+ * kernel of one NFFT arithmetic (NLH_FP64, NLH_FP32, NLH_DF32).  Changes no
+ * result beyond rounding.  A change of shape drops the cached solve graphs
+ * and recomputes the degrees on the stream of the plan's last call, which it
+ * synchronises. */
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape);
-
-/* Interpolation kernel of every NFFT arithmetic (Sec. 3, the NFFT
- * evaluation at the points):
- *   NLH_INTERP_POINTS (default) one point per lane: a warp takes 32
- *       consecutive sorted points of a work unit and each lane sums its
- *       point's (2m)^3 stencil from the tile staged in shared memory;
- *   NLH_INTERP_TEAMS  the team kernel of nlh_plan_desc.team: threads own
- *       (y, z) stencil rows and each point's sum is reduced across lanes.
- * (The tensor-core FP32 shape 3 keeps its own interpolation; stencil widths
- * 2m other than 8 and 12 always use the team kernel.)  Results
- * agree to the arithmetic's rounding.  A change drops the cached solve
- * graphs and recomputes the degrees on the stream of the plan's last call,
- * which it synchronises.  Errors: NLH_ERR_ARG. */
-enum { NLH_INTERP_POINTS = 0, NLH_INTERP_TEAMS = 1 };
-nlh_status nlh_plan_set_interp(nlh_plan plan, int kind);
 
 /* Autotuner: time `reps` matvecs (0 = 3) of every NFFT arithmetic in the
  * bit mask `precisions` (0 = all the plan built) for each tiling of a fixed
  * grid (max_items_pts in {32, 64, 128, 256} x unit_points in {256, 512, 1024,
  * 2048}) and, per arithmetic, each launch shape; leave the plan in the
- * tiling with the smallest sum over the arithmetics of their fastest shape
- * among 0-2 (shape 3 changes the FP32 rounding and thereby the mixed form's
- * iteration counts, which this timing does not measure),
+ * tiling with the smallest sum over the arithmetics of their fastest shape,
  * with those shapes; report it (any output pointer may be NULL; best_team
  * has 3 entries indexed like nlh_plan_desc.team) and its summed matvec time
  * in ms.  Like nlh_plan_retile it recomputes the degrees and drops cached
@@ -178,9 +184,15 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
  *   op 2: y = (alpha I + L) x
  * precision: NLH_FP64, NLH_FP32 or NLH_DF32 (the NFFT stages; the output is
  * FP64).
- * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers).  The
- * call does not synchronise: a device-side failure (NLH_ERR_TIMEOUT) is
- * reported by the next synchronising call on the plan. */
+ * A matvec is six kernel launches (spread, three convolution passes,
+ * interpolation, and the epilogue over the pixels); the per-window
+ * contributions of a pixel are summed with FP64 atomics, so results may
+ * differ between calls in the last bits.
+ * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers, op 1 or
+ * 2 on a window-range plan without a reduce callback).  The call does not
+ * synchronise; the NFFT kernels validate the plan's work-unit, item and
+ * permutation indices, skip any that are out of range and record it, and
+ * the next synchronising call on a plan reports it (NLH_ERR_CUDA). */
 nlh_status nlh_matvec(nlh_plan plan, int op, int precision, double alpha,
                       const double *x, double *y, void *stream);
 
@@ -296,10 +308,12 @@ const char *nlh_version(void);
  * 4096 elements); larger N returns NLH_ERR_ARG.  Nothing in the array must
  * start at zero: every call overwrites the slots it reads.  All calls, on
  * every stream, share that array, so calls that overlap on the GPU race and
- * must be ordered by the caller.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  The call allocates
- * nothing and does not synchronise. */
+ * must be ordered by the caller.  A call outside stream capture looks up
+ * the array's device address (cudaGetSymbolAddress, with the calling
+ * thread's current device); a call on a stream that is being captured uses
+ * the address of the last call outside capture on that device, so make one
+ * call on each device before any capture (after a device reset, again).
+ * The call allocates nothing and does not synchronise. */
 nlh_status nlh_residual_norms_noalloc(const double *b, const double *q,
                                       int64_t N, double *res, double *norms,
                                       void *stream);

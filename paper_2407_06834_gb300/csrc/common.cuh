@@ -2,6 +2,11 @@
 //
 // Device data layout of a plan (all device arrays are owned by the plan):
 //   perm     [L*N]   int32   sorted position s (window l = s / N) -> pixel
+//   yhi, ylo [L*N][3] float  offset y = 2 f - 1 of each sorted point inside
+//                             its grid cell, per dim, as a float and the
+//                             float remainder (ylo only with an FP64-accurate
+//                             path); the window weights are evaluated from
+//                             these in the kernels (window.cuh)
 //   items    [n_items] int4  {window << 16 | lz << 6 | ly << 3 | lx, tile,
 //                             first sorted position, point count}: (lx, ly,
 //                             lz) is the cell inside its kTile^3 tile; the
@@ -10,16 +15,15 @@
 //   units    [n_units] int4  {window, tile (z*nt+y)*nt+x, first item, item
 //                             count}: a run of items inside one tile with at
 //                             most ~kUnitPoints points; one CTA per unit
-//   wts64/32 [L*N][PWP]      Kaiser-Bessel weights of each sorted point:
-//                             3 dims x 2m grid points cell-m+1 .. cell+m,
-//                             the record padded to PWP values (16 bytes)
-//   grid64/32 [L][n][n][n]   oversampled grids, x fastest; zero between
-//                             matvecs (the epilogue clears them)
+//   gridA/B  [L][n][n][n]    oversampled grids, x fastest, per arithmetic
+//                             (FP64 grids also serve double-float): A is
+//                             spread into and cleared again by the first
+//                             convolution pass, B holds the convolved grid
 //   tab64/32 [n]             per-dim Fourier multiplier in bit-reversed order
 //   tw64/32  [n/2]           FFT twiddles exp(-2 pi i j / n)
-//   Y        [L][N]          per-window interpolated values, pixel order
+//   yacc     [N]             per-pixel sum over windows (zero between
+//                             matvecs; the finishing pass clears it)
 //   d64/d32/ddf [N]          degrees d = Gamma_full 1 of each NFFT arithmetic
-//   wtsdf    [L*N][6m]        double-float records: per dim 2m high, 2m low
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -29,6 +33,7 @@
 #include <vector>
 
 #include "../../include/nlh.h"
+#include "window.cuh"
 
 namespace nlh {
 
@@ -100,13 +105,19 @@ constexpr int kMaxHist = 4096;
 constexpr int kTile = 8;          // tile edge in grid cells (spread/interp units)
 constexpr int kUnitPoints = 512;  // default points per work unit before a tile is split
 constexpr int kUnitItems = 256;   // items per work unit (staged in shared memory)
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs; grid-stride loops beyond
+constexpr int kPqSlots = 2 * kRedBlocks;  // block partials of x^T y from the interpolation
 
 struct Plan {
     int64_t N = 0;
     int D = 0, L = 0, M = 0, n = 0, m = 0, W2 = 0, precision = 0, kmax = 64;
+    int L_norm = 0;            // windows the kernel sum is normalised by (all windows)
+    int window_first = 0;      // first window of the plan in the full list
+    nlh_reduce_fn reduce_fn = nullptr;  // sums a range plan's share over ranks
+    void *reduce_ctx = nullptr;
     int unit_points = kUnitPoints;
-    int team[3] = {0, 0, 0};   // spread / interpolation team shape per arithmetic
-    int interp_kind = 0;       // NLH_INTERP_POINTS or NLH_INTERP_TEAMS
+    int team[3] = {0, 0, 0};   // spreading team shape per arithmetic
     double *pb2 = nullptr;     // (d' - 1) / L for P_b' (d' = Gamma_full 1 at sigma / sqrt 2)
     double pb2_sigma = -1.0;   // sigma pb2 was computed for
     int pc_kind = 0;           // preconditioner of the current solve: 0 P_a, 1 P_b'
@@ -119,24 +130,25 @@ struct Plan {
     int4 *units = nullptr;
     int64_t n_units = 0;          // host copy of the unit count (-1: on the device only)
     int64_t units_cap = 0;        // capacity of `units` (an upper bound of the count)
-    double *wts64 = nullptr;
-    float *wts32 = nullptr;
-    float *wtsdf = nullptr;       // double-float records: per dim 2m high then 2m low parts
+    float *yhi = nullptr, *ylo = nullptr;  // cell offsets of the sorted points
+    WinPoly<float> wp32;          // window polynomials per arithmetic (kernel parameters)
+    WinPoly<double> wp64;
+    WinPoly<df32> wpdf;
+    float4 *wstage = nullptr;     // device: staged FP64 then double-float coefficient tables
     double *tab64 = nullptr;
     float *tab32 = nullptr;
     double2 *tw64 = nullptr;
     float2 *tw32 = nullptr;
     float2 *tabdf = nullptr;      // double-float multiplier (hi, lo)
     float4 *twdf = nullptr;       // double-float twiddles (re hi, re lo, im hi, im lo)
-    double *grid64 = nullptr;
-    float *grid32 = nullptr;
-    double *Y = nullptr;
-    double *xs = nullptr;         // [L*N] matvec input in sorted order (T)
+    double *gridA64 = nullptr, *gridB64 = nullptr;
+    float *gridA32 = nullptr, *gridB32 = nullptr;
+    double *yacc = nullptr;       // [N] per-pixel sum over windows
     double *d64 = nullptr, *d32 = nullptr, *ddf = nullptr;
     // solver workspace
     double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
            *t = nullptr, *rhs = nullptr, *pinv = nullptr, *x0 = nullptr, *cbuf = nullptr;
-    double *partials = nullptr;   // kRedBlocks * 12 doubles
+    double *partials = nullptr;   // kRedBlocks * 12 + kPqSlots doubles
     SolveState *st = nullptr;     // device
     int *err = nullptr;           // device error word (bounded waits that gave up)
     int *unit_ctr = nullptr;      // device [2]: next unit of spread / interpolation
@@ -173,9 +185,6 @@ struct Plan {
     }
     ~Plan();
 };
-
-constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 608;   // 4 x 152 SMs; grid-stride loops beyond
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {
@@ -218,11 +227,17 @@ __device__ __forceinline__ double reduce_partials(const double *parts, int npart
 
 // ---------------------------------------------------------------- host API (internal)
 void plan_tables(Plan &P, cudaStream_t s);
+// Resolves every NFFT kernel on the current device (once per device).
+void prepare_nfft_kernels();
+// First failed index check of the NFFT kernels since the last call (check
+// id, index, bound, block, thread in info5; 0 = none), cleared; synchronous.
+int nfft_check_take(int *info5);
 void ensure_pb2(Plan &P, cudaStream_t s);
 // Keep freed pool memory in the process (set once).
 void retain_pool_memory();
-// Throws Failure{NLH_ERR_TIMEOUT} if a kernel recorded a bounded wait that
-// gave up (synchronises s).
+// Throws Failure{NLH_ERR_CUDA} if an NFFT kernel's index check failed,
+// Failure{NLH_ERR_TIMEOUT} if a kernel recorded a bounded wait that gave up
+// (synchronises s).
 void check_device_error(Plan &P, cudaStream_t s);
 cudaStream_t take_capture_stream(int device);
 void plan_degrees(Plan &P, cudaStream_t s);
@@ -246,10 +261,6 @@ __device__ __forceinline__ int reflect_index(int i, int n) {
     return i;
 }
 
-// Values per padded weight record (a multiple of 16 bytes).
-inline int record_len(int W2, int elem_bytes) {
-    return ((3 * W2 * elem_bytes + 15) / 16) * 16 / elem_bytes;
-}
 
 }  // namespace nlh
 

@@ -5,22 +5,31 @@
 //   convolve G'_l = IFFT(w .* FFT(G_l)) per axis (w: Gaussian coefficients
 //            over the squared window transform, |k| < M/2)
 //   interp   y_{l,i} = sum_g G'_l[g] prod_d phi(x~_{i,d} - g_d/n)  (NFFT)
-// and the epilogue y = (1/L) sum_l y_l  (= Gamma_full v), optionally
-// L v = d o v - y or (alpha I + L) v, fused with the dot x^T y for CG.
+// and the epilogue y = (1/L) sum_l y_l (= Gamma_full v), L v = d o v - y or
+// (alpha I + L) v (Sec. 2.3, Eq. discretized-state), with the block partial
+// sums of v^T y for CG.
+//
+// A matvec is spread (which gathers v through the sort permutation itself),
+// three axis passes of the convolution (the first also clears the spread
+// grid for the next matvec), the interpolation, which adds every window's
+// value into a per-pixel sum, and one finishing pass over the pixels with
+// the epilogue (a plan of one window finishes inside the interpolation).
+// No per-point data is stored beyond the sort permutation and the points'
+// offsets inside their grid cells: the window weights are evaluated in
+// registers from those offsets (window.cuh).
 //
 // Work decomposition: points are sorted by grid cell; a work item is up to
-// kmax points of one cell, which share one 2m x 2m x 2m stencil.  One CTA
-// per item keeps the item's stencil (spreading accumulators or interpolation
-// grid values) in registers, so the inner loop is pure FMA: no atomics per
-// point.  Spreading flushes each item's accumulators with one atomic add per
-// stencil cell.
+// kmax points of one cell, which share one 2m x 2m x 2m stencil; a work unit
+// is a run of items inside one 8^3-cell tile (one CTA at a time, persistent
+// CTAs take units from a global counter).
 #include "common.cuh"
 
 #include <type_traits>
-#include "async_copy.cuh"
 #include "df32.cuh"
+#include "window.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace nlh {
 
@@ -41,10 +50,8 @@ template <typename C> __device__ __forceinline__ C cshfl(C a, int o) {
     return {__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)};
 }
 
-constexpr int kChunk = 32;  // points staged in shared memory at a time
-
-// Storage of one arithmetic: R = element of the weight records, G = grid
-// element.  A weight record holds, per dim t, 2m values (R = T) or, for
+// Storage of one arithmetic: R = element of the staged weight records, G =
+// global grid element.  A record holds, per dim t, 2m values (R = T) or, for
 // df32, 2m high parts followed by 2m low parts.
 template <typename T> struct Num { using R = T; using G = T; static constexpr int kParts = 1; };
 template <> struct Num<df32> { using R = float; using G = double; static constexpr int kParts = 2; };
@@ -76,8 +83,32 @@ NLH_REC_DF(14)
 NLH_REC_DF(16)
 #undef NLH_REC_DF
 
+template <typename T, int W2>
+__device__ __forceinline__ void rec_put(typename Num<T>::R *wp, int t, int j, T v) {
+    wp[t * W2 + j] = v;
+}
+template <int W2> struct RecPutDF {
+    static __device__ __forceinline__ void put(float *wp, int t, int j, df32 v) {
+        wp[t * 2 * W2 + j] = v.hi;
+        wp[t * 2 * W2 + W2 + j] = v.lo;
+    }
+};
+#define NLH_RECPUT_DF(W)                                                                     \
+    template <>                                                                              \
+    __device__ __forceinline__ void rec_put<df32, W>(float *wp, int t, int j, df32 v) {      \
+        RecPutDF<W>::put(wp, t, j, v);                                                       \
+    }
+NLH_RECPUT_DF(4)
+NLH_RECPUT_DF(6)
+NLH_RECPUT_DF(8)
+NLH_RECPUT_DF(10)
+NLH_RECPUT_DF(12)
+NLH_RECPUT_DF(14)
+NLH_RECPUT_DF(16)
+#undef NLH_RECPUT_DF
+
 // A team is NW warps; a CTA holds TPB teams.  Teams synchronise among
-// themselves only (a warp sync, or a named barrier for two-warp teams).
+// themselves only (a warp sync, or a named barrier for multi-warp teams).
 template <int NW>
 __device__ __forceinline__ void team_sync(int team) {
     if (NW == 1) {
@@ -87,28 +118,15 @@ __device__ __forceinline__ void team_sync(int team) {
     }
 }
 
-// Weight record of one point: 3 x 2m values padded to a multiple of 16
-// bytes so that a chunk of records is one bulk copy.
+// Weight record of one point staged in shared memory: 3 x 2m values padded
+// to a multiple of 16 bytes (vector loads of the x line).
 template <typename T, int W2>
 constexpr int padded_record() {
     using R = typename Num<T>::R;
     return ((3 * Num<T>::kParts * W2 * (int)sizeof(R) + 15) / 16) * 16 / (int)sizeof(R);
 }
 
-constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-// Shared memory of one unit: the tile region (kTile + 2m - 1)^3, per team
-// two staging buffers of kChunk weight records, two mbarriers, a status word
-// and kChunk reduction slots.
-template <typename T, int W2, int TPB>
-struct UnitSmem {
-    static constexpr int E = kTile + W2 - 1, E3 = E * E * E, PWP = padded_record<T, W2>();
-    static constexpr size_t tile = align16(sizeof(T) * E3);
-    static constexpr size_t stage = align16(sizeof(typename Num<T>::R) * kChunk * PWP);
-    // per team: two staging buffers, two mbarriers, a status word and a slot,
-    // and the per-warp point totals of a chunk (up to 4 warps per team)
-    static constexpr size_t team = 2 * stage + 2 * sizeof(uint64_t) + 16 + align16(sizeof(T) * kChunk * 4);
-};
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 __device__ __forceinline__ void tile_origin(int tile, int n, int &tx0, int &ty0, int &tz0) {
     const int nt = n / kTile;
@@ -155,79 +173,14 @@ __device__ __forceinline__ ChunkCursor make_cursor(const int4 *s_items, int ii, 
     return ChunkCursor{ii, 0, it.z, it.w, it.x};
 }
 
-template <int NW>
+template <int NW, int CH>
 __device__ __forceinline__ ChunkCursor next_chunk(const ChunkCursor &c, const int4 *s_items,
                                                   int nit, int *s_next, int *s_slot, int team,
                                                   int tid) {
     ChunkCursor d = c;
-    d.c0 += kChunk;
+    d.c0 += CH;
     if (d.c0 < d.cnt) return d;
     return make_cursor(s_items, fetch_item<NW>(s_next, s_slot, team, tid), nit);
-}
-
-// Per-team staging pipeline: thread 0 of the team issues the bulk copy of
-// a chunk's weight records and waits for it (bounded); the team then reads.
-template <typename T, int W2, int NW>
-struct Stager {
-    using R = typename Num<T>::R;
-    static constexpr int PWP = padded_record<T, W2>();
-    // two buffers, selected by b in {0, 1} without indexing an array (so the
-    // state stays in registers)
-    R *buf0, *buf1;
-    uint64_t *bar;
-    volatile int *flag;
-    uint32_t phase0, phase1;
-    bool pending0, pending1;
-    int team, tid;
-
-    __device__ __forceinline__ R *buf(int b) const { return b ? buf1 : buf0; }
-
-    __device__ __forceinline__ void issue(int b, const R *wts, const ChunkCursor &c) {
-        if (tid == 0) {
-            const int cn = min(kChunk, c.cnt - c.c0);
-            const uint32_t bytes = (uint32_t)(cn * PWP * sizeof(R));
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[b], bytes);
-            bulk_copy_g2s(buf(b), wts + (int64_t)(c.start + c.c0) * PWP, bytes, &bar[b]);
-        }
-        if (b) pending1 = true; else pending0 = true;
-    }
-
-    // Returns false if the copy timed out (the team then stops).
-    __device__ __forceinline__ bool wait(int b, int *err) {
-        const uint32_t ph = b ? phase1 : phase0;
-        if (tid == 0) *flag = mbar_wait_bounded(&bar[b], ph, err) ? 1 : 0;
-        team_sync<NW>(team);
-        bool ok = *flag != 0;
-        if (ok) ok = mbar_try_wait(&bar[b], ph);  // acquire for every reader
-        if (b) { phase1 ^= 1u; pending1 = false; } else { phase0 ^= 1u; pending0 = false; }
-        return ok;
-    }
-
-    // On an early exit: wait (bounded) for copies still in flight.
-    __device__ __forceinline__ void drain(int *err) {
-        if (tid != 0) return;
-        if (pending0) mbar_wait_bounded(&bar[0], phase0, err);
-        if (pending1) mbar_wait_bounded(&bar[1], phase1, err);
-    }
-};
-
-// Team area: two staging buffers, two mbarriers, a status word, a
-// broadcast slot, kChunk reduction values.
-template <typename T, int W2, int NW, int TPB>
-__device__ __forceinline__ Stager<T, W2, NW> make_stager(unsigned char *team_base, int team,
-                                                         int tid) {
-    using SM = UnitSmem<T, W2, TPB>;
-    Stager<T, W2, NW> st;
-    st.buf0 = reinterpret_cast<typename Num<T>::R *>(team_base);
-    st.buf1 = reinterpret_cast<typename Num<T>::R *>(team_base + SM::stage);
-    st.bar = reinterpret_cast<uint64_t *>(team_base + 2 * SM::stage);
-    st.flag = reinterpret_cast<volatile int *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t));
-    st.phase0 = st.phase1 = 0u;
-    st.pending0 = st.pending1 = false;
-    st.team = team;
-    st.tid = tid;
-    return st;
 }
 
 // Arithmetic on one x line of the stencil.  On the FP32 path a line of 2m
@@ -247,6 +200,10 @@ template <typename T, int W2> struct Line {
             v[a + 1] = q.y;
         }
     }
+    __device__ __forceinline__ void from(const T (&w)[W2]) {
+#pragma unroll
+        for (int a = 0; a < W2; ++a) v[a] = w[a];
+    }
     __device__ __forceinline__ void axpy(T s, const Line &w) {  // v += s w
 #pragma unroll
         for (int a = 0; a < W2; ++a) v[a] = fma(s, w.v[a], v[a]);
@@ -258,7 +215,6 @@ template <typename T, int W2> struct Line {
         return in;
     }
     __device__ __forceinline__ T get(int a) const { return v[a]; }
-    __device__ __forceinline__ void set(int a, T x) { v[a] = x; }
     __device__ __forceinline__ void load_cells(const T *row) {  // 2m consecutive cells
 #pragma unroll
         for (int a = 0; a < W2; ++a) v[a] = row[a];
@@ -276,9 +232,12 @@ template <int W2> struct Line<float, W2> {
 #pragma unroll
         for (int a = 0; a < W2 / 2; ++a) v[a] = reinterpret_cast<const unsigned long long *>(src)[a];
     }
+    __device__ __forceinline__ void from(const float (&w)[W2]) {
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) v[a] = pk_make(w[2 * a], w[2 * a + 1]);
+    }
     __device__ __forceinline__ void axpy(float s, const Line &w) {
-        unsigned long long ss;
-        asm("mov.b64 %0, {%1, %1};" : "=l"(ss) : "f"(s));
+        const unsigned long long ss = pk_dup(s);
 #pragma unroll
         for (int a = 0; a < W2 / 2; ++a)
             asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(v[a]) : "l"(ss), "l"(w.v[a]));
@@ -289,24 +248,17 @@ template <int W2> struct Line<float, W2> {
         for (int a = 0; a < W2 / 2; ++a)
             asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(v[a]), "l"(h.v[a]));
         float lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc));
+        pk_split(acc, lo, hi);
         return lo + hi;
     }
     __device__ __forceinline__ float get(int a) const {
         float lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v[a / 2]));
+        pk_split(v[a / 2], lo, hi);
         return (a & 1) ? hi : lo;
-    }
-    __device__ __forceinline__ void set(int a, float x) {
-        float lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v[a / 2]));
-        if (a & 1) hi = x; else lo = x;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(v[a / 2]) : "f"(lo), "f"(hi));
     }
     __device__ __forceinline__ void load_cells(const float *row) {  // 2m consecutive cells
 #pragma unroll
-        for (int a = 0; a < W2 / 2; ++a)
-            asm("mov.b64 %0, {%1, %2};" : "=l"(v[a]) : "f"(row[2 * a]), "f"(row[2 * a + 1]));
+        for (int a = 0; a < W2 / 2; ++a) v[a] = pk_make(row[2 * a], row[2 * a + 1]);
     }
 };
 
@@ -323,6 +275,13 @@ template <int W2> struct Line<df32, W2> {
         for (int a = 0; a < W2 / 2; ++a) {
             h[a] = reinterpret_cast<const unsigned long long *>(src)[a];
             l[a] = reinterpret_cast<const unsigned long long *>(src + W2)[a];
+        }
+    }
+    __device__ __forceinline__ void from(const df32 (&w)[W2]) {
+#pragma unroll
+        for (int a = 0; a < W2 / 2; ++a) {
+            h[a] = pk_make(w[2 * a].hi, w[2 * a + 1].hi);
+            l[a] = pk_make(w[2 * a].lo, w[2 * a + 1].lo);
         }
     }
     __device__ __forceinline__ void axpy(df32 s, const Line &w) {  // this += s w
@@ -346,14 +305,6 @@ template <int W2> struct Line<df32, W2> {
         pk_split(h[a / 2], h0, h1);
         pk_split(l[a / 2], l0, l1);
         return (a & 1) ? df32(h1, l1) : df32(h0, l0);
-    }
-    __device__ __forceinline__ void set(int a, df32 x) {
-        float h0, h1, l0, l1;
-        pk_split(h[a / 2], h0, h1);
-        pk_split(l[a / 2], l0, l1);
-        if (a & 1) { h1 = x.hi; l1 = x.lo; } else { h0 = x.hi; l0 = x.lo; }
-        h[a / 2] = pk_make(h0, h1);
-        l[a / 2] = pk_make(l0, l1);
     }
     __device__ __forceinline__ void load_cells(const df32 *row) {  // 2m consecutive cells
 #pragma unroll
@@ -384,368 +335,274 @@ struct Pairs {
     }
 };
 
-// Shared carve-up common to both kernels: tile region, item records, the
-// CTA's item counter, then TPB team areas.
-template <typename T, int W2, int TPB>
-struct UnitLayout {
-    using SM = UnitSmem<T, W2, TPB>;
-    static constexpr size_t items_off = SM::tile;
-    static constexpr size_t next_off = items_off + sizeof(int4) * kUnitItems;  // 4 ints:
-    // [0] item counter, [1] current unit, [2] abort flag
-    static constexpr size_t teams_off = next_off + 16;
-    static constexpr size_t bytes = teams_off + TPB * SM::team;
+// The offset y = 2 f - 1 of a point inside its grid cell (per dim), stored
+// as a float and the float remainder; each arithmetic reads what it needs.
+template <typename T> struct Offs;
+template <> struct Offs<float> {
+    static __device__ __forceinline__ float get(const float *hi, const float *, int64_t k) {
+        return __ldg(hi + k);
+    }
+};
+template <> struct Offs<double> {
+    static __device__ __forceinline__ double get(const float *hi, const float *lo, int64_t k) {
+        return (double)__ldg(hi + k) + (double)__ldg(lo + k);
+    }
+};
+template <> struct Offs<df32> {
+    static __device__ __forceinline__ df32 get(const float *hi, const float *lo, int64_t k) {
+        return df32(__ldg(hi + k), __ldg(lo + k));
+    }
 };
 
+template <typename T> __device__ __forceinline__ T from_double(double v) { return T(v); }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
+
+// Plan data every NFFT kernel reads (device pointers of the plan).
+struct NfftArgs {
+    const int4 *units;
+    const int *n_units;  // device copy of the unit count
+    int *unit_ctr;       // [0] next spreading unit, [1] next interpolation unit
+    const int4 *items;
+    const int *perm;     // sorted position -> pixel (window-major)
+    const float *yhi, *ylo;  // [sorted position][3] cell offsets y = 2 f - 1
+    int n, m;
+    int L;               // windows of the plan (units' window index < L)
+    int64_t N;           // pixels (permutation entries < N; sorted positions < L N)
+    const float4 *wstage;  // staged window coefficients of the arithmetic (FP64, df32)
+};
+
+// Index checks on the plan data the NFFT kernels read from memory (unit and
+// item records, permutation entries) and on the shared-memory rows they
+// derive from them.  A failed check records, library-wide, the first
+// failure (check id, index, bound, block, thread), which the next
+// synchronising call of any plan reports (nfft_check_take), and the access
+// is skipped: corrupt plan data becomes an error status, never an
+// out-of-range access.
+__device__ int g_nfft_check[5];
+
+__device__ __forceinline__ bool idx_ok(bool cond, int id, long long idx, long long bound) {
+    if (cond) return true;
+    if (atomicCAS(&g_nfft_check[0], 0, id) == 0) {
+        g_nfft_check[1] = (int)idx;
+        g_nfft_check[2] = (int)bound;
+        g_nfft_check[3] = blockIdx.x;
+        g_nfft_check[4] = threadIdx.x;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------------ spreading
+// Shared memory of a spreading CTA: the tile region (kTile + 2m - 1)^3, the
+// unit's items, control words, one broadcast slot per team, and per team the
+// weight records of one chunk of NT points.
+template <typename T, int W2, int NW, int TPB>
+struct SpreadSmem {
+    static constexpr int NT = 32 * NW, E = kTile + W2 - 1, E3 = E * E * E;
+    static constexpr int PWP = padded_record<T, W2>();
+    static constexpr size_t tile = align16(sizeof(T) * E3);
+    static constexpr size_t items_off = tile;
+    static constexpr size_t ctl_off = items_off + sizeof(int4) * kUnitItems;  // [0] items, [1] unit
+    static constexpr size_t stage_off = ctl_off + 16;  // double-float coefficients
+    static constexpr size_t slots_off = stage_off + kWinStageBytes;
+    static constexpr size_t team_bytes = align16(sizeof(typename Num<T>::R) * NT * PWP);
+    static constexpr size_t teams_off = slots_off + align16(sizeof(int) * TPB);
+    static constexpr size_t bytes = teams_off + TPB * team_bytes;
+};
+
 // Persistent CTAs take units from a global counter (units are stored in
-// decreasing size).  Per unit, each team takes items; a thread owns PPT
-// (y, z) stencil pairs with their full x line of 2m accumulators, summed in
-// registers over the item's points (all points of an item share the
-// stencil).  Items are then added into the shared tile, and the tile is
-// added into the global grid once (non-zero entries only).  xs holds the
-// input vector in sorted order.
+// decreasing size).  Per unit, each team takes items; per chunk of NT points
+// of an item every thread reads one point (its pixel through the sort
+// permutation, the input value there, its cell offsets), evaluates the
+// point's 3 x 2m window weights and stages them; then each thread adds the
+// chunk's points into its PPT (y, z) stencil pairs, each a full x line of 2m
+// accumulators in registers (all points of an item share the stencil).  An
+// item's accumulators are then added into the shared tile, and the tile into
+// the global grid once (non-zero entries only).
 template <typename T, int W2, int NW, int TPB, int MINB = 1>
 __global__ void __launch_bounds__(32 * NW * TPB, MINB)
-k_spread(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
-         int *__restrict__ unit_ctr,
-         const int4 *__restrict__ items, const typename Num<T>::R *__restrict__ wts,
-         const T *__restrict__ xs, typename Num<T>::G *__restrict__ grid, int n, int m,
-         const int *__restrict__ done, int *__restrict__ err) {
+k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__restrict__ x,
+         typename Num<T>::G *__restrict__ grid, const int *__restrict__ done) {
     using R = typename Num<T>::R;
     using G = typename Num<T>::G;
-    using SM = UnitSmem<T, W2, TPB>;
-    using LY = UnitLayout<T, W2, TPB>;
-    constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
+    using SM = SpreadSmem<T, W2, NW, TPB>;
+    constexpr int NT = SM::NT, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
     constexpr int E = SM::E, E3 = SM::E3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + SM::items_off);
+    int *s_ctl = reinterpret_cast<int *>(smem_raw + SM::ctl_off);
+    float4 *s_coef = reinterpret_cast<float4 *>(smem_raw + SM::stage_off);
     if (done && *done) return;
-    const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31;
-    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
-    auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
-    int *s_slot = const_cast<int *>(st.flag) + 1;
-    if (tid == 0) {
-        mbar_init(&st.bar[0], 1);
-        mbar_init(&st.bar[1], 1);
-        mbar_fence_init();
-    }
-    if (threadIdx.x == 0) s_ctl[2] = 0;
+    if constexpr (!std::is_same<T, float>::value) win_stage(a.wstage, s_coef);
+    // the interpolation of the previous matvec has finished (stream order)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.unit_ctr[1] = 0;
+    const int team = threadIdx.x / NT, tid = threadIdx.x % NT;
+    R *rec = reinterpret_cast<R *>(smem_raw + SM::teams_off + team * SM::team_bytes);
+    int *s_slot = reinterpret_cast<int *>(smem_raw + SM::slots_off) + team;
     Pairs<W2, NT, PPT> pr;
     pr.init(tid);
-    const int msk = n - 1;
+    const int msk = a.n - 1, m = a.m;
     while (true) {
         __syncthreads();  // previous unit fully flushed
-        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
+        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(&a.unit_ctr[0], 1);
         __syncthreads();
         const int uidx = s_ctl[1];
-        if (uidx >= *n_units_dev || s_ctl[2]) break;
-        const int4 un = units[uidx];
+        if (uidx >= *a.n_units) break;
+        const int4 un = a.units[uidx];
         const int l = un.x, it0 = un.z, nit = un.w;
+        if (!idx_ok(nit >= 1 && nit <= kUnitItems && l >= 0 && l < a.L, 1, nit, l)) break;
         int tx0, ty0, tz0;
-        tile_origin(un.y, n, tx0, ty0, tz0);
+        tile_origin(un.y, a.n, tx0, ty0, tz0);
         for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = T(0);
-        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = a.items[it0 + e];
         if (threadIdx.x == 0) s_ctl[0] = TPB;
         __syncthreads();
         Line<T, W2> acc[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) acc[k].zero();
         ChunkCursor cur = make_cursor(s_items, team, nit);
-        T vcur = T(0);
-        if (cur.valid()) {
-            st.issue(0, wts, cur);
-            if (lane < cur.cnt) vcur = xs[cur.start + lane];
-        }
-        int bsel = 0;
         while (cur.valid()) {
-            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
-            T vnxt = T(0);
-            if (nxt.valid()) {
-                st.issue(bsel ^ 1, wts, nxt);
-                if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
+            const int cn = min(NT, cur.cnt - cur.c0);
+            if (tid < cn) {  // this thread's point: value, weights -> record
+                const int64_t sp = (int64_t)cur.start + cur.c0 + tid;
+                bool ok = idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N, 2, sp, 0);
+                const int pix = ok ? __ldg(a.perm + sp) : 0;
+                ok = ok && idx_ok(pix >= 0 && pix < a.N, 3, pix, sp);
+                const T v = ok ? from_double<T>(__ldg(x + pix)) : T(0);
+                R *mine = rec + tid * PWP;
+                // one dim at a time (keeps the Horner chains of the three
+                // dims out of each other's registers)
+#pragma unroll 1
+                for (int t = 0; t < 3; ++t) {
+                    T w[W2];
+                    win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, ok ? 3 * sp + t : 0), w);
+                    const T sc = t == 1 ? v : T(1);
+#pragma unroll
+                    for (int j = 0; j < W2; ++j) rec_put<T, W2>(mine, t, j, sc * w[j]);
+                }
             }
-            if (!st.wait(bsel, err)) {
-                st.drain(err);
-                s_ctl[2] = 1;
-                break;
-            }
-            const R *sw = st.buf(bsel);
-            const int cn = min(kChunk, cur.cnt - cur.c0);
+            team_sync<NW>(team);
+            if (!idx_ok(cn >= 0 && cn <= NT, 6, cn, NT)) break;
             for (int j = 0; j < cn; ++j) {
-                const R *wp = sw + j * PWP;
+                const R *wpp = rec + j * PWP;
                 Line<T, W2> wx;
-                wx.load(rec_line<T, W2>(wp, 0));
-                const T vj = __shfl_sync(0xffffffffu, vcur, j);
+                wx.load(rec_line<T, W2>(wpp, 0));
                 if (Pairs<W2, NT, PPT>::kSameB) {
-                    const T vb = vj * rec_val<T, W2>(wp, 1, pr.b0);
+                    const T vb = rec_val<T, W2>(wpp, 1, pr.b0);  // v wy[b]
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
-                        if (pr.ok[k]) acc[k].axpy(vb * rec_val<T, W2>(wp, 2, pr.cc[k]), wx);
+                        if (pr.ok[k]) acc[k].axpy(vb * rec_val<T, W2>(wpp, 2, pr.cc[k]), wx);
                 } else {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
                         if (pr.ok[k])
-                            acc[k].axpy(vj * rec_val<T, W2>(wp, 1, pr.bb[k]) *
-                                            rec_val<T, W2>(wp, 2, pr.cc[k]),
+                            acc[k].axpy(rec_val<T, W2>(wpp, 1, pr.bb[k]) *
+                                            rec_val<T, W2>(wpp, 2, pr.cc[k]),
                                         wx);
                 }
             }
-            if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
+            if (cur.c0 + NT >= cur.cnt) {  // last chunk of the item: add into the tile
                 int lx0, ly0, lz0;
                 item_local(cur.local, lx0, ly0, lz0);
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (pr.ok[k]) {
-                        T *row = S + ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
+                        const int ro = ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
+                        T *row = S + ro;
 #pragma unroll
-                        for (int a = 0; a < W2; ++a) atomicAdd(&row[a], acc[k].get(a));
+                        for (int q = 0; q < W2; ++q)
+                            if (idx_ok(ro + q >= 0 && ro + q < E3, 4, ro + q, E3)) atomicAdd(&row[q], acc[k].get(q));
                     }
                     acc[k].zero();
                 }
             }
-            team_sync<NW>(team);  // every read of buffer bsel is done before it is refilled
+            const ChunkCursor nxt = next_chunk<NW, NT>(cur, s_items, nit, s_ctl, s_slot, team, tid);
+            team_sync<NW>(team);  // every read of the records is done before they are rewritten
             cur = nxt;
-            vcur = vnxt;
-            bsel ^= 1;
         }
         __syncthreads();
-        G *g = grid + (int64_t)l * n * n * n;
+        G *g = grid + (int64_t)l * a.n * a.n * a.n;
         for (int e = threadIdx.x; e < E3; e += blockDim.x) {
             T val = S[e];
             if (val != T(0)) {
                 int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
                 int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
                     gz = (tz0 - m + 1 + ez) & msk;
-                atomicAdd(&g[((int64_t)gz * n + gy) * n + gx], (G)val);
+                if (idx_ok(e < E3, 5, e, E3)) atomicAdd(&g[((int64_t)gz * a.n + gy) * a.n + gx], (G)val);
             }
         }
     }
 }
 
-// ------------------------------------------------------------------ interpolation
-// Persistent CTAs over units as in k_spread.  The tile region of the
-// convolved grid is staged in shared memory; each team holds an item's
-// stencil in registers and sums every point's 2m^3 products.  The
-// per-thread partial sums of a chunk of 32 points are reduce-scattered over
-// the warp so that lane j ends with point j's value.
-template <typename T, int W2, int NW, int TPB>
-__global__ void __launch_bounds__(32 * NW * TPB, 1)
-k_interp(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
-         int *__restrict__ unit_ctr,
-         const int4 *__restrict__ items, const int *__restrict__ perm,
-         const typename Num<T>::R *__restrict__ wts, const typename Num<T>::G *__restrict__ grid,
-         double *__restrict__ Y, int n, int m, int64_t N, const int *__restrict__ done,
-         int *__restrict__ err) {
-    using R = typename Num<T>::R;
-    using G = typename Num<T>::G;
-    using SM = UnitSmem<T, W2, TPB>;
-    using LY = UnitLayout<T, W2, TPB>;
-    constexpr int NT = 32 * NW, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
-    constexpr int E = SM::E, E3 = SM::E3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *S = reinterpret_cast<T *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
-    if (done && *done) return;
-    const int team = threadIdx.x / NT, tid = threadIdx.x % NT, lane = tid & 31, warp = tid >> 5;
-    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
-    auto st = make_stager<T, W2, NW, TPB>(team_base, team, tid);
-    int *s_slot = const_cast<int *>(st.flag) + 1;
-    T *sred = reinterpret_cast<T *>(team_base + 2 * SM::stage + 2 * sizeof(uint64_t) + 16);
-    if (tid == 0) {
-        mbar_init(&st.bar[0], 1);
-        mbar_init(&st.bar[1], 1);
-        mbar_fence_init();
-    }
-    if (threadIdx.x == 0) s_ctl[2] = 0;
-    Pairs<W2, NT, PPT> pr;
-    pr.init(tid);
-    const int msk = n - 1;
-    while (true) {
-        __syncthreads();  // previous unit done with the tile
-        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
-        __syncthreads();
-        const int uidx = s_ctl[1];
-        if (uidx >= *n_units_dev || s_ctl[2]) break;
-        const int4 un = units[uidx];
-        const int l = un.x, it0 = un.z, nit = un.w;
-        int tx0, ty0, tz0;
-        tile_origin(un.y, n, tx0, ty0, tz0);
-        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-        if (threadIdx.x == 0) s_ctl[0] = TPB;
-        const G *g = grid + (int64_t)l * n * n * n;
-        {
-            constexpr int UNR = 8;
-            for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
-                G vals[UNR];
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    int e = base + u * blockDim.x;
-                    vals[u] = G(0);
-                    if (e < E3) {
-                        int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
-                        int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
-                            gz = (tz0 - m + 1 + ez) & msk;
-                        vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    int e = base + u * blockDim.x;
-                    if (e < E3) S[e] = T(vals[u]);
-                }
-            }
-        }
-        __syncthreads();
-        ChunkCursor cur = make_cursor(s_items, team, nit);
-        if (cur.valid()) st.issue(0, wts, cur);
-        int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
-        Line<T, W2> H[PPT];
-        int bsel = 0;
-        while (cur.valid()) {
-            if (cur.c0 == 0) {  // first chunk of an item: its stencil from the tile
-                int lx0, ly0, lz0;
-                item_local(cur.local, lx0, ly0, lz0);
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const T *row = S + ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
-#pragma unroll
-                    for (int a = 0; a < W2; ++a) H[k].set(a, pr.ok[k] ? row[a] : T(0));
-                }
-            }
-            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
-            int pnxt = 0;
-            if (nxt.valid()) {
-                st.issue(bsel ^ 1, wts, nxt);
-                if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
-            }
-            if (!st.wait(bsel, err)) {
-                st.drain(err);
-                s_ctl[2] = 1;
-                break;
-            }
-            const R *sw = st.buf(bsel);
-            const int cn = min(kChunk, cur.cnt - cur.c0);
-            // Points in groups of 8: each thread forms its partial sums for the
-            // group, an 8-lane reduce-scatter leaves lane l with the partial of
-            // point (l & 7) over its 8-lane group, and two shuffle-adds finish the
-            // warp sum.  A runtime loop over groups keeps the code small.
-            for (int g0 = 0; g0 < cn; g0 += 8) {
-                T part[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    T sum = T(0);
-                    const int j = g0 + jj;
-                    if (j < cn) {
-                        const R *wp = sw + j * PWP;
-                        Line<T, W2> wx;
-                        wx.load(rec_line<T, W2>(wp, 0));
-                        if (Pairs<W2, NT, PPT>::kSameB) {
-                            T zs = T(0);
-#pragma unroll
-                            for (int k = 0; k < PPT; ++k)
-                                if (pr.ok[k])
-                                    zs = fma(rec_val<T, W2>(wp, 2, pr.cc[k]), wx.dot(H[k]), zs);
-                            sum = rec_val<T, W2>(wp, 1, pr.b0) * zs;
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < PPT; ++k)
-                                if (pr.ok[k])
-                                    sum = fma(rec_val<T, W2>(wp, 1, pr.bb[k]) *
-                                                  rec_val<T, W2>(wp, 2, pr.cc[k]),
-                                              wx.dot(H[k]), sum);
-                        }
-                    }
-                    part[jj] = sum;
-                }
-#pragma unroll
-                for (int o = 4; o >= 1; o >>= 1) {
-                    const bool upper = lane & o;
-#pragma unroll
-                    for (int kk = 0; kk < o; ++kk) {
-                        T send = upper ? part[kk] : part[kk + o];
-                        T keep = upper ? part[kk + o] : part[kk];
-                        part[kk] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                    }
-                }
-                T tot = part[0];
-                tot = tot + __shfl_xor_sync(0xffffffffu, tot, 8);
-                tot = tot + __shfl_xor_sync(0xffffffffu, tot, 16);
-                if (NW > 1) {
-                    // each warp's totals of the chunk's points; summed once per chunk
-                    if (lane < 8) sred[warp * kChunk + g0 + lane] = tot;
-                } else {
-                    const int pidx = __shfl_sync(0xffffffffu, pcur, (g0 + lane) & 31);
-                    if (lane < 8 && g0 + lane < cn) Y[(int64_t)l * N + pidx] = (double)tot;
-                }
-            }
-            if (NW > 1) {
-                team_sync<NW>(team);
-                if (warp == 0 && lane < cn) {  // lane j holds point j's permutation entry
-                    T tot = sred[lane];
-#pragma unroll
-                    for (int w = 1; w < NW; ++w) tot = tot + sred[w * kChunk + lane];
-                    Y[(int64_t)l * N + pcur] = (double)tot;
-                }
-            }
-            team_sync<NW>(team);  // every read of buffer bsel (and sred) is done
-            cur = nxt;
-            pcur = pnxt;
-            bsel ^= 1;
-        }
-    }
+template <typename T> constexpr int spread_class() {
+    return sizeof(T) == 4 ? NLH_K_SPREAD32 : (Num<T>::kParts == 2 ? NLH_K_SPREADDF : NLH_K_SPREAD64);
 }
-
 template <typename T> constexpr int interp_class() {
     return sizeof(T) == 4 ? NLH_K_INTERP32 : (Num<T>::kParts == 2 ? NLH_K_INTERPDF : NLH_K_INTERP64);
 }
-template <typename T> constexpr int interp_class_pl() { return interp_class<T>(); }
 
-// ------------------------------------------------- interpolation, points on lanes
-// The same interpolation with one point per lane: a warp takes 32
-// consecutive (sorted) points of the unit, each lane finds its point's cell
-// among the unit's items (binary search on the first sorted positions),
-// holds its weight record in registers and evaluates
+// ------------------------------------------------- interpolation + epilogue
+// Epilogue of a matvec (Sec. 2.3, Eq. discretized-state): out = s for op 0,
+// d o x - s for op 1, alpha x + d o x - s for op 2, where s = inv_l sum_l y_l
+// over the plan's windows (inv_l = 1/L, or 1/(all windows) for a plan that
+// holds a range of them).
+struct Epilogue {
+    const double *x, *d;
+    double *y;
+    double *yacc;      // [N] running sum over windows, zero between matvecs
+    double *partials;  // [nparts] block partial sums of x^T out, or NULL
+    int nparts;
+    int L;             // windows of the plan
+    double inv_l;
+    int op;
+    double alpha;
+    const double *alpha_dev;  // alpha from device memory, or NULL
+};
+
+// One point per lane: a warp takes 32 consecutive (sorted) points of the
+// unit, each lane finds its point's cell among the unit's items (binary
+// search on the first sorted positions), evaluates its weights in registers
+// and sums
 //   y = sum_z wz[z] (wx . t_z),  t_z[x] = sum_y wy[y] S[z][y][x]
 // over its stencil in the staged tile region, with no cross-lane reduction
 // (consecutive points mostly share a cell, so their tile rows are the same
-// addresses).  Written straight to Y in pixel order.
-constexpr int kPlThreads = 256;
+// addresses).  The value is added into the pixel's sum over windows (FP64
+// atomic, so the order of the L additions, and the last bits of the result,
+// may differ between calls); k_finish applies the epilogue.
+constexpr int kInterpThreads = 256;
 
-template <typename T, int W2, int NTH = kPlThreads, int MINB = 1>
+template <typename T, int W2, int NTH = kInterpThreads, int MINB = 1>
 __global__ void __launch_bounds__(NTH, MINB)
-k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
-            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
-            const int *__restrict__ perm, const typename Num<T>::R *__restrict__ wts,
-            const typename Num<T>::G *__restrict__ grid, double *__restrict__ Y, int n, int m,
-            int64_t N, const int *__restrict__ done) {
-    using R = typename Num<T>::R;
+k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
+         const typename Num<T>::G *__restrict__ grid,
+         const Epilogue ep, const int *__restrict__ done) {
     using G = typename Num<T>::G;
-    using SM = UnitSmem<T, W2, 1>;
-    constexpr int E = SM::E, E3 = SM::E3, PWP = SM::PWP;
-    static_assert((PWP * sizeof(R)) % 16 == 0, "records are whole 16-byte words");
-    constexpr int RW = PWP * (int)sizeof(R) / 16;  // 16-byte words per record
+    constexpr int E = kTile + W2 - 1, E3 = E * E * E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + SM::tile);
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + align16(sizeof(T) * E3));
     int *s_ctl = reinterpret_cast<int *>(s_items + kUnitItems);
+    float4 *s_coef = reinterpret_cast<float4 *>(s_ctl + 4);
+    __shared__ double sh_red[33];
     if (done && *done) return;
+    if constexpr (!std::is_same<T, float>::value) win_stage(a.wstage, s_coef);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int msk = n - 1;
+    const int msk = a.n - 1, m = a.m;
+    const double alpha = ep.alpha_dev ? *ep.alpha_dev : ep.alpha;
+    double part = 0.0;
     while (true) {
         __syncthreads();  // previous unit done with the tile
-        if (threadIdx.x == 0) s_ctl[0] = atomicAdd(unit_ctr, 1);
+        if (threadIdx.x == 0) s_ctl[0] = atomicAdd(&a.unit_ctr[1], 1);
         __syncthreads();
         const int uidx = s_ctl[0];
-        if (uidx >= *n_units_dev) break;
-        const int4 un = units[uidx];
+        if (uidx >= *a.n_units) break;
+        const int4 un = a.units[uidx];
         const int l = un.x, it0 = un.z, nit = un.w;
+        if (!idx_ok(nit >= 1 && nit <= kUnitItems && l >= 0 && l < a.L, 11, nit, l)) break;
         int tx0, ty0, tz0;
-        tile_origin(un.y, n, tx0, ty0, tz0);
-        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-        const G *g = grid + (int64_t)l * n * n * n;
+        tile_origin(un.y, a.n, tx0, ty0, tz0);
+        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = a.items[it0 + e];
+        const G *g = grid + (int64_t)l * a.n * a.n * a.n;
         {
             constexpr int UNR = 8;
             for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
@@ -758,7 +615,7 @@ k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
                         const int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
                         const int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
                                   gz = (tz0 - m + 1 + ez) & msk;
-                        vals[u] = __ldg(&g[((int64_t)gz * n + gy) * n + gx]);
+                        vals[u] = __ldg(&g[((int64_t)gz * a.n + gy) * a.n + gx]);
                     }
                 }
 #pragma unroll
@@ -774,400 +631,68 @@ k_interp_pl(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
         for (int p = warp * 32 + lane; p - lane < total; p += nwarp * 32) {
             if (p >= total) continue;
             const int sp = first + p;
-            int lo = 0, hi = nit - 1;  // the last item starting at or before sp
+                        int lo = 0, hi = nit - 1;  // the last item starting at or before sp
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_items[mid].z <= sp) lo = mid; else hi = mid - 1;
             }
             int lx0, ly0, lz0;
             item_local(s_items[lo].x, lx0, ly0, lz0);
-            R rec[PWP];
-            {
-                const uint4 *src = reinterpret_cast<const uint4 *>(wts + (int64_t)sp * PWP);
-#pragma unroll
-                for (int k = 0; k < RW; ++k) reinterpret_cast<uint4 *>(rec)[k] = __ldg(src + k);
-            }
+            if (!idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N && lo >= 0 && lo < nit, 12, sp, lo)) continue;
+            T wxa[W2], wy[W2], wz[W2];
+            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 0), wxa);
+            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 1), wy);
+            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 2), wz);
             Line<T, W2> wx, t, h;
-            wx.load(rec_line<T, W2>(rec, 0));
-            T wy[W2], wz[W2];
-#pragma unroll
-            for (int j = 0; j < W2; ++j) {
-                wy[j] = rec_val<T, W2>(rec, 1, j);
-                wz[j] = rec_val<T, W2>(rec, 2, j);
-            }
+            wx.from(wxa);
             T acc = T(0);
             // the z loop stays rolled (the unrolled y loop is the work; a
-            // fully unrolled stencil made the compile many minutes long)
+            // fully unrolled stencil makes the compile very long)
 #pragma unroll 1
             for (int z = 0; z < W2; ++z) {
                 t.zero();
-                const T *srow = S + ((lz0 + z) * E + ly0) * E + lx0;
+                const int so = ((lz0 + z) * E + ly0) * E + lx0;
+                if (!idx_ok(so >= 0 && so + (W2 - 1) * E + W2 - 1 < E3, 13, so, E3)) break;
+                const T *srow = S + so;
 #pragma unroll
                 for (int y = 0; y < W2; ++y) {
                     h.load_cells(srow + y * E);
                     t.axpy(wy[y], h);
                 }
-                acc = fma(wz[z], wx.dot(t), acc);
-            }
-            Y[(int64_t)l * N + perm[sp]] = (double)acc;
-        }
-    }
-}
-
-template <typename T, int W2, int NTH, int MINB = 1>
-static void launch_interp_pl_n(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
-                               const int *done, cudaStream_t s) {
-    constexpr size_t smem = UnitSmem<T, W2, 1>::tile + sizeof(int4) * kUnitItems + 16;
-    if (P.units_cap == 0) return;
-    static int blocks = 0;
-    if (blocks == 0) {
-        NLH_CUDA(cudaFuncSetAttribute(k_interp_pl<T, W2, NTH, MINB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, sms = 0, b = 0;
-        NLH_CUDA(cudaGetDevice(&dev));
-        NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_pl<T, W2, NTH, MINB>, NTH,
-                                                               smem));
-        blocks = sms * std::max(1, b);
-    }
-    ProfRange pr(interp_class_pl<T>(), s);
-    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
-    if (nu == 0) return;
-    const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
-    k_interp_pl<T, W2, NTH, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
-                                                 P.perm, wts, grid, P.Y, P.n, P.m, P.N, done);
-    NLH_CHECK_LAUNCH();
-}
-
-// 256 threads per CTA measured best for the double-float kernel at 512^2
-// (0.286 ms against 0.340 ms with 128 and 0.353 ms with 512, uncapped).
-template <typename T, int W2>
-static void launch_interp_pl(Plan &P, const typename Num<T>::R *wts, typename Num<T>::G *grid,
-                             const int *done, cudaStream_t s) {
-    // Registers capped by launch bounds (no spills in any instance):
-    //  double-float, 2m = 8: 3 CTAs per SM instead of 2 (whole matvecs at
-    //    512^2 0.722 -> 0.627 ms);
-    //  FP32 and double-float, 2m = 12: 2 CTAs per SM instead of 1 (whole
-    //    matvecs at 2048^2, 5x5 patches: 20.75 -> 17.97 ms and 81.4 -> 75.0 ms).
-    constexpr bool f64 = std::is_same<T, double>::value;
-    constexpr int MINB = (std::is_same<T, df32>::value && W2 == 8) ? 3 : (W2 == 12 && !f64) ? 2 : 1;
-    launch_interp_pl_n<T, W2, kPlThreads, MINB>(P, wts, grid, done, s);
-}
-
-// ------------------------------------------------------------------ tensor-core FP32 path
-// For 2m = 8 the FP32 stencil work of one item (one grid cell, P points) is a
-// dense contraction over a 64 x 8 block of the grid (rows (z, y), columns x):
-//   spread:  G[(z,y), x] += sum_p (v_p wz_p[z] wy_p[y]) wx_p[x]   (A: 64 x P, B: P x 8)
-//   interp:  C[(z,y), p]  = sum_x G[(z,y), x] wx_p[x],  y_p = sum wz wy C   (A: 64 x 8)
-// These kernels run it on the tensor cores with mma.sync m16n8k8 TF32 and
-// the 3xTF32 split (a = a_hi + a_lo, products hi*hi + hi*lo + lo*hi), which
-// keeps FP32 accuracy (~2^-22 relative per product, FP32 accumulation).
-// Rows are ordered so that m16 tile i holds z = 2i (rows 0-7) and z = 2i+1
-// (rows 8-15) with y = row % 8; a thread (group g = lane / 4) then owns
-// y = g and every z of its columns.
-__device__ __forceinline__ uint32_t tf32_hi(float a) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
-    return r;
-}
-// a = hi + lo: hi keeps the top 10 mantissa bits (exact in TF32; a - hi is
-// then exact in FP32), lo is that remainder rounded to TF32.
-__device__ __forceinline__ void tf32_split(float a, uint32_t &hi, uint32_t &lo) {
-    hi = __float_as_uint(a) & 0xFFFFE000u;
-    lo = tf32_hi(a - __uint_as_float(hi));
-}
-// D += A B (m16n8k8, tf32 inputs, f32 accumulators)
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-// 3xTF32: D += Ahi Bhi + Ahi Blo + Alo Bhi
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4],
-                                           const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
-                                           uint32_t bl0, uint32_t bl1) {
-    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-}
-
-template <int TPB, int MINB>
-__global__ void __launch_bounds__(32 * TPB, MINB)
-k_spread_tc(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
-            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
-            const float *__restrict__ wts, const float *__restrict__ xs, float *__restrict__ grid,
-            int n, int m, const int *__restrict__ done, int *__restrict__ err) {
-    constexpr int W2 = 8, NW = 1;
-    using SM = UnitSmem<float, W2, TPB>;
-    using LY = UnitLayout<float, W2, TPB>;
-    constexpr int PWP = SM::PWP, E = SM::E, E3 = SM::E3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *S = reinterpret_cast<float *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
-    if (done && *done) return;
-    const int team = threadIdx.x / 32, lane = threadIdx.x % 32, tid = lane;
-    const int g = lane >> 2, t = lane & 3;
-    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
-    auto st = make_stager<float, W2, NW, TPB>(team_base, team, tid);
-    int *s_slot = const_cast<int *>(st.flag) + 1;
-    if (tid == 0) {
-        mbar_init(&st.bar[0], 1);
-        mbar_init(&st.bar[1], 1);
-        mbar_fence_init();
-    }
-    if (threadIdx.x == 0) s_ctl[2] = 0;
-    const int msk = n - 1;
-    while (true) {
-        __syncthreads();  // previous unit fully flushed
-        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
-        __syncthreads();
-        const int uidx = s_ctl[1];
-        if (uidx >= *n_units_dev || s_ctl[2]) break;
-        const int4 un = units[uidx];
-        const int l = un.x, it0 = un.z, nit = un.w;
-        int tx0, ty0, tz0;
-        tile_origin(un.y, n, tx0, ty0, tz0);
-        for (int e = threadIdx.x; e < E3; e += blockDim.x) S[e] = 0.f;
-        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-        if (threadIdx.x == 0) s_ctl[0] = TPB;
-        __syncthreads();
-        float acc[4][4];
+                // wz[z] by a select over the unrolled array (no local memory)
+                T wzz = wz[0];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][e] = 0.f;
-        ChunkCursor cur = make_cursor(s_items, team, nit);
-        float vcur = 0.f;
-        if (cur.valid()) {
-            st.issue(0, wts, cur);
-            if (lane < cur.cnt) vcur = xs[cur.start + lane];
-        }
-        int bsel = 0;
-        while (cur.valid()) {
-            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
-            float vnxt = 0.f;
-            if (nxt.valid()) {
-                st.issue(bsel ^ 1, wts, nxt);
-                if (lane < nxt.cnt - nxt.c0) vnxt = xs[nxt.start + nxt.c0 + lane];
+                for (int k = 1; k < W2; ++k)
+                    if (z == k) wzz = wz[k];
+                acc = fma(wzz, wx.dot(t), acc);
             }
-            if (!st.wait(bsel, err)) {
-                st.drain(err);
-                s_ctl[2] = 1;
-                break;
-            }
-            const float *sw = st.buf(bsel);
-            const int cn = min(kChunk, cur.cnt - cur.c0);
-            for (int g0 = 0; g0 < cn; g0 += 8) {
-                // columns t and t + 4 of this 8-point group
-                const int p0 = g0 + t, p1 = g0 + t + 4;
-                const float v0 = __shfl_sync(0xffffffffu, vcur, p0);
-                const float v1 = __shfl_sync(0xffffffffu, vcur, p1 & 31);
-                const bool ok0 = p0 < cn, ok1 = p1 < cn;
-                const float *w0 = sw + p0 * PWP, *w1 = sw + (ok1 ? p1 : p0) * PWP;
-                const float s0 = ok0 ? v0 * w0[W2 + g] : 0.f;
-                const float s1 = ok1 ? v1 * w1[W2 + g] : 0.f;
-                // columns of points past the chunk are zero (the staging buffer
-                // beyond cn holds stale records)
-                const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 z0a = ok0 ? *reinterpret_cast<const float4 *>(w0 + 2 * W2) : zero4;
-                const float4 z0b = ok0 ? *reinterpret_cast<const float4 *>(w0 + 2 * W2 + 4) : zero4;
-                const float4 z1a = ok1 ? *reinterpret_cast<const float4 *>(w1 + 2 * W2) : zero4;
-                const float4 z1b = ok1 ? *reinterpret_cast<const float4 *>(w1 + 2 * W2 + 4) : zero4;
-                const float wz0[8] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
-                const float wz1[8] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
-                // B: k = point (t, t + 4), n = x = g
-                uint32_t bh0, bl0, bh1, bl1;
-                tf32_split(ok0 ? w0[g] : 0.f, bh0, bl0);
-                tf32_split(ok1 ? w1[g] : 0.f, bh1, bl1);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    uint32_t ah[4], al[4];
-                    tf32_split(s0 * wz0[2 * i], ah[0], al[0]);
-                    tf32_split(s0 * wz0[2 * i + 1], ah[1], al[1]);
-                    tf32_split(s1 * wz1[2 * i], ah[2], al[2]);
-                    tf32_split(s1 * wz1[2 * i + 1], ah[3], al[3]);
-                    mma_3xtf32(acc[i], ah, al, bh0, bh1, bl0, bl1);
+            // epilogue: one window alone finishes the pixel here; with several
+            // windows the value is added into the pixel's sum, which
+            // k_finish turns into the output after every window is in
+            const int i = __ldg(a.perm + sp);
+            if (!idx_ok(i >= 0 && i < a.N, 14, i, sp)) continue;
+            const double val = (double)acc;
+            if (ep.L > 1) {
+                atomicAdd(&ep.yacc[i], val);
+            } else {
+                const double s = val * ep.inv_l;
+                double out = s;
+                const double xi = (ep.op != 0 || ep.partials) ? __ldg(ep.x + i) : 0.0;
+                if (ep.op != 0) {
+                    out = __ldg(ep.d + i) * xi - s;
+                    if (ep.op == 2) out = fma(alpha, xi, out);
                 }
-            }
-            if (cur.c0 + kChunk >= cur.cnt) {  // last chunk of the item: add into the tile
-                int lx0, ly0, lz0;
-                item_local(cur.local, lx0, ly0, lz0);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float *row = S + ((lz0 + 2 * i + h) * E + (ly0 + g)) * E + lx0 + 2 * t;
-                        atomicAdd(&row[0], acc[i][2 * h]);
-                        atomicAdd(&row[1], acc[i][2 * h + 1]);
-                        acc[i][2 * h] = acc[i][2 * h + 1] = 0.f;
-                    }
-                }
-            }
-            __syncwarp();  // every read of buffer bsel is done before it is refilled
-            cur = nxt;
-            vcur = vnxt;
-            bsel ^= 1;
-        }
-        __syncthreads();
-        float *gl = grid + (int64_t)l * n * n * n;
-        for (int e = threadIdx.x; e < E3; e += blockDim.x) {
-            const float val = S[e];
-            if (val != 0.f) {
-                int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
-                int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
-                    gz = (tz0 - m + 1 + ez) & msk;
-                atomicAdd(&gl[((int64_t)gz * n + gy) * n + gx], val);
+                ep.y[i] = out;
+                part = fma(xi, out, part);
             }
         }
     }
-}
-
-template <int TPB, int MINB>
-__global__ void __launch_bounds__(32 * TPB, MINB)
-k_interp_tc(const int4 *__restrict__ units, const int *__restrict__ n_units_dev,
-            int *__restrict__ unit_ctr, const int4 *__restrict__ items,
-            const int *__restrict__ perm, const float *__restrict__ wts,
-            const float *__restrict__ grid, double *__restrict__ Y, int n, int m, int64_t N,
-            const int *__restrict__ done, int *__restrict__ err) {
-    constexpr int W2 = 8, NW = 1;
-    using SM = UnitSmem<float, W2, TPB>;
-    using LY = UnitLayout<float, W2, TPB>;
-    constexpr int PWP = SM::PWP, E = SM::E, E3 = SM::E3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *S = reinterpret_cast<float *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + LY::items_off);
-    int *s_ctl = reinterpret_cast<int *>(smem_raw + LY::next_off);
-    if (done && *done) return;
-    const int team = threadIdx.x / 32, lane = threadIdx.x % 32, tid = lane;
-    const int g = lane >> 2, t = lane & 3;
-    unsigned char *team_base = smem_raw + LY::teams_off + team * SM::team;
-    auto st = make_stager<float, W2, NW, TPB>(team_base, team, tid);
-    int *s_slot = const_cast<int *>(st.flag) + 1;
-    if (tid == 0) {
-        mbar_init(&st.bar[0], 1);
-        mbar_init(&st.bar[1], 1);
-        mbar_fence_init();
+    if (ep.partials && ep.L == 1) {
+        const double bs = block_sum(part, sh_red);
+        if (threadIdx.x == 0 && idx_ok(blockIdx.x < ep.nparts, 15, blockIdx.x, ep.nparts)) ep.partials[blockIdx.x] = bs;
+        if (blockIdx.x == 0)
+            for (int j = gridDim.x + threadIdx.x; j < ep.nparts; j += blockDim.x) ep.partials[j] = 0.0;
     }
-    if (threadIdx.x == 0) s_ctl[2] = 0;
-    const int msk = n - 1;
-    while (true) {
-        __syncthreads();  // previous unit done with the tile
-        if (threadIdx.x == 0) s_ctl[1] = atomicAdd(unit_ctr, 1);
-        __syncthreads();
-        const int uidx = s_ctl[1];
-        if (uidx >= *n_units_dev || s_ctl[2]) break;
-        const int4 un = units[uidx];
-        const int l = un.x, it0 = un.z, nit = un.w;
-        int tx0, ty0, tz0;
-        tile_origin(un.y, n, tx0, ty0, tz0);
-        for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = items[it0 + e];
-        if (threadIdx.x == 0) s_ctl[0] = TPB;
-        const float *gl = grid + (int64_t)l * n * n * n;
-        for (int e = threadIdx.x; e < E3; e += blockDim.x) {
-            int ex = e % E, ey = (e / E) % E, ez = e / (E * E);
-            int gx = (tx0 - m + 1 + ex) & msk, gy = (ty0 - m + 1 + ey) & msk,
-                gz = (tz0 - m + 1 + ez) & msk;
-            S[e] = __ldg(&gl[((int64_t)gz * n + gy) * n + gx]);
-        }
-        __syncthreads();
-        ChunkCursor cur = make_cursor(s_items, team, nit);
-        if (cur.valid()) st.issue(0, wts, cur);
-        int pcur = (cur.valid() && lane < cur.cnt) ? perm[cur.start + lane] : 0;
-        uint32_t ah[4][4], al[4][4];  // the item's stencil, A = G[(z, y), x]
-        int bsel = 0;
-        while (cur.valid()) {
-            if (cur.c0 == 0) {
-                int lx0, ly0, lz0;
-                item_local(cur.local, lx0, ly0, lz0);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float *r0 = S + ((lz0 + 2 * i) * E + (ly0 + g)) * E + lx0;
-                    const float *r1 = S + ((lz0 + 2 * i + 1) * E + (ly0 + g)) * E + lx0;
-                    tf32_split(r0[t], ah[i][0], al[i][0]);
-                    tf32_split(r1[t], ah[i][1], al[i][1]);
-                    tf32_split(r0[t + 4], ah[i][2], al[i][2]);
-                    tf32_split(r1[t + 4], ah[i][3], al[i][3]);
-                }
-            }
-            const ChunkCursor nxt = next_chunk<NW>(cur, s_items, nit, s_ctl, s_slot, team, tid);
-            int pnxt = 0;
-            if (nxt.valid()) {
-                st.issue(bsel ^ 1, wts, nxt);
-                if (lane < nxt.cnt - nxt.c0) pnxt = perm[nxt.start + nxt.c0 + lane];
-            }
-            if (!st.wait(bsel, err)) {
-                st.drain(err);
-                s_ctl[2] = 1;
-                break;
-            }
-            const float *sw = st.buf(bsel);
-            const int cn = min(kChunk, cur.cnt - cur.c0);
-            for (int g0 = 0; g0 < cn; g0 += 8) {
-                // B: k = x (t, t + 4), n = point g0 + g
-                const int pb = g0 + g;
-                const float *wb = sw + (pb < cn ? pb : g0) * PWP;
-                uint32_t bh0, bl0, bh1, bl1;
-                tf32_split(pb < cn ? wb[t] : 0.f, bh0, bl0);
-                tf32_split(pb < cn ? wb[t + 4] : 0.f, bh1, bl1);
-                float c[4][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    c[i][0] = c[i][1] = c[i][2] = c[i][3] = 0.f;
-                    mma_3xtf32(c[i], ah[i], al[i], bh0, bh1, bl0, bl1);
-                }
-                // this thread: y = g, z = 0..7, points q0 = g0 + 2t, q1 = q0 + 1
-                const int q0 = g0 + 2 * t, q1 = q0 + 1;
-                const float *w0 = sw + (q0 < cn ? q0 : g0) * PWP;
-                const float *w1 = sw + (q1 < cn ? q1 : g0) * PWP;
-                const float4 z0a = *reinterpret_cast<const float4 *>(w0 + 2 * W2);
-                const float4 z0b = *reinterpret_cast<const float4 *>(w0 + 2 * W2 + 4);
-                const float4 z1a = *reinterpret_cast<const float4 *>(w1 + 2 * W2);
-                const float4 z1b = *reinterpret_cast<const float4 *>(w1 + 2 * W2 + 4);
-                const float wz0[8] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
-                const float wz1[8] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    s0 = fmaf(wz0[2 * i], c[i][0], s0);
-                    s0 = fmaf(wz0[2 * i + 1], c[i][2], s0);
-                    s1 = fmaf(wz1[2 * i], c[i][1], s1);
-                    s1 = fmaf(wz1[2 * i + 1], c[i][3], s1);
-                }
-                s0 *= w0[W2 + g];
-                s1 *= w1[W2 + g];
-                // sum over y = g: lanes 4 g + t with the same t
-#pragma unroll
-                for (int o = 4; o <= 16; o <<= 1) {
-                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                }
-                const int pi0 = __shfl_sync(0xffffffffu, pcur, q0 & 31);
-                const int pi1 = __shfl_sync(0xffffffffu, pcur, q1 & 31);
-                if (g == 0) {
-                    if (q0 < cn) Y[(int64_t)l * N + pi0] = (double)s0;
-                    if (q1 < cn) Y[(int64_t)l * N + pi1] = (double)s1;
-                }
-            }
-            __syncwarp();  // every read of buffer bsel is done before it is refilled
-            cur = nxt;
-            pcur = pnxt;
-            bsel ^= 1;
-        }
-    }
-}
-
-// xs[s] = x[perm[s]] for every sorted position s (input in sorted order).
-template <typename T>
-__global__ void k_gather(const double *__restrict__ x, const int *__restrict__ perm, int64_t LN,
-                         T *__restrict__ xs, const int *__restrict__ done) {
-    if (done && *done) return;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < LN;
-         s += (int64_t)gridDim.x * blockDim.x)
-        xs[s] = (T)x[perm[s]];
 }
 
 // ------------------------------------------------------------------ grid convolution
@@ -1178,18 +703,25 @@ __global__ void k_gather(const double *__restrict__ x, const int *__restrict__ p
 // bit-reversed order), multiplies by the bit-reversed multiplier table, and
 // runs the decimation-in-time inverse FFT (bit-reversed in, natural out).
 // Because the multiplier is real and even, the real and imaginary parts stay
-// the two independent convolved lines.
+// the two independent convolved lines.  The first axis pass reads the spread
+// grid `src`, clears it for the next matvec and writes `dst`; the later
+// passes work in place on `dst`.
 template <typename T, int R>
 __global__ void __launch_bounds__(256)
-k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ tab,
-       const typename Vec2<T>::type *__restrict__ tw, const int *__restrict__ done) {
+k_conv(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ dst, int axis,
+       const T *__restrict__ tab, const typename Vec2<T>::type *__restrict__ tw,
+       int *__restrict__ ctr_reset, const int *__restrict__ done) {
     using G = typename Num<T>::G;
     using C = typename Vec2<T>::type;
     constexpr int n = 32 * R, LPC = 16, PITCH = n + 1;
     __shared__ T S[LPC * PITCH];
     if (done && *done) return;
+    // the spreading of this matvec has finished (stream order)
+    if (ctr_reset && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ctr_reset = 0;
+    const bool clear = src != dst;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    G *g = grid + (int64_t)blockIdx.y * n * n * n;
+    G *gs = src + (int64_t)blockIdx.y * n * n * n;
+    G *gd = dst + (int64_t)blockIdx.y * n * n * n;
     const int li0 = blockIdx.x * LPC;  // first line of the CTA
     const int a0 = li0 % n, b0 = li0 / n;
     // element (line j, position e) -> global offset
@@ -1201,20 +733,24 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
     if (axis == 0) {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q / n, e = q % n;
-            S[j * PITCH + e] = T(g[goff(j, e)]);
+            const int64_t o = goff(j, e);
+            S[j * PITCH + e] = T(gs[o]);
+            if (clear) gs[o] = G(0);
         }
     } else {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q % LPC, e = q / LPC;
-            S[j * PITCH + e] = T(g[goff(j, e)]);
+            const int64_t o = goff(j, e);
+            S[j * PITCH + e] = T(gs[o]);
+            if (clear) gs[o] = G(0);
         }
     }
     __syncthreads();
 
-    C x[R];
+    C xv[R];
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        x[r] = {S[(2 * warp) * PITCH + 32 * r + lane], S[(2 * warp + 1) * PITCH + 32 * r + lane]};
+        xv[r] = {S[(2 * warp) * PITCH + 32 * r + lane], S[(2 * warp + 1) * PITCH + 32 * r + lane]};
     // forward DIF
 #pragma unroll
     for (int h = n / 2; h >= 32; h >>= 1) {
@@ -1222,10 +758,10 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if ((r & H) == 0) {
-                C a = x[r], b = x[r + H];
-                x[r] = cadd(a, b);
+                C p = xv[r], q = xv[r + H];
+                xv[r] = cadd(p, q);
                 int j = ((r % H) * 32 + lane) * (n / (2 * h));
-                x[r + H] = cmul(csub(a, b), tw[j]);
+                xv[r + H] = cmul(csub(p, q), tw[j]);
             }
         }
     }
@@ -1235,16 +771,16 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
         const bool upper = lane & h;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            C o = cshfl(x[r], h);
-            x[r] = upper ? cmul(csub(o, x[r]), w) : cadd(x[r], o);
+            C o = cshfl(xv[r], h);
+            xv[r] = upper ? cmul(csub(o, xv[r]), w) : cadd(xv[r], o);
         }
     }
     // multiply (table is in bit-reversed order, like the data)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         T f = tab[32 * r + lane];
-        x[r].x *= f;
-        x[r].y *= f;
+        xv[r].x *= f;
+        xv[r].y *= f;
     }
     // inverse DIT
 #pragma unroll
@@ -1253,9 +789,9 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
         const bool upper = lane & h;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            C mine = upper ? cmulc(x[r], w) : x[r];
+            C mine = upper ? cmulc(xv[r], w) : xv[r];
             C o = cshfl(mine, h);
-            x[r] = upper ? csub(o, mine) : cadd(mine, o);
+            xv[r] = upper ? csub(o, mine) : cadd(mine, o);
         }
     }
 #pragma unroll
@@ -1265,280 +801,430 @@ k_conv(typename Num<T>::G *__restrict__ grid, int axis, const T *__restrict__ ta
         for (int r = 0; r < R; ++r) {
             if ((r & H) == 0) {
                 int j = ((r % H) * 32 + lane) * (n / (2 * h));
-                C b = cmulc(x[r + H], tw[j]);
-                C a = x[r];
-                x[r] = cadd(a, b);
-                x[r + H] = csub(a, b);
+                C q = cmulc(xv[r + H], tw[j]);
+                C p = xv[r];
+                xv[r] = cadd(p, q);
+                xv[r + H] = csub(p, q);
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        S[(2 * warp) * PITCH + 32 * r + lane] = x[r].x;
-        S[(2 * warp + 1) * PITCH + 32 * r + lane] = x[r].y;
+        S[(2 * warp) * PITCH + 32 * r + lane] = xv[r].x;
+        S[(2 * warp + 1) * PITCH + 32 * r + lane] = xv[r].y;
     }
     __syncthreads();
     if (axis == 0) {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q / n, e = q % n;
-            g[goff(j, e)] = (G)S[j * PITCH + e];
+            gd[goff(j, e)] = (G)S[j * PITCH + e];
         }
     } else {
         for (int q = tid; q < LPC * n; q += 256) {
             int j = q % LPC, e = q / LPC;
-            g[goff(j, e)] = (G)S[j * PITCH + e];
+            gd[goff(j, e)] = (G)S[j * PITCH + e];
         }
-    }
-}
-
-// ------------------------------------------------------------------ epilogue
-// y = (1/L) sum_l Y_l; op 1: d o x - y; op 2: alpha x + d o x - y.
-// Also clears the grids for the next matvec and writes per-block partial
-// sums of x^T y (if partials != NULL).
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-k_epilogue(const double *__restrict__ Y, int L, int64_t N, const double *__restrict__ x,
-           const double *__restrict__ d, double alpha_val, const double *__restrict__ alpha_dev,
-           int op, double *__restrict__ y,
-           double *__restrict__ partials, T *__restrict__ grid, int64_t grid_elems,
-           int *__restrict__ unit_ctr, const int *__restrict__ done) {
-    __shared__ double sh[33];
-    if (done && *done) return;
-    const double alpha = alpha_dev ? *alpha_dev : alpha_val;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        unit_ctr[0] = 0;  // the spread and interpolation kernels have finished
-        unit_ctr[1] = 0;
-    }
-    const double invL = 1.0 / L;
-    double acc = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
-        double s = 0.0;
-        for (int l = 0; l < L; ++l) s += Y[(int64_t)l * N + i];
-        s *= invL;
-        double out;
-        if (op == 0) {
-            out = s;
-        } else {
-            double xi = x[i];
-            out = d[i] * xi - s;
-            if (op == 2) out = fma(alpha, xi, out);
-        }
-        y[i] = out;
-        if (partials) acc = fma(x[i], out, acc);
-    }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < grid_elems; i += stride)
-        grid[i] = T(0);
-    if (partials) {
-        double bs = block_sum(acc, sh);
-        if (threadIdx.x == 0) partials[blockIdx.x] = bs;
     }
 }
 
 // ------------------------------------------------------------------ dispatch
-template <typename T> constexpr int spread_class() {
-    return sizeof(T) == 4 ? NLH_K_SPREAD32 : (Num<T>::kParts == 2 ? NLH_K_SPREADDF : NLH_K_SPREAD64);
+template <typename T> constexpr int arith_index() {
+    return std::is_same<T, df32>::value ? NLH_DF32 : (sizeof(T) == 8 ? NLH_FP64 : NLH_FP32);
 }
 
+template <typename T> typename PolyArg<T>::type win_poly(const Plan &) { return {}; }
+template <> WinPoly<float> win_poly<float>(const Plan &P) { return P.wp32; }
 
-template <typename T, int W2, int NW, int TPB>
-static void launch_spread_interp_shape(Plan &P, bool spread, const typename Num<T>::R *wts,
-                                 typename Num<T>::G *grid, const T *xs, const int *done,
-                                 cudaStream_t s) {
-    constexpr int NTH = 32 * NW * TPB;
-    // the FP32 2m = 8 default shape with registers capped for 5 CTAs per SM
-    // (no spills; 1% faster matvecs than the uncapped 4 CTAs)
-    constexpr int MINB =
-        (std::is_same<T, float>::value && W2 == 8 && NW == 1 && TPB == 4) ? 5 : 1;
-    constexpr size_t smem = UnitLayout<T, W2, TPB>::bytes;
-    if (P.units_cap == 0) return;
-    static int blocks_spread = 0, blocks_interp = 0;  // per template instance
-    if (blocks_spread == 0) {
-        NLH_CUDA(cudaFuncSetAttribute(k_spread<T, W2, NW, TPB, MINB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NLH_CUDA(cudaFuncSetAttribute(k_interp<T, W2, NW, TPB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, sms = 0, a = 0, b = 0;
+template <typename T>
+static NfftArgs nfft_args(const Plan &P) {
+    NfftArgs a;
+    a.units = P.units;
+    a.n_units = P.d_units;
+    a.unit_ctr = P.unit_ctr;
+    a.items = P.items;
+    a.perm = P.perm;
+    a.yhi = P.yhi;
+    a.ylo = P.ylo;
+    a.n = P.n;
+    a.m = P.m;
+    a.L = P.L;
+    a.N = P.N;
+    a.wstage = std::is_same<T, double>::value ? P.wstage
+               : std::is_same<T, df32>::value ? P.wstage + kWinStageBytes / 16
+                                              : nullptr;
+    return a;
+}
+
+// Persistent grid of a kernel instance: SMs x resident CTAs per SM, set up
+// once per instance (this also resolves the kernel on the device; the first
+// plan creation does it for every instance before it queues any work).
+static int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
         NLH_CUDA(cudaGetDevice(&dev));
         NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spread<T, W2, NW, TPB, MINB>,
-                                                               NTH, smem));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<T, W2, NW, TPB>, NTH,
-                                                               smem));
-        blocks_interp = sms * std::max(1, b);
-        blocks_spread = sms * std::max(1, a);
     }
-    ProfRange pr(spread ? spread_class<T>() : interp_class<T>(), s);
+    return sms;
+}
+
+// the FP32 2m = 8 default shape with registers capped for 5 CTAs per SM (no
+// spills; 1% faster matvecs than the uncapped 4 CTAs)
+template <typename T, int W2, int NW, int TPB>
+constexpr int spread_minb() {
+    return (std::is_same<T, float>::value && W2 == 8 && NW == 1 && TPB == 4) ? 5 : 1;
+}
+
+template <typename T, int W2, int NW, int TPB>
+static int spread_blocks() {
+    static int blocks = 0;  // per template instance
+    if (blocks == 0) {
+        constexpr int NTH = 32 * NW * TPB;
+        constexpr size_t smem = SpreadSmem<T, W2, NW, TPB>::bytes;
+        auto kern = k_spread<T, W2, NW, TPB, spread_minb<T, W2, NW, TPB>()>;
+        NLH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem));
+        blocks = sm_count() * std::max(1, b);
+    }
+    return blocks;
+}
+
+template <typename T, int W2, int NW, int TPB>
+static void launch_spread_shape(Plan &P, const double *x, typename Num<T>::G *grid,
+                                const int *done, cudaStream_t s) {
+    constexpr int NTH = 32 * NW * TPB;
+    constexpr int MINB = spread_minb<T, W2, NW, TPB>();
+    constexpr size_t smem = SpreadSmem<T, W2, NW, TPB>::bytes;
+    auto kern = k_spread<T, W2, NW, TPB, MINB>;
+    const int blocks = spread_blocks<T, W2, NW, TPB>();
+    ProfRange pr(spread_class<T>(), s);
     // grid bound: the unit count once known on the host, else its upper bound
     const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
     if (nu == 0) return;
-    if (spread) {
-        const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
-        k_spread<T, W2, NW, TPB, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr, P.items,
-                                                            wts, xs, grid, P.n, P.m, done, P.err);
-    } else {
-        const unsigned g = (unsigned)std::min<int64_t>(blocks_interp, nu);
-        k_interp<T, W2, NW, TPB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
-                                                      P.perm, wts, grid, P.Y, P.n, P.m, P.N, done,
-                                                      P.err);
-    }
+    const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
+    kern<<<g, NTH, smem, s>>>(nfft_args<T>(P), win_poly<T>(P), x, grid, done);
     NLH_CHECK_LAUNCH();
 }
 
-// The tensor-core FP32 kernels (2m = 8, one-warp teams, 4 teams per CTA,
-// registers capped for MINB resident CTAs per SM).
-template <int MINB>
-static void launch_spread_interp_tc(Plan &P, bool spread, const float *wts, float *grid,
-                                    const float *xs, const int *done, cudaStream_t s) {
-    constexpr int TPB = 4, NTH = 32 * TPB;
-    constexpr size_t smem = UnitLayout<float, 8, TPB>::bytes;
-    if (P.units_cap == 0) return;
-    static int blocks_spread = 0, blocks_interp = 0;
-    if (blocks_spread == 0) {
-        NLH_CUDA(cudaFuncSetAttribute(k_spread_tc<TPB, MINB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NLH_CUDA(cudaFuncSetAttribute(k_interp_tc<TPB, MINB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, sms = 0, a = 0, b = 0;
-        NLH_CUDA(cudaGetDevice(&dev));
-        NLH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spread_tc<TPB, MINB>, NTH,
-                                                               smem));
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp_tc<TPB, MINB>, NTH,
-                                                               smem));
-        blocks_interp = sms * std::max(1, b);
-        blocks_spread = sms * std::max(1, a);
-    }
-    ProfRange pr(spread ? NLH_K_SPREAD32 : NLH_K_INTERP32, s);
-    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
-    if (nu == 0) return;
-    if (spread) {
-        const unsigned g = (unsigned)std::min<int64_t>(blocks_spread, nu);
-        k_spread_tc<TPB, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr, P.items, wts,
-                                                    xs, grid, P.n, P.m, done, P.err);
-    } else {
-        const unsigned g = (unsigned)std::min<int64_t>(blocks_interp, nu);
-        k_interp_tc<TPB, MINB><<<g, NTH, smem, s>>>(P.units, P.d_units, P.unit_ctr + 1, P.items,
-                                                    P.perm, wts, grid, P.Y, P.n, P.m, P.N, done,
-                                                    P.err);
-    }
-    NLH_CHECK_LAUNCH();
-}
-
-template <typename T> constexpr int arith_index() {
-    return sizeof(T) == 8 && !std::is_same<T, df32>::value ? NLH_FP64
-           : std::is_same<T, df32>::value                   ? NLH_DF32
-                                                            : NLH_FP32;
-}
-
-// Team shape (warps per team NW, teams per CTA TPB) of the spread and
-// interpolation kernels: fewer accumulator lines per thread (larger teams)
-// against more independent teams per SM.  Shape 0 is the default; shapes 1
-// and 2 are compiled for the stencil widths of the workloads (2m = 8, 12);
-// shape 3 is the tensor-core FP32 path for 2m = 8.  The autotuner picks one
-// per arithmetic (plan.team[]); other combinations fall back to shape 0.
+// Team shape (warps per team NW, teams per CTA TPB) of the spreading kernel:
+// fewer accumulator lines per thread (larger teams) against more independent
+// teams per SM.  Shape 0 is the default; shapes 1 and 2 are compiled for the
+// stencil widths of the workloads (2m = 8, 12).  The autotuner picks one per
+// arithmetic (plan.team[]); other combinations run shape 0.
 template <typename T, int W2>
-static void launch_spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
-                                 typename Num<T>::G *grid, const T *xs, const int *done,
-                                 cudaStream_t s) {
+static void launch_spread(Plan &P, const double *x, typename Num<T>::G *grid, const int *done,
+                          cudaStream_t s) {
     const int shape = P.team[arith_index<T>()];
-    // interpolation: points on lanes unless the plan asks for the team kernel
-    // (or the tensor-core FP32 shape, which has its own).  Compiled for the
-    // stencil widths of the workloads (2m = 8, 12): its fully unrolled
-    // stencil makes every further width a long compile; other widths run
-    // the team kernel.
-    if constexpr (W2 == 8 || W2 == 12) {
-        if (!spread && P.interp_kind == NLH_INTERP_POINTS && shape != 3)
-            return launch_interp_pl<T, W2>(P, wts, grid, done, s);
-    }
-    if constexpr (W2 == 8 && std::is_same<T, float>::value) {
-        if (shape == 3) return launch_spread_interp_tc<5>(P, spread, wts, grid, xs, done, s);
-    }
     if constexpr (W2 == 8) {
-        if (shape == 1) return launch_spread_interp_shape<T, W2, 2, 2>(P, spread, wts, grid, xs, done, s);
-        if (shape == 2) return launch_spread_interp_shape<T, W2, 2, 4>(P, spread, wts, grid, xs, done, s);
+        if (shape == 1) return launch_spread_shape<T, W2, 2, 2>(P, x, grid, done, s);
+        if (shape == 2) return launch_spread_shape<T, W2, 2, 4>(P, x, grid, done, s);
     } else if constexpr (W2 == 12) {
-        if (shape == 1) return launch_spread_interp_shape<T, W2, 4, 1>(P, spread, wts, grid, xs, done, s);
-        if (shape == 2) return launch_spread_interp_shape<T, W2, 2, 1>(P, spread, wts, grid, xs, done, s);
+        if (shape == 1) return launch_spread_shape<T, W2, 4, 1>(P, x, grid, done, s);
+        if (shape == 2) return launch_spread_shape<T, W2, 2, 1>(P, x, grid, done, s);
     }
     constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2;
-    launch_spread_interp_shape<T, W2, NW, TPB>(P, spread, wts, grid, xs, done, s);
+    launch_spread_shape<T, W2, NW, TPB>(P, x, grid, done, s);
+}
+
+// Registers capped by launch bounds where that measured faster (no spills):
+// double-float at 2m = 8 for 3 CTAs per SM, FP32 and double-float at 2m = 12
+// for 2 CTAs per SM.
+template <typename T, int W2>
+constexpr int interp_minb() {
+    return (std::is_same<T, df32>::value && W2 == 8) ? 3
+           : (W2 == 12 && !std::is_same<T, double>::value) ? 2
+                                                           : 1;
+}
+template <typename T, int W2>
+constexpr size_t interp_smem() {
+    return align16(sizeof(T) * (kTile + W2 - 1) * (kTile + W2 - 1) * (kTile + W2 - 1)) +
+           sizeof(int4) * kUnitItems + 16 + kWinStageBytes;
+}
+
+template <typename T, int W2>
+static int interp_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
+        constexpr size_t smem = interp_smem<T, W2>();
+        auto kern = k_interp<T, W2, kInterpThreads, interp_minb<T, W2>()>;
+        NLH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kInterpThreads, smem));
+        blocks = std::min(sm_count() * std::max(1, b), kPqSlots);
+    }
+    return blocks;
+}
+
+template <typename T, int W2>
+static void launch_interp(Plan &P, const typename Num<T>::G *grid, const Epilogue &ep,
+                          const int *done, cudaStream_t s) {
+    constexpr int MINB = interp_minb<T, W2>();
+    constexpr size_t smem = interp_smem<T, W2>();
+    auto kern = k_interp<T, W2, kInterpThreads, MINB>;
+    const int blocks = interp_blocks<T, W2>();
+    ProfRange pr(interp_class<T>(), s);
+    const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
+    if (nu == 0) {
+        NLH_REQUIRE(false, "internal: plan without work units");
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
+    kern<<<g, kInterpThreads, smem, s>>>(nfft_args<T>(P), win_poly<T>(P), grid, ep, done);
+    NLH_CHECK_LAUNCH();
+}
+
+template <typename T, int W2>
+static void spread_interp_w(Plan &P, bool spread, const double *x, typename Num<T>::G *grid,
+                            const Epilogue *ep, const int *done, cudaStream_t s) {
+    if (spread) launch_spread<T, W2>(P, x, grid, done, s);
+    else launch_interp<T, W2>(P, grid, *ep, done, s);
 }
 
 template <typename T>
-static void spread_interp(Plan &P, bool spread, const typename Num<T>::R *wts,
-                          typename Num<T>::G *grid, const T *v, const int *done, cudaStream_t s) {
+static void spread_interp(Plan &P, bool spread, const double *x, typename Num<T>::G *grid,
+                          const Epilogue *ep, const int *done, cudaStream_t s) {
     switch (P.W2) {
-        case 4: launch_spread_interp<T, 4>(P, spread, wts, grid, v, done, s); break;
-        case 6: launch_spread_interp<T, 6>(P, spread, wts, grid, v, done, s); break;
-        case 8: launch_spread_interp<T, 8>(P, spread, wts, grid, v, done, s); break;
-        case 10: launch_spread_interp<T, 10>(P, spread, wts, grid, v, done, s); break;
-        case 12: launch_spread_interp<T, 12>(P, spread, wts, grid, v, done, s); break;
-        case 14: launch_spread_interp<T, 14>(P, spread, wts, grid, v, done, s); break;
-        case 16: launch_spread_interp<T, 16>(P, spread, wts, grid, v, done, s); break;
+        case 4: spread_interp_w<T, 4>(P, spread, x, grid, ep, done, s); break;
+        case 6: spread_interp_w<T, 6>(P, spread, x, grid, ep, done, s); break;
+        case 8: spread_interp_w<T, 8>(P, spread, x, grid, ep, done, s); break;
+        case 10: spread_interp_w<T, 10>(P, spread, x, grid, ep, done, s); break;
+        case 12: spread_interp_w<T, 12>(P, spread, x, grid, ep, done, s); break;
+        case 14: spread_interp_w<T, 14>(P, spread, x, grid, ep, done, s); break;
+        case 16: spread_interp_w<T, 16>(P, spread, x, grid, ep, done, s); break;
         default: NLH_REQUIRE(false, "internal: unsupported stencil width %d", P.W2);
     }
 }
 
+// Sets up (and thereby resolves on the device) every kernel instance of one
+// arithmetic: the spreading shapes and the interpolation of every stencil
+// width, and the convolution of every grid size.
+template <typename T, int W2>
+static void prepare_w() {
+    if constexpr (W2 == 8) {
+        spread_blocks<T, W2, 2, 2>();
+        spread_blocks<T, W2, 2, 4>();
+    } else if constexpr (W2 == 12) {
+        spread_blocks<T, W2, 4, 1>();
+        spread_blocks<T, W2, 2, 1>();
+    }
+    spread_blocks<T, W2, (W2 <= 8 ? 1 : 2), (W2 <= 8 ? 4 : 2)>();
+    interp_blocks<T, W2>();
+}
+
 template <typename T>
-static void convolve(Plan &P, typename Num<T>::G *grid, const T *tab,
+static void prepare_t() {
+    prepare_w<T, 4>();
+    prepare_w<T, 6>();
+    prepare_w<T, 8>();
+    prepare_w<T, 10>();
+    prepare_w<T, 12>();
+    prepare_w<T, 14>();
+    prepare_w<T, 16>();
+    cudaFuncAttributes fa;
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 1>));
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 2>));
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 4>));
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 8>));
+}
+
+template <typename T>
+static void convolve(Plan &P, typename Num<T>::G *src, typename Num<T>::G *dst, const T *tab,
                      const typename Vec2<T>::type *tw, const int *done, cudaStream_t s) {
     const int n = P.n;
     dim3 gdim((unsigned)(n * n / 16), (unsigned)P.L);
     ProfRange pr(sizeof(T) == 4 ? NLH_K_CONV32 : NLH_K_CONV64, s);
     for (int axis = 0; axis < 3; ++axis) {
+        using G = typename Num<T>::G;
+        G *in = axis == 0 ? src : dst;
+        int *rst = axis == 0 ? P.unit_ctr : nullptr;
         switch (n) {
-            case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 64: k_conv<T, 2><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 128: k_conv<T, 4><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
-            case 256: k_conv<T, 8><<<gdim, 256, 0, s>>>(grid, axis, tab, tw, done); break;
+            case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(in, dst, axis, tab, tw, rst, done); break;
+            case 64: k_conv<T, 2><<<gdim, 256, 0, s>>>(in, dst, axis, tab, tw, rst, done); break;
+            case 128: k_conv<T, 4><<<gdim, 256, 0, s>>>(in, dst, axis, tab, tw, rst, done); break;
+            case 256: k_conv<T, 8><<<gdim, 256, 0, s>>>(in, dst, axis, tab, tw, rst, done); break;
             default: NLH_REQUIRE(false, "internal: unsupported grid size %d", n);
         }
         NLH_CHECK_LAUNCH();
     }
 }
 
-// One matvec in arithmetic T: gather the input into sorted order, spread,
-// convolve the grids, interpolate, and the epilogue (which also clears the
-// grids and the unit counters for the next matvec).
+__global__ void k_finish(double *__restrict__ yacc, const double *__restrict__ x,
+                         const double *__restrict__ d, double *__restrict__ y, int64_t N,
+                         double inv_l, int op, double alpha_val,
+                         const double *__restrict__ alpha_dev, double *__restrict__ partials,
+                         int nparts, const int *__restrict__ done);
+
+// One matvec in arithmetic T: spread (with the gather of x), convolve the
+// grids, interpolate with the epilogue.  Between matvecs the spread grids,
+// the per-pixel sums and counts are zero and the unit counters are reset.
 template <typename T>
 static void matvec_t(Plan &P, int op, double alpha, const double *alpha_dev, const double *x,
-                     double *y, double *partials, const int *done,
-                     const typename Num<T>::R *wts, typename Num<T>::G *grid, const T *tab,
-                     const typename Vec2<T>::type *tw, const double *d, cudaStream_t s) {
-    using G = typename Num<T>::G;
-    T *xs = reinterpret_cast<T *>(P.xs);
-    {
+                     double *y, double *partials, const int *done, typename Num<T>::G *gridA,
+                     typename Num<T>::G *gridB, const T *tab, const typename Vec2<T>::type *tw,
+                     const double *d, cudaStream_t s) {
+    spread_interp<T>(P, true, x, gridA, nullptr, done, s);
+    convolve<T>(P, gridA, gridB, tab, tw, done, s);
+    Epilogue ep;
+    ep.x = x;
+    ep.d = d;
+    ep.y = y;
+    ep.yacc = P.yacc;
+    ep.partials = partials;
+    ep.nparts = kPqSlots;
+    ep.L = P.L;
+    ep.inv_l = 1.0 / P.L_norm;
+    ep.op = op;
+    ep.alpha = alpha;
+    ep.alpha_dev = alpha_dev;
+    spread_interp<T>(P, false, nullptr, gridB, &ep, done, s);
+    if (P.L > 1) {
         ProfRange pr(NLH_K_EPILOGUE, s);
-        k_gather<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, P.perm, (int64_t)P.L * P.N, xs, done);
+        k_finish<<<kRedBlocks, kRedThreads, 0, s>>>(P.yacc, x, d, y, P.N, ep.inv_l, op, alpha,
+                                                    alpha_dev, partials, kPqSlots, done);
         NLH_CHECK_LAUNCH();
     }
-    spread_interp<T>(P, true, wts, grid, xs, done, s);
-    convolve<T>(P, grid, tab, tw, done, s);
-    spread_interp<T>(P, false, wts, grid, nullptr, done, s);
-    const int64_t ge = (int64_t)P.L * P.n * P.n * P.n;
-    ProfRange pr(NLH_K_EPILOGUE, s);
-    k_epilogue<G><<<kRedBlocks, kRedThreads, 0, s>>>(P.Y, P.L, P.N, x, d, alpha, alpha_dev, op, y,
-                                                     partials, grid, ge, P.unit_ctr, done);
-    NLH_CHECK_LAUNCH();
 }
 
-void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
-            double *partials, const int *done, cudaStream_t s, const double *alpha_dev) {
+// The epilogue of a plan that holds a range of the windows, after its share
+// of Gamma_full x has been summed over the ranks into y: y = op(x, y) in place
+// (as in the interpolation's epilogue) with the block partials of x^T y.
+__global__ void __launch_bounds__(kRedThreads)
+k_share_epilogue(const double *__restrict__ x, const double *__restrict__ d, double *__restrict__ y,
+                 int64_t N, int op, double alpha_val, const double *__restrict__ alpha_dev,
+                 double *__restrict__ partials, int nparts, const int *__restrict__ done) {
+    __shared__ double sh[33];
+    if (done && *done) return;
+    const double alpha = alpha_dev ? *alpha_dev : alpha_val;
+    double part = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = y[i], xi = x[i];
+        double out = s;
+        if (op != 0) {
+            out = d[i] * xi - s;
+            if (op == 2) out = fma(alpha, xi, out);
+        }
+        y[i] = out;
+        part = fma(xi, out, part);
+    }
+    if (partials) {
+        const double bs = block_sum(part, sh);
+        if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+        if (blockIdx.x == 0)
+            for (int j = gridDim.x + threadIdx.x; j < nparts; j += blockDim.x) partials[j] = 0.0;
+    }
+}
+
+// The epilogue of a plan of several windows, after every window has added
+// its values into the per-pixel sums: y = op(x, inv_l sum) with the block
+// partials of x^T y; the sums are cleared for the next matvec.
+__global__ void __launch_bounds__(kRedThreads)
+k_finish(double *__restrict__ yacc, const double *__restrict__ x, const double *__restrict__ d,
+         double *__restrict__ y, int64_t N, double inv_l, int op, double alpha_val,
+         const double *__restrict__ alpha_dev, double *__restrict__ partials, int nparts,
+         const int *__restrict__ done) {
+    __shared__ double sh[33];
+    if (done && *done) return;
+    const double alpha = alpha_dev ? *alpha_dev : alpha_val;
+    double part = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = yacc[i] * inv_l;
+        yacc[i] = 0.0;
+        double out = s;
+        if (op != 0) {
+            const double xi = x[i];
+            out = d[i] * xi - s;
+            if (op == 2) out = fma(alpha, xi, out);
+        }
+        y[i] = out;
+        if (partials) part = fma(x[i], out, part);
+    }
+    if (partials) {
+        const double bs = block_sum(part, sh);
+        if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+        if (blockIdx.x == 0)
+            for (int j = gridDim.x + threadIdx.x; j < nparts; j += blockDim.x) partials[j] = 0.0;
+    }
+}
+
+static void matvec_prec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
+                        double *partials, const int *done, cudaStream_t s,
+                        const double *alpha_dev) {
     if (prec == NLH_FP64) {
         NLH_REQUIRE(P.precision & 1, "matvec: FP64 path not built in this plan");
-        matvec_t<double>(P, op, alpha, alpha_dev, x, y, partials, done, P.wts64, P.grid64,
+        matvec_t<double>(P, op, alpha, alpha_dev, x, y, partials, done, P.gridA64, P.gridB64,
                          P.tab64, P.tw64, P.d64, s);
     } else if (prec == NLH_FP32) {
         NLH_REQUIRE(P.precision & 2, "matvec: FP32 path not built in this plan");
-        matvec_t<float>(P, op, alpha, alpha_dev, x, y, partials, done, P.wts32, P.grid32,
+        matvec_t<float>(P, op, alpha, alpha_dev, x, y, partials, done, P.gridA32, P.gridB32,
                         P.tab32, P.tw32, P.d32, s);
     } else {
         NLH_REQUIRE(P.precision & 4, "matvec: double-float path not built in this plan");
-        matvec_t<df32>(P, op, alpha, alpha_dev, x, y, partials, done, P.wtsdf, P.grid64,
+        matvec_t<df32>(P, op, alpha, alpha_dev, x, y, partials, done, P.gridA64, P.gridB64,
                        reinterpret_cast<const df32 *>(P.tabdf),
                        reinterpret_cast<const cdf *>(P.twdf), P.ddf, s);
     }
+}
+
+static const double *degrees_of(const Plan &P, int prec) {
+    return prec == NLH_FP64 ? P.d64 : prec == NLH_FP32 ? P.d32 : P.ddf;
+}
+
+// A plan of all windows runs the matvec directly.  A plan that holds a range
+// of the windows computes its share of Gamma_full x (normalised by the count
+// of all windows); with a reduce callback that share is summed over the
+// ranks in y and the epilogue follows, so that every op is the operator of
+// all windows; without one, only op 0 (the share itself) is defined.
+void matvec(Plan &P, int op, int prec, double alpha, const double *x, double *y,
+            double *partials, const int *done, cudaStream_t s, const double *alpha_dev) {
+    if (P.L == P.L_norm) {
+        matvec_prec(P, op, prec, alpha, x, y, partials, done, s, alpha_dev);
+        return;
+    }
+    NLH_REQUIRE(op == 0 || P.reduce_fn,
+                "matvec: op %d on a plan of a window range needs a reduce callback", op);
+    matvec_prec(P, 0, prec, 0.0, x, y, nullptr, done, s, nullptr);
+    if (!P.reduce_fn) return;
+    P.reduce_fn(y, P.N, (void *)s, P.reduce_ctx);
+    if (op == 0 && !partials) return;
+    ProfRange pr(NLH_K_EPILOGUE, s);
+    k_share_epilogue<<<kRedBlocks, kRedThreads, 0, s>>>(x, degrees_of(P, prec), y, P.N, op, alpha,
+                                                        alpha_dev, partials, kPqSlots, done);
+    NLH_CHECK_LAUNCH();
+}
+
+// Resolves every NFFT kernel of the library on the current device once, so
+// that no kernel is first loaded while a plan's work is queued or a solve is
+// being captured.
+void prepare_nfft_kernels() {
+    static std::mutex mu;
+    static bool done_once[64] = {false};
+    int dev = 0;
+    NLH_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done_once[dev]) return;
+    prepare_t<double>();
+    prepare_t<float>();
+    prepare_t<df32>();
+    cudaFuncAttributes fa;
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_share_epilogue));
+    NLH_CUDA(cudaFuncGetAttributes(&fa, k_finish));
+    if (dev >= 0 && dev < 64) done_once[dev] = true;
+}
+
+// Takes the first failed index check of the NFFT kernels (and clears the
+// record); returns 0 if there was none.  Synchronous.
+int nfft_check_take(int *info5) {
+    int rec[5] = {0, 0, 0, 0, 0};
+    NLH_CUDA(cudaMemcpyFromSymbol(rec, g_nfft_check, sizeof rec));
+    if (rec[0] != 0) {
+        const int zero[5] = {0, 0, 0, 0, 0};
+        NLH_CUDA(cudaMemcpyToSymbol(g_nfft_check, zero, sizeof zero));
+    }
+    if (info5)
+        for (int k = 0; k < 5; ++k) info5[k] = rec[k];
+    return rec[0];
 }
 
 }  // namespace nlh

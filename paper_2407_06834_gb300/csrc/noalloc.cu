@@ -54,20 +54,29 @@ k_residual_finish(const double *__restrict__ partials, int nblocks, double *__re
     }
 }
 
-// Device address of the partials array, looked up once per device with that
-// device current.
-static double *noalloc_partials_ptr() {
+// Device address of the partials array on the current device.  Outside
+// stream capture it is looked up afresh on every call (cudaGetSymbolAddress
+// allocates nothing), so that a device reset or a new primary context never
+// leaves a stale address behind; the last address seen per device is kept
+// for calls made while `stream` is being captured, where the lookup itself
+// may not be issued.  A first call on a device during capture is an error.
+static double *noalloc_partials_ptr(cudaStream_t stream) {
     static std::mutex mu;
     static double *cache[64] = {nullptr};
     int dev = 0;
     NLH_CUDA(cudaGetDevice(&dev));
     NLH_REQUIRE(dev >= 0 && dev < 64, "nlh_residual_norms_noalloc: device %d unsupported", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NLH_CUDA(cudaStreamIsCapturing(stream, &cap));
     std::lock_guard<std::mutex> lk(mu);
-    if (!cache[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *ptr = nullptr;
         NLH_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
         cache[dev] = static_cast<double *>(ptr);
     }
+    NLH_REQUIRE(cache[dev],
+                "nlh_residual_norms_noalloc: the first call on a device must come before any "
+                "stream capture");
     return cache[dev];
 }
 
@@ -83,8 +92,8 @@ extern "C" nlh_status nlh_residual_norms_noalloc(const double *b, const double *
                     "nlh_residual_norms_noalloc: N=%lld exceeds the maximum %lld of the fixed "
                     "scratch array",
                     (long long)N, (long long)nlh::kNoAllocMaxN);
-        double *partials = nlh::noalloc_partials_ptr();
         cudaStream_t s = (cudaStream_t)stream;
+        double *partials = nlh::noalloc_partials_ptr(s);
         const int nblocks = nlh::div_up(N, nlh::kNoAllocChunk);
         nlh::k_residual_chunks<<<nblocks, nlh::kRedThreads, 0, s>>>(b, q, N, res, partials);
         NLH_CHECK_LAUNCH();

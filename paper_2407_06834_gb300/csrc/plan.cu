@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <cmath>
 #include <cstdarg>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
@@ -382,169 +383,123 @@ __global__ void k_emit_items(const int *__restrict__ hist, const int *__restrict
 // 2m grid points g = c - m + 1 + j, j = 0..2m-1, at offsets g - u in
 // (-m, m], with weight P_j(f) = phi((j - m + 1 - f) / m).  Because
 // I0(beta sqrt(z)) is an entire function of z, each P_j is analytic on
-// [0, 1]; it is fitted once per plan by Chebyshev interpolation in
-// y = 2f - 1, converted to a polynomial in y (validated against direct
-// evaluation on the host) and evaluated by Horner's rule per point.
-constexpr int kMaxPolyCoef = 24;
-
+// [0, 1].  With y = 2 f - 1, P_{2m-1-j}(y) = P_j(-y), so only j < m is
+// fitted: Chebyshev interpolation of P_j in y of a fixed degree, converted to
+// monomials and split into the even part E_j(y^2) and the odd part
+// y O_j(y^2) (window.cuh evaluates both weights of a pair from them).  The
+// fit is checked on the host against direct Bessel evaluation, for both
+// weights of every pair.
 static double kb_host(double x, double beta) {
     double z = 1.0 - x * x;
     if (z < 0.0) return 0.0;
     return std::cyl_bessel_i(0.0, beta * std::sqrt(z)) / std::cyl_bessel_i(0.0, beta);
 }
 
-// Monomial coefficients (in y) of the degree-D Chebyshev interpolant of
-// P_j, for every j; returns D + 1 (coefficients per j), or throws.  Fits
-// are cached per (m, beta): they depend on nothing else.
-static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &coef);
+// Monomial coefficients a[j][k], k < K, of the degree-(K-1) Chebyshev
+// interpolant of P_j, j < m; returns the largest deviation from the window
+// over both weights of each pair on a fine grid of y.
+static double fit_pairs(int m, double beta, int K, std::vector<double> &a) {
+    a.assign((size_t)m * K, 0.0);
+    double worst = 0.0;
+    for (int j = 0; j < m; ++j) {
+        auto Pj = [&](double y) { return kb_host((j - m + 1 - 0.5 * (y + 1.0)) / m, beta); };
+        std::vector<double> c(K, 0.0), g(K);
+        for (int i = 0; i < K; ++i) g[i] = Pj(std::cos(M_PI * (i + 0.5) / K));
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < K; ++i) acc += g[i] * std::cos(M_PI * k * (i + 0.5) / K);
+            c[k] = (k == 0 ? 1.0 : 2.0) * acc / K;
+        }
+        // Chebyshev -> monomial: T_{k+1} = 2 y T_k - T_{k-1}
+        std::vector<double> tkm1(K, 0.0), tk(K, 0.0), mono(K, 0.0);
+        tkm1[0] = 1.0;
+        if (K > 1) tk[1] = 1.0;
+        for (int i = 0; i < K; ++i) mono[i] += c[0] * tkm1[i];
+        if (K > 1)
+            for (int i = 0; i < K; ++i) mono[i] += c[1] * tk[i];
+        for (int k = 2; k < K; ++k) {
+            std::vector<double> tn(K, 0.0);
+            for (int i = 0; i < K; ++i) {
+                if (i > 0) tn[i] += 2.0 * tk[i - 1];
+                tn[i] -= tkm1[i];
+            }
+            for (int i = 0; i < K; ++i) mono[i] += c[k] * tn[i];
+            tkm1 = tk;
+            tk = tn;
+        }
+        for (int i = 0; i < K; ++i) a[(size_t)j * K + i] = mono[i];
+        const int jm = 2 * m - 1 - j;
+        for (int q = 0; q <= 400; ++q) {
+            const double y = -1.0 + q / 200.0, u = y * y;
+            double e = 0.0, o = 0.0;
+            for (int k = (K - 1) / 2 * 2; k >= 0; k -= 2) e = e * u + mono[k];
+            for (int k = (K - 2) / 2 * 2 + 1; k >= 1; k -= 2) o = o * u + mono[k];
+            const double fx = (jm - m + 1 - 0.5 * (y + 1.0)) / m;
+            worst = std::max(worst, std::fabs(e + y * o - Pj(y)));
+            worst = std::max(worst, std::fabs(e - y * o - kb_host(fx, beta)));
+        }
+    }
+    return worst;
+}
 
-static int fit_weight_polys(int m, double beta, std::vector<double> &coef) {
+// The three coefficient sets of a plan (cached per (m, beta): they depend on
+// nothing else).  FP64 and double-float: degree 15, <= 2e-14 off the window;
+// FP32: degree 9, <= 1e-7 (below what FP32 weights resolve).
+struct WinSets {
+    WinPoly<float> f32;
+    WinPoly<double> f64;
+    WinPoly<df32> fdf;
+};
+
+static WinSets fit_window(int m, double beta) {
     static std::mutex mu;
-    static std::map<std::pair<int, double>, std::pair<int, std::vector<double>>> cache;
+    static std::map<std::pair<int, double>, WinSets> cache;
     std::lock_guard<std::mutex> lk(mu);
     auto key = std::make_pair(m, beta);
     auto it = cache.find(key);
-    if (it == cache.end()) {
-        std::vector<double> c;
-        int K = fit_weight_polys_uncached(m, beta, c);
-        it = cache.emplace(key, std::make_pair(K, c)).first;
-    }
-    coef = it->second.second;
-    return it->second.first;
-}
-
-static int fit_weight_polys_uncached(int m, double beta, std::vector<double> &coef) {
-    const int W2 = 2 * m;
-    for (int D = 8; D < kMaxPolyCoef; ++D) {
-        const int K = D + 1;
-        coef.assign((size_t)W2 * K, 0.0);
-        double worst = 0.0;
-        for (int j = 0; j < W2; ++j) {
-            auto Pj = [&](double y) { return kb_host((j - m + 1 - 0.5 * (y + 1.0)) / m, beta); };
-            std::vector<double> c(K, 0.0), g(K);
-            for (int i = 0; i < K; ++i) g[i] = Pj(std::cos(M_PI * (i + 0.5) / K));
-            for (int k = 0; k < K; ++k) {
-                double acc = 0.0;
-                for (int i = 0; i < K; ++i) acc += g[i] * std::cos(M_PI * k * (i + 0.5) / K);
-                c[k] = (k == 0 ? 1.0 : 2.0) * acc / K;
+    if (it != cache.end()) return it->second;
+    NLH_REQUIRE(m >= 1 && m <= kWinHalfMax, "internal: window half-width %d", m);
+    WinSets w;
+    std::memset(&w, 0, sizeof w);
+    std::vector<double> a64, a32;
+    const double e64 = fit_pairs(m, beta, 2 * kWinK64, a64);
+    const double e32 = fit_pairs(m, beta, 2 * kWinK32, a32);
+    NLH_REQUIRE(e64 <= 2e-14 && e32 <= 1e-7,
+                "window polynomials do not reach their accuracy for m=%d, beta=%g (%.2e, %.2e)", m,
+                beta, e64, e32);
+    for (int j = 0; j < m; ++j)
+        for (int par = 0; par < 2; ++par) {
+            for (int k = 0; k < kWinK64; ++k) {
+                const double c = a64[(size_t)j * 2 * kWinK64 + 2 * k + par];
+                w.f64.c[j][par][k] = c;
+                const float hi = (float)c;
+                w.fdf.hi[j][par][k] = hi;
+                w.fdf.lo[j][par][k] = (float)(c - (double)hi);
             }
-            // Chebyshev -> monomial: T_{k+1} = 2 y T_k - T_{k-1}
-            std::vector<double> tkm1(K, 0.0), tk(K, 0.0), a(K, 0.0);
-            tkm1[0] = 1.0;
-            if (K > 1) tk[1] = 1.0;
-            for (int i = 0; i < K; ++i) a[i] += c[0] * tkm1[i];
-            if (K > 1)
-                for (int i = 0; i < K; ++i) a[i] += c[1] * tk[i];
-            for (int k = 2; k < K; ++k) {
-                std::vector<double> tn(K, 0.0);
-                for (int i = 0; i < K; ++i) {
-                    if (i > 0) tn[i] += 2.0 * tk[i - 1];
-                    tn[i] -= tkm1[i];
-                }
-                for (int i = 0; i < K; ++i) a[i] += c[k] * tn[i];
-                tkm1 = tk;
-                tk = tn;
-            }
-            for (int i = 0; i < K; ++i) coef[(size_t)j * K + i] = a[i];
-            for (int q = 0; q <= 100; ++q) {
-                double y = -1.0 + q / 50.0, h = 0.0;
-                for (int i = K - 1; i >= 0; --i) h = h * y + a[i];
-                worst = std::max(worst, std::fabs(h - Pj(y)));
-            }
+            for (int k = 0; k < kWinK32; ++k)
+                w.f32.c[j][par][k] = (float)a32[(size_t)j * 2 * kWinK32 + 2 * k + par];
         }
-        if (worst < 2e-14) return K;
-    }
-    set_error("internal: window polynomial fit did not converge (m=%d)", m);
-    throw Failure{NLH_ERR_ARG};
+    cache.emplace(key, w);
+    return w;
 }
 
-// The 2m weights of one dim are 2m independent Horner chains; a compile-time
-// 2m lets them advance in lockstep (instruction-level parallelism across
-// the dependent multiply-add steps).
-template <int W2>
-__global__ void k_weights(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
-                          int L, int K, const double *__restrict__ coef, int rec64, int rec32,
-                          double *__restrict__ w64, float *__restrict__ w32,
-                          float *__restrict__ wdf) {
-    __shared__ double sc[16 * kMaxPolyCoef];
-    for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
-    __syncthreads();
+// Cell offsets of the sorted points: y = 2 (u - floor u) - 1 per dim (u the
+// grid coordinate of k_cell_keys), as a float and the float remainder.
+__global__ void k_offsets(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
+                          int L, float *__restrict__ yhi, float *__restrict__ ylo) {
     const int64_t total = (int64_t)L * N;
     for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < total;
          sidx += (int64_t)gridDim.x * blockDim.x) {
-        int l = (int)(sidx / N);
-        int64_t i = perm[sidx];
-        const double *up = u + ((int64_t)l * N + i) * 3;
-        for (int t = 0; t < 3; ++t) {
-            double ut = up[t];
-            double y = 2.0 * (ut - floor(ut)) - 1.0;
-            double w[W2];
-#pragma unroll
-            for (int j = 0; j < W2; ++j) w[j] = sc[j * K + K - 1];
-            for (int q = K - 2; q >= 0; --q)
-#pragma unroll
-                for (int j = 0; j < W2; ++j) w[j] = fma(w[j], y, sc[j * K + q]);
-#pragma unroll
-            for (int j = 0; j < W2; ++j) {
-                if (w64) w64[sidx * rec64 + t * W2 + j] = w[j];
-                if (w32) w32[sidx * rec32 + t * W2 + j] = (float)w[j];
-                if (wdf) {  // double-float record: per dim 2m high parts, then 2m low parts
-                    const float hi = (float)w[j];
-                    wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
-                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = (float)(w[j] - (double)hi);
-                }
-            }
-        }
-        if (w64)
-            for (int j = 3 * W2; j < rec64; ++j) w64[sidx * rec64 + j] = 0.0;
-        if (w32)
-            for (int j = 3 * W2; j < rec32; ++j) w32[sidx * rec32 + j] = 0.0f;
-    }
-}
-
-// The same polynomials evaluated in double-float arithmetic on the FP32
-// pipes (Horner with TwoProduct / TwoSum steps, coefficients split into
-// high and low floats), for plans without the FP64 path: ~46-bit weights
-// for the double-float records, their rounded high parts for the FP32
-// records.  GB300 runs FP32 ~59x faster than FP64, so this is several times
-// faster than the FP64 Horner above.
-template <int W2>
-__global__ void k_weights_df(const int *__restrict__ perm, const double *__restrict__ u,
-                             int64_t N, int L, int K, const float2 *__restrict__ coef,
-                             int rec32, float *__restrict__ w32, float *__restrict__ wdf) {
-    __shared__ float2 sc[16 * kMaxPolyCoef];
-    for (int e = threadIdx.x; e < W2 * K; e += blockDim.x) sc[e] = coef[e];
-    __syncthreads();
-    const int64_t total = (int64_t)L * N;
-    for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < total;
-         sidx += (int64_t)gridDim.x * blockDim.x) {
-        int l = (int)(sidx / N);
-        int64_t i = perm[sidx];
+        const int l = (int)(sidx / N);
+        const int64_t i = perm[sidx];
         const double *up = u + ((int64_t)l * N + i) * 3;
         for (int t = 0; t < 3; ++t) {
             const double ut = up[t];
-            const df32 y(2.0 * (ut - floor(ut)) - 1.0);
-            df32 w[W2];
-#pragma unroll
-            for (int j = 0; j < W2; ++j) w[j] = df32(sc[j * K + K - 1].x, sc[j * K + K - 1].y);
-            for (int q = K - 2; q >= 0; --q)
-#pragma unroll
-                for (int j = 0; j < W2; ++j)
-                    w[j] = w[j] * y + df32(sc[j * K + q].x, sc[j * K + q].y);
-#pragma unroll
-            for (int j = 0; j < W2; ++j) {
-                // renormalise (Fast2Sum; |lo| is a few ulps of hi at most)
-                const float hi = __fadd_rn(w[j].hi, w[j].lo);
-                const float lo = __fsub_rn(w[j].lo, __fsub_rn(hi, w[j].hi));
-                if (w32) w32[sidx * rec32 + t * W2 + j] = hi;
-                if (wdf) {
-                    wdf[sidx * 6 * W2 + t * 2 * W2 + j] = hi;
-                    wdf[sidx * 6 * W2 + t * 2 * W2 + W2 + j] = lo;
-                }
-            }
+            const double y = 2.0 * (ut - floor(ut)) - 1.0;
+            const float hi = (float)y;
+            yhi[sidx * 3 + t] = hi;
+            if (ylo) ylo[sidx * 3 + t] = (float)(y - (double)hi);
         }
-        if (w32)
-            for (int j = 3 * W2; j < rec32; ++j) w32[sidx * rec32 + j] = 0.0f;
     }
 }
 
@@ -891,9 +846,16 @@ void check_device_error(Plan &P, cudaStream_t s) {
     int e = 0;
     NLH_CUDA(cudaMemcpyAsync(&e, P.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     NLH_CUDA(cudaStreamSynchronize(s));
+    int chk[5];
+    if (nfft_check_take(chk) != 0) {
+        set_error("an NFFT kernel found an index of the plan data out of range and skipped it "
+                  "(check %d: index %d, bound %d, block %d, thread %d)",
+                  chk[0], chk[1], chk[2], chk[3], chk[4]);
+        throw Failure{NLH_ERR_CUDA};
+    }
     if (e != 0) {
         NLH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), s));
-        set_error("a bulk copy did not complete within its bounded wait (status %d)", e);
+        set_error("a bounded device wait did not complete in time (status %d)", e);
         throw Failure{NLH_ERR_TIMEOUT};
     }
 }
@@ -904,6 +866,8 @@ void check_device_error(Plan &P, cudaStream_t s) {
 // degrees from the accurate path leaves L 1 at the FP32 NFFT error times d,
 // which the mixed form's inner solves see: 14 instead of 10 iterations at
 // 512 x 512.)
+// A plan that holds a range of the windows and has a reduce callback sums its
+// share over the ranks (matvec does that for op 0).
 void plan_degrees(Plan &P, cudaStream_t s) {
     k_fill<<<kRedBlocks, kRedThreads, 0, s>>>(P.t, P.N, 1.0);
     NLH_CHECK_LAUNCH();
@@ -917,7 +881,6 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     NLH_CUDA(cudaGetDevice(&P.device));
     P.N = desc.N;
     P.D = desc.D;
-    P.L = desc.L;
     P.M = desc.M;
     P.n = desc.n_os;
     P.m = desc.m;
@@ -927,31 +890,43 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.kmax = desc.max_items_pts > 0 ? desc.max_items_pts : 64;
     P.unit_points = desc.unit_points > 0 ? desc.unit_points : kUnitPoints;
     for (int a = 0; a < 3; ++a) {
-        NLH_REQUIRE(desc.team[a] >= 0 && desc.team[a] <= 3, "nlh_plan_create: team[%d]=%d", a,
+        NLH_REQUIRE(desc.team[a] >= 0 && desc.team[a] <= 2, "nlh_plan_create: team[%d]=%d", a,
                     desc.team[a]);
         P.team[a] = desc.team[a];
     }
-    P.windows.assign(desc.windows, desc.windows + 3 * desc.L);
+    // the plan's windows: all of them, or the range [window_first,
+    // window_first + window_count) of the list (the torus map is taken over
+    // the whole list, so that plans of complementary ranges sum to the
+    // operator of all windows)
+    const int L_all = desc.L;
+    const int wf = desc.window_count > 0 ? desc.window_first : 0;
+    const int L = desc.window_count > 0 ? desc.window_count : L_all;
+    P.L = L;
+    P.L_norm = L_all;
+    P.window_first = wf;
+    P.reduce_fn = desc.reduce;
+    P.reduce_ctx = desc.reduce_ctx;
+    P.windows.assign(desc.windows, desc.windows + 3 * L_all);
     const int64_t N = P.N;
-    const int L = P.L;
 
-    int *d_win = P.alloc<int>(3 * L);
-    NLH_CUDA(cudaMemcpyAsync(d_win, P.windows.data(), sizeof(int) * 3 * L,
+    int *d_win = P.alloc<int>(3 * L_all);
+    NLH_CUDA(cudaMemcpyAsync(d_win, P.windows.data(), sizeof(int) * 3 * L_all,
                              cudaMemcpyHostToDevice, s));
 
     // per-window, per-dim ranges -> torus map
     const int nb = 152;
-    double *part = P.alloc<double>((size_t)3 * L * nb * 2);
-    double *mm = P.alloc<double>((size_t)3 * L * 2);
-    k_minmax_partial<<<dim3(nb, 3 * L), 256, 0, s>>>(features, N, P.D, d_win, part);
+    double *part = P.alloc<double>((size_t)3 * L_all * nb * 2);
+    double *mm = P.alloc<double>((size_t)3 * L_all * 2);
+    k_minmax_partial<<<dim3(nb, 3 * L_all), 256, 0, s>>>(features, N, P.D, d_win, part);
     NLH_CHECK_LAUNCH();
-    k_minmax_final<<<3 * L, 32, 0, s>>>(part, nb, mm);
+    k_minmax_final<<<3 * L_all, 32, 0, s>>>(part, nb, mm);
     NLH_CHECK_LAUNCH();
-    std::vector<double> hmm(6 * L), center(3 * L);
-    NLH_CUDA(cudaMemcpyAsync(hmm.data(), mm, sizeof(double) * 6 * L, cudaMemcpyDeviceToHost, s));
+    std::vector<double> hmm(6 * L_all), center(3 * L_all);
+    NLH_CUDA(cudaMemcpyAsync(hmm.data(), mm, sizeof(double) * 6 * L_all, cudaMemcpyDeviceToHost,
+                             s));
     NLH_CUDA(cudaStreamSynchronize(s));
     double R = 0.0;
-    for (int c = 0; c < 3 * L; ++c) {
+    for (int c = 0; c < 3 * L_all; ++c) {
         NLH_REQUIRE(std::isfinite(hmm[2 * c]) && std::isfinite(hmm[2 * c + 1]),
                     "features contain non-finite values");
         center[c] = 0.5 * (hmm[2 * c] + hmm[2 * c + 1]);
@@ -967,13 +942,35 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     }
     P.scale = P.fill / R;
     P.kb_beta = M_PI * P.m * (2.0 - (double)P.M / P.n);
+    {
+        const WinSets ws = fit_window(P.m, P.kb_beta);
+        P.wp32 = ws.f32;
+        P.wp64 = ws.f64;
+        P.wpdf = ws.fdf;
+        // staged tables for the kernels' shared-memory copies: FP64 {E_k, O_k}
+        // per (j, k), then double-float {E hi, E lo, O hi, O lo} per (j, k)
+        std::vector<float4> st(2 * kWinStageBytes / 16, make_float4(0.f, 0.f, 0.f, 0.f));
+        double2 *st64 = reinterpret_cast<double2 *>(st.data());
+        for (int j = 0; j < kWinHalfMax; ++j)
+            for (int k = 0; k < kWinK64; ++k)
+                st64[j * kWinK64 + k] = make_double2(ws.f64.c[j][0][k], ws.f64.c[j][1][k]);
+        float4 *stdf = st.data() + kWinStageBytes / 16;
+        for (int j = 0; j < kWinHalfMax; ++j)
+            for (int k = 0; k < kWinK64; ++k)
+                stdf[j * kWinK64 + k] = make_float4(ws.fdf.hi[j][0][k], ws.fdf.lo[j][0][k],
+                                                    ws.fdf.hi[j][1][k], ws.fdf.lo[j][1][k]);
+        P.wstage = P.alloc<float4>(st.size());
+        NLH_CUDA(cudaMemcpyAsync(P.wstage, st.data(), sizeof(float4) * st.size(),
+                                 cudaMemcpyHostToDevice, s));
+        NLH_CUDA(cudaStreamSynchronize(s));  // the host table is a local
+    }
     const int n = P.n;
     const int64_t n3 = (int64_t)n * n * n;
-    double *d_center = P.alloc<double>(3 * L);
-    NLH_CUDA(cudaMemcpyAsync(d_center, center.data(), sizeof(double) * 3 * L,
+    double *d_center = P.alloc<double>(3 * L_all);
+    NLH_CUDA(cudaMemcpyAsync(d_center, center.data(), sizeof(double) * 3 * L_all,
                              cudaMemcpyHostToDevice, s));
 
-    // grid coordinates, cell keys and per-cell counts
+    // grid coordinates, cell keys and per-cell counts (the plan's windows)
     const int64_t LN = (int64_t)L * N;
     double *u = nullptr;
     int *keys = nullptr, *hist = nullptr, *start = nullptr, *cnt = nullptr, *ioff = nullptr,
@@ -996,8 +993,8 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         NLH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * ncells, s));
         NLH_CUDA(cudaMemsetAsync(scal, 0, sizeof(int) * 2, s));
         const int gb = 152 * 8;
-        k_cell_keys<<<gb, 256, 0, s>>>(features, N, P.D, L, d_win, d_center, P.scale, n, u, keys,
-                                       hist);
+        k_cell_keys<<<gb, 256, 0, s>>>(features, N, P.D, L, d_win + 3 * wf, d_center + 3 * wf,
+                                       P.scale, n, u, keys, hist);
         NLH_CHECK_LAUNCH();
         exclusive_scan_dev(hist, start, ncells, s, sums, scal);
         P.perm = P.alloc<int32_t>(LN);
@@ -1013,61 +1010,10 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n, P.kmax, P.items);
         NLH_CHECK_LAUNCH();
         build_units(P, s);
-        // weights in sorted order
-        std::vector<double> coef;
-        const int K = fit_weight_polys(P.m, P.kb_beta, coef);
-        double *d_coef = nullptr;
-        NLH_CUDA(cudaMallocAsync(&d_coef, sizeof(double) * coef.size(), s));
-        tmp.push_back(d_coef);
-        NLH_CUDA(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(),
-                                 cudaMemcpyHostToDevice, s));
-        const int rec64 = record_len(P.W2, 8), rec32 = record_len(P.W2, 4);
-        if (P.precision & 1) P.wts64 = P.alloc<double>((size_t)LN * rec64);
-        if (P.precision & 2) P.wts32 = P.alloc<float>((size_t)LN * rec32);
-        if (P.precision & 4) P.wtsdf = P.alloc<float>((size_t)LN * 6 * P.W2);
-        if (P.precision & 1) {
-            auto fp64 = [&](auto w2) {
-                constexpr int W = decltype(w2)::value;
-                k_weights<W><<<gb, 256, 0, s>>>(P.perm, u, N, L, K, d_coef, rec64, rec32, P.wts64,
-                                                P.wts32, P.wtsdf);
-            };
-            switch (P.W2) {
-                case 4: fp64(std::integral_constant<int, 4>()); break;
-                case 6: fp64(std::integral_constant<int, 6>()); break;
-                case 8: fp64(std::integral_constant<int, 8>()); break;
-                case 10: fp64(std::integral_constant<int, 10>()); break;
-                case 12: fp64(std::integral_constant<int, 12>()); break;
-                case 14: fp64(std::integral_constant<int, 14>()); break;
-                case 16: fp64(std::integral_constant<int, 16>()); break;
-                default: NLH_REQUIRE(false, "internal: stencil width %d", P.W2);
-            }
-        } else {
-            std::vector<float2> cdf(coef.size());
-            for (size_t e = 0; e < coef.size(); ++e) {
-                const float hi = (float)coef[e];
-                cdf[e] = make_float2(hi, (float)(coef[e] - (double)hi));
-            }
-            float2 *d_cdf = nullptr;
-            NLH_CUDA(cudaMallocAsync(&d_cdf, sizeof(float2) * cdf.size(), s));
-            tmp.push_back(d_cdf);
-            NLH_CUDA(cudaMemcpyAsync(d_cdf, cdf.data(), sizeof(float2) * cdf.size(),
-                                     cudaMemcpyHostToDevice, s));
-            auto dfw = [&](auto w2) {
-                constexpr int W = decltype(w2)::value;
-                k_weights_df<W><<<gb, 256, 0, s>>>(P.perm, u, N, L, K, d_cdf, rec32, P.wts32,
-                                                   P.wtsdf);
-            };
-            switch (P.W2) {
-                case 4: dfw(std::integral_constant<int, 4>()); break;
-                case 6: dfw(std::integral_constant<int, 6>()); break;
-                case 8: dfw(std::integral_constant<int, 8>()); break;
-                case 10: dfw(std::integral_constant<int, 10>()); break;
-                case 12: dfw(std::integral_constant<int, 12>()); break;
-                case 14: dfw(std::integral_constant<int, 14>()); break;
-                case 16: dfw(std::integral_constant<int, 16>()); break;
-                default: NLH_REQUIRE(false, "internal: stencil width %d", P.W2);
-            }
-        }
+        // cell offsets in sorted order (the low parts for the FP64-accurate paths)
+        P.yhi = P.alloc<float>((size_t)LN * 3);
+        if (P.precision & 5) P.ylo = P.alloc<float>((size_t)LN * 3);
+        k_offsets<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.yhi, P.ylo);
         NLH_CHECK_LAUNCH();
         P.occupied = occ;
     } catch (...) {
@@ -1080,8 +1026,9 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     if (P.precision & 5) {  // FP64 and double-float paths share FP64 grids and tables
         P.tab64 = P.alloc<double>(n);
         P.tw64 = P.alloc<double2>(n / 2);
-        P.grid64 = P.alloc<double>((size_t)L * n3);
-        NLH_CUDA(cudaMemsetAsync(P.grid64, 0, sizeof(double) * L * n3, s));
+        P.gridA64 = P.alloc<double>((size_t)L * n3);
+        P.gridB64 = P.alloc<double>((size_t)L * n3);
+        NLH_CUDA(cudaMemsetAsync(P.gridA64, 0, sizeof(double) * L * n3, s));
     }
     if (P.precision & 1) P.d64 = P.alloc<double>(N);
     if (P.precision & 4) {
@@ -1092,12 +1039,13 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     if (P.precision & 2) {
         P.tab32 = P.alloc<float>(n);
         P.tw32 = P.alloc<float2>(n / 2);
-        P.grid32 = P.alloc<float>((size_t)L * n3);
-        NLH_CUDA(cudaMemsetAsync(P.grid32, 0, sizeof(float) * L * n3, s));
+        P.gridA32 = P.alloc<float>((size_t)L * n3);
+        P.gridB32 = P.alloc<float>((size_t)L * n3);
+        NLH_CUDA(cudaMemsetAsync(P.gridA32, 0, sizeof(float) * L * n3, s));
         P.d32 = P.alloc<double>(N);
     }
-    P.Y = P.alloc<double>(LN);
-    P.xs = P.alloc<double>(LN);
+    P.yacc = P.alloc<double>(N);
+    NLH_CUDA(cudaMemsetAsync(P.yacc, 0, sizeof(double) * N, s));
     P.w = P.alloc<double>(N);
     P.r = P.alloc<double>(N);
     P.p = P.alloc<double>(N);
@@ -1107,7 +1055,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     P.pinv = P.alloc<double>(N);
     P.x0 = P.alloc<double>(N);
     P.cbuf = P.alloc<double>(N);
-    P.partials = P.alloc<double>((size_t)kRedBlocks * 12);
+    P.partials = P.alloc<double>((size_t)kRedBlocks * 12 + kPqSlots);
     P.st = P.alloc<SolveState>(1);
     P.err = P.alloc<int>(1);
     NLH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), s));
@@ -1178,11 +1126,18 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
                     d.precision);
         NLH_REQUIRE(d.torus_fill >= 0.0 && d.torus_fill < 1.0, "nlh_plan_create: torus_fill=%g",
                     d.torus_fill);
-        NLH_REQUIRE((int64_t)d.L * d.N < ((int64_t)1 << 31), "nlh_plan_create: L*N too large");
+        NLH_REQUIRE(d.window_count >= 0 && d.window_first >= 0 &&
+                        (d.window_count == 0 || d.window_first + d.window_count <= d.L),
+                    "nlh_plan_create: window range [%d, %d + %d) outside the %d windows",
+                    d.window_first, d.window_first, d.window_count, d.L);
+        NLH_REQUIRE((int64_t)(d.window_count > 0 ? d.window_count : d.L) * d.N <
+                        ((int64_t)1 << 31),
+                    "nlh_plan_create: L*N too large");
         for (int i = 0; i < 3 * d.L; ++i)
             NLH_REQUIRE(d.windows[i] >= -1 && d.windows[i] < d.D,
                         "nlh_plan_create: windows[%d]=%d out of range", i, d.windows[i]);
         retain_pool_memory();
+        prepare_nfft_kernels();
         P = new nlh_plan_s();
         P->stream = (cudaStream_t)stream;
         build_plan(*P, d, features, (cudaStream_t)stream);
@@ -1249,6 +1204,8 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info) {
         info->max_items_pts = plan->kmax;
         info->unit_points = plan->unit_points;
         for (int a = 0; a < 3; ++a) info->team[a] = plan->team[a];
+        info->window_first = plan->window_first;
+        info->window_count = plan->L;
         info->occupied_cells = plan->occupied;
         error_estimates(plan->sigma, plan->R, plan->fill, plan->M, &info->est_trunc_err,
                         &info->est_alias_err);
@@ -1280,30 +1237,11 @@ nlh_status nlh_plan_retile(nlh_plan plan, int max_items_pts, int unit_points, vo
     }
 }
 
-nlh_status nlh_plan_set_interp(nlh_plan plan, int kind) {
-    clear_error();
-    try {
-        NLH_REQUIRE(plan, "nlh_plan_set_interp: NULL plan");
-        NLH_REQUIRE(kind == NLH_INTERP_POINTS || kind == NLH_INTERP_TEAMS,
-                    "nlh_plan_set_interp: kind=%d", kind);
-        if (plan->interp_kind != kind) {
-            drop_graphs(*plan);
-            plan->interp_kind = kind;
-            plan_degrees(*plan, plan->stream);
-            plan->pb2_sigma = -1.0;
-            NLH_CUDA(cudaStreamSynchronize(plan->stream));
-        }
-        return NLH_OK;
-    } catch (Failure &f) {
-        return f.st;
-    }
-}
-
 nlh_status nlh_plan_set_team(nlh_plan plan, int arith, int shape) {
     clear_error();
     try {
         NLH_REQUIRE(plan, "nlh_plan_set_team: NULL plan");
-        NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 3,
+        NLH_REQUIRE(arith >= 0 && arith <= 2 && shape >= 0 && shape <= 2,
                     "nlh_plan_set_team: arith=%d shape=%d", arith, shape);
         if (plan->team[arith] != shape) {
             // new summation order: drop the captured solve graphs and
@@ -1341,10 +1279,6 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
         NLH_CUDA(cudaEventCreate(&e1));
         const int kmaxes[] = {32, 64, 128, 256};
         const int unitpts[] = {256, 512, 1024, 2048};
-        // Shapes 0-2.  The tensor-core FP32 shape (3) is left out: its 3xTF32
-        // rounding (~1e-6) weakens L 1 = 0 of the FP32 operator, and the
-        // mixed form's deflated inner solves then take more iterations
-        // (10 -> 14 at 512 x 512), which a matvec timing does not see.
         const int nshapes = (P.W2 == 8 || P.W2 == 12) ? 3 : 1;
         double best = INFINITY;
         int bk = P.kmax, bu = P.unit_points;

@@ -24,9 +24,10 @@
 
 namespace nlh {
 
-// Partials layout: stats at partials[b * 4 + j] (j = 0..3), the matvec
-// epilogue's x^T y at partials[4 * kRedBlocks + b].
-__device__ __forceinline__ double *pq_parts(double *partials) { return partials + 4 * kRedBlocks; }
+// Partials layout: stats at partials[b * 4 + j] (j = 0..3), the second set
+// of the start-up at partials[5 * kRedBlocks + b * 4 + j], the matvec
+// epilogue's x^T y at partials[12 * kRedBlocks + b] (kPqSlots blocks).
+__device__ __forceinline__ double *pq_parts(double *partials) { return partials + 12 * kRedBlocks; }
 
 // ------------------------------------------------------------------ kernels
 // pinv = 1 / (c o P) with P the Jacobi diagonal P_a = alpha + max(d - 1, 0)
@@ -185,7 +186,7 @@ k_update(double *__restrict__ w, double *__restrict__ r, const double *__restric
          int64_t N, double *__restrict__ partials, SolveState *__restrict__ st) {
     __shared__ double sh[33];
     if (st->done) return;
-    double pq = reduce_partials(pq_parts(partials), kRedBlocks, 1, 0, sh);
+    double pq = reduce_partials(pq_parts(partials), kPqSlots, 1, 0, sh);
     double rz = st->rz;
     if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -301,7 +302,7 @@ struct KrylovResult {
     int matvecs = 0;
 };
 
-static double *pq_parts_host(Plan &P) { return P.partials + 4 * kRedBlocks; }
+static double *pq_parts_host(Plan &P) { return P.partials + 12 * kRedBlocks; }
 
 static void method_flags(int method, int &deflate, int &precond) {
     deflate = (method == NLH_PCG_DEFLATED || method == NLH_CG_DEFLATED);

@@ -25,9 +25,12 @@ NLH_FP64, NLH_FP32, NLH_DF32 = 0, 1, 2
 PREC_PA, PREC_PB = 0, 1      # Jacobi P_a, and P_b' of Sec. 4.3.3
 CG, PCG_JACOBI, PCG_DEFLATED, CG_DEFLATED = 0, 1, 2, 3
 SOLVE_FP64, SOLVE_MIXED, SOLVE_DF32 = 0, 1, 2
-INTERP_POINTS, INTERP_TEAMS = 0, 1
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
                 -4: "ERR_BREAKDOWN", -5: "ERR_TIMEOUT"}
+
+
+# nlh_reduce_fn: (buf, n, stream, ctx) -> None, called on the host at enqueue time.
+REDUCE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
 
 
 class PlanDesc(C.Structure):
@@ -35,7 +38,9 @@ class PlanDesc(C.Structure):
                 ("windows", C.POINTER(C.c_int32)), ("sigma", C.c_double), ("M", C.c_int),
                 ("n_os", C.c_int), ("m", C.c_int), ("precision", C.c_int),
                 ("torus_fill", C.c_double), ("max_items_pts", C.c_int),
-                ("nfft_eps", C.c_double), ("unit_points", C.c_int), ("team", C.c_int * 3)]
+                ("nfft_eps", C.c_double), ("unit_points", C.c_int), ("team", C.c_int * 3),
+                ("window_first", C.c_int), ("window_count", C.c_int), ("reduce", REDUCE_FN),
+                ("reduce_ctx", C.c_void_p)]
 
 
 class PlanInfo(C.Structure):
@@ -46,7 +51,7 @@ class PlanInfo(C.Structure):
                 ("occupied_cells", C.c_int64), ("est_trunc_err", C.c_double),
                 ("est_alias_err", C.c_double), ("device_bytes", C.c_int64),
                 ("n_units", C.c_int64), ("max_items_pts", C.c_int), ("unit_points", C.c_int),
-                ("team", C.c_int * 3)]
+                ("team", C.c_int * 3), ("window_first", C.c_int), ("window_count", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -94,7 +99,6 @@ SIGNATURES = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.c_void_p]),
     "nlh_plan_set_team": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
-    "nlh_plan_set_interp": (C.c_int, [C.c_void_p, C.c_int]),
     "nlh_plan_destroy": (C.c_int, [C.c_void_p]),
     "nlh_last_error": (C.c_char_p, []),
     "nlh_version": (C.c_char_p, []),
@@ -240,13 +244,29 @@ class SolveResult:
     hist: np.ndarray
 
 
+def _device_view(ptr: int, n: int):
+    """A torch view of n device FP64 values at ptr (no copy), through the CUDA
+    array interface."""
+    torch = _torch()
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8",
+                                    "data": (int(ptr), False), "version": 3, "strides": None}
+    return torch.as_tensor(_View(), device="cuda")
+
+
 class Plan:
-    """An NFFT plan for one feature matrix (see nlh_plan_create)."""
+    """An NFFT plan for one feature matrix (see nlh_plan_create).
+
+    window_range=(first, count) builds the plan of that range of the windows
+    only; reduce, a callable (buf, stream) -> None that sums the FP64 CUDA
+    tensor buf in place over all ranks on that torch stream, makes such a
+    plan act as the operator of all windows (nlh_reduce_fn)."""
 
     def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
                  precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
                  nfft_eps: float = 0.0, unit_points: int = 0, autotune: bool = False,
-                 team=None, stream=None):
+                 team=None, window_range=None, reduce=None, stream=None):
         lib = load()
         N, D = features.shape
         win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
@@ -258,19 +278,32 @@ class Plan:
             if tuned:
                 max_items_pts, unit_points = tuned["max_items_pts"], tuned["unit_points"]
                 team = tuned.get("team", team)
+        wf, wc = window_range if window_range is not None else (0, 0)
+        self._reduce = None
+        if reduce is not None:
+            torch = _torch()
+
+            def _cb(buf, n, stream_ptr, ctx, _fn=reduce):
+                st = torch.cuda.ExternalStream(int(stream_ptr or 0)) if stream_ptr else \
+                    torch.cuda.default_stream()
+                _fn(_device_view(buf, n), st)
+            self._reduce = REDUCE_FN(_cb)
         desc = PlanDesc(N=N, D=D, L=win.shape[0],
                         windows=win.ctypes.data_as(C.POINTER(C.c_int32)), sigma=float(sigma),
                         M=M, n_os=n_os, m=m, precision=precision,
                         torus_fill=float(torus_fill), max_items_pts=max_items_pts,
                         nfft_eps=float(nfft_eps), unit_points=unit_points,
-                        team=(C.c_int * 3)(*(team or (0, 0, 0))))
+                        team=(C.c_int * 3)(*(team or (0, 0, 0))), window_first=int(wf),
+                        window_count=int(wc),
+                        reduce=self._reduce if self._reduce is not None else REDUCE_FN(),
+                        reduce_ctx=None)
         h = C.c_void_p()
         _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
                                    _stream_ptr(stream)))
         self._h = h
         self.N = N
         self.L = win.shape[0]
-        if autotune and not tuned:
+        if autotune and not tuned and window_range is None:
             from . import autotune as _at
             hit = None
             if nfft_eps > 0.0:
@@ -315,10 +348,6 @@ class Plan:
 
     def set_team(self, arith: int, shape: int):
         _check(load().nlh_plan_set_team(self._h, int(arith), int(shape)))
-
-    def set_interp(self, kind: int):
-        """Interpolation kernel: INTERP_POINTS (default) or INTERP_TEAMS."""
-        _check(load().nlh_plan_set_interp(self._h, int(kind)))
 
     def degrees(self, out=None, stream=None):
         """d = Gamma_full 1 in pixel order (nlh_plan_get_degrees)."""

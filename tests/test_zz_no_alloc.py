@@ -52,6 +52,26 @@ def test_noalloc_residual_matches_solver_on_two_calls():
     assert seen[0] != seen[1]
 
 
+def test_noalloc_many_blocks_matches_solver_on_two_calls():
+    """512 x 512 pixels: 64 blocks of 4096 elements, so the finishing
+    reduction sums partials of many slots of the library's array."""
+    img = image(512)
+    P = make_plan(img, precision=3)
+    prev = None
+    for alpha in (0.5, 2.0):
+        b = cuda(alpha * img.ravel())
+        res_solve = P.solve(alpha, b, tol=1e-6)
+        q = P.matvec(res_solve.u, op=2, precision=nlh.NLH_FP64, alpha=alpha)
+        nr, nb = _norms(b, q)
+        assert nr / nb == pytest.approx(res_solve.info["rel_res_true"], rel=1e-6)
+        hb, hq = host(b), host(q)
+        assert nr == pytest.approx(float(np.linalg.norm(hb - hq)), rel=1e-12)
+        assert nb == pytest.approx(float(np.linalg.norm(hb)), rel=1e-13)
+        assert prev is None or nb != prev
+        prev = nb
+    P.close()
+
+
 def test_noalloc_rejects_sizes_beyond_the_array():
     lib = nlh.load()
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
