@@ -2,24 +2,33 @@
 """Benchmark of the NFFT nonlocal-denoising hot path (one JSON line).
 
 A step is one pass of the whole path over one synthetic image: patch
-features, the plan (torus map, sort by cell, weights, tables, degrees), and
-a deflated Jacobi-PCG solve of (alpha I + L) u = alpha f to relative
-residual 1e-6 in the mixed form (FP32-NFFT inner solves, FP64 refinement
-residuals).  The metric is NFFT matvec throughput in Gpts/s: point-windows
-(N * L per matvec) pushed through the NFFT per second, over the whole step;
-the seconds-to-solve of the FP64 and mixed forms are reported beside it.
+features, the plan (torus map, sort by cell with the points' cell offsets,
+multiplier tables, degrees), and a deflated Jacobi-PCG solve of
+(alpha I + L) u = alpha f to relative residual 1e-6 in the mixed form
+(FP32-NFFT inner solves, FP64-accurate refinement residuals).  The default
+workload is the 2048 x 2048 image with 5x5 patches (9 windows, M = 64,
+n_os = 128, m = 6) at sigma = 0.2; sigma = 0.1 and 0.4 are solved beside it.
+The metric is NFFT matvec throughput in Gpts/s: point-windows (N * L per
+matvec) pushed through the NFFT per second, over the whole step; the
+seconds-to-solve of the mixed and the FP64-accurate forms are reported
+beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs N independent replicas (one per rank, launched by torchrun): the
-path has no exchange step, so there is no data collective; the ranks only
-meet at the timing barriers and the max-over-ranks of the step time.
+N > 1 (launched by torchrun): --shard windows (default) gives every rank a
+contiguous range of the windows (Sec. 3: the ANOVA kernel is a mean of
+independent per-window Gauss transforms); each matvec sums the ranks'
+shares of Gamma_full x with one NCCL all-reduce and the Krylov scalars are
+computed redundantly ("scaling": "strong").  --shard replicas runs N
+independent replicas ("scaling": "weak").
 --impl reference times the CPU FP64 oracle (direct O(N^2) sums) on the host
 cores on a bounded row sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -38,28 +47,37 @@ from paper_2407_06834_gb300.inputs import WORKLOADS  # noqa: E402
 
 METRIC = "NFFT kernel matvec Gpts/s (whole features+plan+solve step, mixed form)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+CSRC = os.path.join(ROOT, "paper_2407_06834_gb300", "csrc")
 # Non-tensor ALU peaks derived from unit counts and the 2070 MHz max clock:
 # FP32: 152 SMs x 128 FMA lanes x 2 flop; FP64: GB300 nominal 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
-# FP32 FLOPs of one double-float stencil multiply-add: TwoProduct by FMA with
-# the two cross terms (1 mul + 3 FMA = 7 FLOP) and TwoSum into the high word
-# with the low word accumulated (8 add/sub) -- 12 instructions, 15 FLOP.
-DF32_FLOP_PER_UPDATE = 15
-# DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/k_nfft_fp32_df32_img512.md (512 x 512 workload); None elsewhere.
-NCU_TRAFFIC_IMG512 = {"spread32": 80.39e6, "interp32": 81.26e6,
-                      "spread_df32": 160.22e6, "interp_df32": 159.31e6}
+# DRAM bytes (read + write) per launch of the NFFT kernels, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 2048 x 2048
+# workload, keyed by a hash of the kernel sources at capture time: when the
+# sources change, the figures no longer describe the kernels and the bench
+# reports traffic null.
+NCU_TRAFFIC = {"sources_sha16": None, "workload": "img2048", "bytes_per_launch": {}}
 
 
-def measured_hbm_gbs():
-    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the
-    profiling fallback of 6.8 TB/s."""
+def kernel_sources_sha16() -> str:
+    """Hash of the sources the NFFT kernels are compiled from."""
+    h = hashlib.sha256()
+    for name in ("nfft.cu", "window.cuh", "common.cuh", "df32.cuh"):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    """The measured copy bandwidth and bf16 rate of the GB300s
+    (MEASURED_PEAKS.json), else the profiling fallback (6.8 TB/s)."""
     try:
         with open(PEAKS_FILE) as f:
-            return float(json.load(f)["hbm_gbs"])
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
     except (OSError, ValueError, KeyError):
-        return 6800.0
+        return 6800.0, "fallback 6.8 TB/s (no measured peaks file)"
 
 
 def parse():
@@ -68,10 +86,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="img512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="img2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--shard", choices=["windows", "replicas"], default="windows",
+                    help="N > 1: windows over ranks (one all-reduce per matvec) or replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle row sample (0 = auto)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form leg")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the side legs (512^2 line, learned, MIS, sweep)")
     ap.add_argument("--learned-triples", type=int, default=512,
                     help="training triples at 256x256 for the learned leg")
     ap.add_argument("--learned-steps", type=int, default=1000, help="Adam steps (batch 16)")
@@ -79,9 +101,10 @@ def parse():
     ap.add_argument("--bilevel", action="store_true",
                     help="learn alpha by the bilevel problem on 8 pairs of 256x256 images")
     ap.add_argument("--sweep", action="store_true",
-                    help="batched bilevel sweep: 64 (sigma, alpha) solves on 8 uneven images")
+                    help="batched bilevel sweep only: 64 (sigma, alpha) solves on 8 uneven images")
     ap.add_argument("--matvec-case", action="store_true",
-                    help="profiling case: one plan, then 2 matvecs per NFFT precision; no JSON")
+                    help="profiling case: one plan of --workload, then 2 matvecs per NFFT "
+                         "arithmetic; no JSON")
     ap.add_argument("--net-case", action="store_true",
                     help="profiling case: 2 x (forward + loss/gradient) of the network on 16 "
                          "images of 256x256; no JSON")
@@ -96,6 +119,14 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def describe(wl):
+    p = 2 * wl.radius + 1
+    return ("%s: %dx%d image (N=%d), %dx%d %s patches -> L=%d windows of 3 dims, sigma=%g, "
+            "alpha=%g, M=%d, n_os=%d, m=%d, tol=%g"
+            % (wl.name, wl.n1, wl.n2, wl.N, p, p, wl.pad, wl.L, wl.sigma, wl.alpha, wl.M,
+               wl.n_os, wl.m, wl.tol))
 
 
 # ------------------------------------------------------------------ clocks
@@ -158,7 +189,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle baseline
 def oracle_rows_baseline(wl, rows: int, seed: int = 99):
-    """Direct O(N^2) oracle sums on a row sample; Gpts/s = rows * L / t."""
+    """Direct O(N^2) oracle sums on a row sample; Gpts/s = rows * L / t.  The
+    full-N direct matvec time is extrapolated from the sample (N / rows x t)."""
     from oracle import oracle as orc
     img = wl.image()
     coords = orc.image_coords(img, wl.radius, wl.windows, wl.pad)
@@ -170,15 +202,17 @@ def oracle_rows_baseline(wl, rows: int, seed: int = 99):
     dt = time.perf_counter() - t0
     return {"value": rows * wl.L / dt / 1e9, "unit": "Gpts/s", "cores": orc.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": "%d random rows of the direct FP64 sum Gamma_full v on %s (N=%d, L=%d)"
+            "full_matvec_seconds_extrapolated": dt * wl.N / rows,
+            "sample": "%d random rows of the direct FP64 sum Gamma_full v on %s (N=%d, L=%d); "
+                      "full-N matvec time extrapolated (N / rows x sample time)"
                       % (rows, wl.name, wl.N, wl.L)}
 
 
 def auto_rows(wl, target_s=12.0):
     from oracle import oracle as orc
-    probe = oracle_rows_baseline(wl, 64)
-    per_row = probe["seconds"] / 64
-    return int(max(64, min(wl.N, target_s / max(per_row, 1e-9)))), orc.num_threads()
+    probe = oracle_rows_baseline(wl, 16)
+    per_row = probe["seconds"] / 16
+    return int(max(16, min(wl.N, target_s / max(per_row, 1e-9)))), orc.num_threads()
 
 
 # ------------------------------------------------------------------ reference arm
@@ -187,25 +221,22 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    rows = args.cpu_rows or max(64, auto_rows(wl, target_s=8.0)[0] // max(1, args.steps + args.warmup))
+    rows = args.cpu_rows or max(16, auto_rows(wl, target_s=8.0)[0] // max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_rows_baseline(wl, max(16, rows // 8))
-    times, vals = [], []
+        oracle_rows_baseline(wl, max(4, rows // 8))
+    times = []
     for k in range(args.steps):
         b = oracle_rows_baseline(wl, rows, seed=100 + k)
         times.append(b["seconds"])
-        vals.append(b["value"])
     total = sum(times)
     value = rows * wl.L * args.steps / total / 1e9
     cpu = {"value": value, "unit": "Gpts/s", "cores": b["cores"], "kind": "oracle",
-           "sample": b["sample"] + " per step"}
+           "sample": b["sample"] + "; per step"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%s: %dx%d synthetic image, 3x3 reflect patches, L=%d, "
-                                   "sigma=%g" % (wl.name, wl.n1, wl.n2, wl.L, wl.sigma),
-                       "sample_rows": rows},
+            "config": {"workload": describe(wl), "sample_rows": rows},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -213,24 +244,120 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def combine_ranks(total_ms: float, pts: float, device) -> float:
-    """Replicas: whole-job Gpts/s = the point-windows all ranks processed
-    divided by the slowest rank's timed region (max over ranks)."""
+def combine_ranks(total_ms: float, pts: float, device, sum_work: bool = True) -> float:
+    """Whole-job Gpts/s: the point-windows all ranks processed (summed over
+    ranks for replicas; the one solve's for window sharding) divided by the
+    slowest rank's timed region (max over ranks)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([total_ms], dtype=torch.float64, device=device)
     p = torch.tensor([pts], dtype=torch.float64, device=device)
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        if sum_work:
+            dist.all_reduce(p, op=dist.ReduceOp.SUM)
     return float(p.item()) / (float(t.item()) * 1e-3) / 1e9
+
+
+KERNEL_CLASSES = ["spread64", "spread32", "conv64", "conv32", "interp64", "interp32", "epilogue",
+                  "krylov", "plan", "spread_df32", "interp_df32"]
+
+
+def read_profile(lib):
+    import ctypes as C
+    prof = {}
+    for c, nm in enumerate(KERNEL_CLASSES):
+        cl, cm = C.c_int64(0), C.c_double(0)
+        lib.nlh_profile_read(c, C.byref(cl), C.byref(cm))
+        if cl.value:
+            prof[nm] = {"launches": cl.value, "ms": cm.value}
+    lib.nlh_profile_reset()
+    return prof
+
+
+def roofline(prof, wl):
+    """The dominant NFFT kernel class of the timed region against its
+    rooflines.  Method work per point-window and direction: (2m)^3 stencil
+    multiply-adds (2m window points per dim), 2 FLOP each, in the kernel's
+    arithmetic (double-float and FP32 kernels run on the FP32 pipes; their
+    peak is the FP32 one).  Algorithmic bytes per launch: half of the
+    per-matvec N * 20 + N * L * 8 (image or coordinates, input, output,
+    permutation)."""
+    nfft = {k: v for k, v in prof.items() if k.startswith(("spread", "interp"))}
+    if not nfft:
+        return None
+    dom = max(nfft, key=lambda k: nfft[k]["ms"])
+    avg_s = nfft[dom]["ms"] / nfft[dom]["launches"] * 1e-3
+    W2 = 2 * wl.m
+    flops = 2.0 * float(wl.N * wl.L) * W2 ** 3
+    ach = flops / avg_s / 1e12
+    if dom.endswith("64"):
+        peak, src = FP64_PEAK_TFLOPS, "GB300 nominal FP64 1.25 TFLOP/s"
+    else:
+        peak = FP32_PEAK_TFLOPS
+        src = ("derived FP32: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz" +
+               ("; the kernel computes FP64-accurate double-float values on the FP32 pipes "
+                "(~6 packed FP32 instructions per stencil update), counted here as 2 FLOP per "
+                "update" if dom.endswith("df32") else ""))
+    hbm_peak, hbm_src = measured_peaks()
+    alg_bytes = 0.5 * (wl.N * 20.0 + wl.N * wl.L * 8.0)
+    # what these kernels read given the stored per-point data: permutation and
+    # cell offsets per point-window, the input or output per pixel, the grid
+    parts = 2 if dom.endswith(("64", "df32")) else 1
+    gbytes = 8 if dom.endswith(("64", "df32")) else 4
+    data_bytes = (wl.N * wl.L * (4.0 + 12.0 * parts) + wl.N * 8.0 +
+                  wl.L * wl.n_os ** 3 * float(gbytes))
+    traffic, tnote = None, None
+    sha = kernel_sources_sha16()
+    if NCU_TRAFFIC.get("sources_sha16") == sha and NCU_TRAFFIC.get("workload") == wl.name:
+        traffic = NCU_TRAFFIC["bytes_per_launch"].get(dom)
+        tnote = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, same kernel sources"
+    else:
+        tnote = ("no ncu capture of the current kernel sources for this workload "
+                 "(sources %s)" % sha)
+    return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": traffic, "traffic_note": tnote,
+            "mean_launch_ms": avg_s * 1e3, "launches": nfft[dom]["launches"],
+            "work": "2 x (2m)^3 FLOP per point-window, N L = %d point-windows per launch"
+                    % (wl.N * wl.L),
+            "peak_source": src,
+            "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / avg_s / 1e9,
+                    "peak_gbs": hbm_peak, "frac": alg_bytes / avg_s / 1e9 / hbm_peak,
+                    "kernel_data_bytes": data_bytes,
+                    "kernel_data_gbs": data_bytes / avg_s / 1e9,
+                    "peak_source": hbm_src}}
+
+
+def time_steps(step, args, dev, world, lib, stream, flush, steps, warmup, barrier):
+    import torch
+    infos = []
+    for _ in range(warmup):
+        infos.append(step())
+    torch.cuda.synchronize()
+    lib.nlh_profile_reset()
+    launches0 = lib.nlh_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    barrier()
+    lib.nlh_profile_enable(1)
+    step_infos = []
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step_infos.append(step())
+        ev[k][1].record(stream)
+    lib.nlh_profile_enable(0)
+    barrier()
+    launches = lib.nlh_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    return step_infos, step_ms, launches
 
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2407_06834_gb300 import nlh
+    from paper_2407_06834_gb300 import nlh, shard
 
     rank, local_rank, world = dist_env()
     if world > 1:
@@ -245,100 +372,42 @@ def run_ours(args):
     N, L = wl.N, wl.L
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    sharded = world > 1 and args.shard == "windows"
+    wrange = shard.window_range(L, world, rank) if sharded else None
 
-    def step(image, u):
-        P = nlh.Plan.from_image(image, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                                n_os=wl.n_os, m=wl.m, precision=6, autotune=True)
+    def make_plan(image, sigma, precision=6, autotune=True):
+        kw = {}
+        if sharded:
+            kw = {"window_range": wrange, "reduce": shard.allreduce_sum}
+            autotune = False
+        return nlh.Plan.from_image(image, wl.radius, wl.windows, sigma, pad=wl.pad, M=wl.M,
+                                   n_os=wl.n_os, m=wl.m, precision=precision,
+                                   autotune=autotune, **kw)
+
+    def step_on(image, u):
+        P = make_plan(image, wl.sigma)
         b = image.reshape(-1) * wl.alpha
         res = P.solve(wl.alpha, b, tol=wl.tol, arith=nlh.SOLVE_MIXED, inner_tol=1e-3, u=u)
         P.close()
-        return res
-
-    u = torch.empty(N, dtype=torch.float64, device=dev)
-    infos = []
-    for _ in range(args.warmup):
-        infos.append(step(img, u).info)
-    torch.cuda.synchronize()
+        return res.info
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region (device-resident inputs)
-    lib.nlh_profile_reset()
-    launches0 = lib.nlh_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    u = torch.empty(N, dtype=torch.float64, device=dev)
     with ClockSampler(local_rank) as clk:
-        barrier()
-        lib.nlh_profile_enable(1)
-        step_infos = []
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step_infos.append(step(img, u).info)
-            ev[k][1].record(stream)
-        lib.nlh_profile_enable(0)
-        barrier()
-    launches = lib.nlh_kernel_launches() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+        step_infos, step_ms, launches = time_steps(lambda: step_on(img, u), args, dev, world,
+                                                   lib, stream, flush, args.steps, args.warmup,
+                                                   barrier)
+    prof = read_profile(lib)
     total_ms = sum(step_ms)
-    # 2 degree matvecs per plan (double-float and FP32) + the solve's matvecs
+    # degree matvecs of the plan (FP32 and double-float) + the solve's matvecs
     mv = [i["matvecs_fp64"] + i["matvecs_fp32"] + 2 for i in step_infos]
     pts = float(N * L * sum(mv))
-    value = combine_ranks(total_ms, pts, dev)
-
-    # per-kernel-class device time inside the timed region
-    prof = {}
-    names = ["spread64", "spread32", "conv64", "conv32", "interp64", "interp32", "epilogue",
-             "krylov", "plan", "spread_df32", "interp_df32"]
-    import ctypes as C
-    for c, nm in enumerate(names):
-        cl, cm = C.c_int64(0), C.c_double(0)
-        lib.nlh_profile_read(c, C.byref(cl), C.byref(cm))
-        if cl.value:
-            prof[nm] = {"launches": cl.value, "ms": cm.value}
-    lib.nlh_profile_reset()
-    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
-    W2 = 2 * wl.m
-    updates = float(N * L * W2 ** 3)          # (2m)^3 stencil updates per point-window
-    roof = None
-    if dom and dom.startswith(("spread", "interp")):
-        avg_s = prof[dom]["ms"] / prof[dom]["launches"] * 1e-3
-        traffic = NCU_TRAFFIC_IMG512.get(dom) if wl.name == "img512" else None
-        if dom.endswith("df32"):
-            ach = DF32_FLOP_PER_UPDATE * updates / avg_s / 1e12
-            peak = FP32_PEAK_TFLOPS
-            src = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; achieved = 15 FP32 FLOP "
-                   "per double-float stencil update (TwoProduct + TwoSum) x (2m)^3 N L / launch "
-                   "time; FP64-accurate rate %.2f TFLOP/s vs FP64 nominal 1.25"
-                   % (2.0 * updates / avg_s / 1e12))
-        elif dom.endswith("64"):
-            ach, peak = 2.0 * updates / avg_s / 1e12, FP64_PEAK_TFLOPS
-            src = "GB300 nominal FP64 1.25 TFLOP/s"
-        else:
-            ach, peak = 2.0 * updates / avg_s / 1e12, FP32_PEAK_TFLOPS
-            src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-        # the same launch against the HBM roofline: algorithmic bytes per
-        # point-window = one weight record + one permutation entry + one FP64
-        # value (interpolation output / spreading input of the FP64-side
-        # vectors); 108 B FP32, 204 B double-float at m = 4, as ncu measures
-        rec_bytes = 3 * W2 * (8 if dom.endswith(("64", "df32")) else 4)
-        alg_bytes = float(N * L) * (((rec_bytes + 15) // 16) * 16 + 4 + 8)
-        hbm_peak = measured_hbm_gbs()
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                "traffic_note": "ncu DRAM read+write bytes per launch, 512x512 capture"
-                if traffic else None,
-                "mean_launch_ms": avg_s * 1e3, "peak_source": src,
-                "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / avg_s / 1e9,
-                        "peak_gbs": hbm_peak,
-                        "frac": (alg_bytes / avg_s / 1e9 / hbm_peak) if hbm_peak else None,
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
-    elif dom:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": None, "unit": "GB/s",
-                "frac": None, "traffic": None}
+    value = combine_ranks(total_ms, pts, dev, sum_work=not sharded)
+    roof = roofline(prof, wl) if not sharded else None
 
     # ---- end to end through the public API with host buffers
     img_h = torch.empty((wl.n1, wl.n2), dtype=torch.float64, pin_memory=True)
@@ -352,7 +421,7 @@ def run_ours(args):
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         img_d.copy_(img_h, non_blocking=True)
-        info = step(img_d, u).info
+        info = step_on(img_d, u)
         u_h.copy_(u, non_blocking=True)
         b_.record(stream)
         torch.cuda.synchronize()
@@ -360,42 +429,52 @@ def run_ours(args):
         mv_e = info["matvecs_fp64"] + info["matvecs_fp32"] + 2
     e2e_val = N * L * mv_e / (statistics.mean(e2e_ms) * 1e-3) / 1e9
 
-    # ---- seconds to 1e-6, FP64 form vs mixed form (plan prebuilt)
-    P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                            n_os=wl.n_os, m=wl.m, precision=7)
-    bvec = img.reshape(-1) * wl.alpha
+    # ---- seconds to 1e-6 per sigma of the workload (plan prebuilt)
     solve_s = {}
+    for sg in (wl.sigmas or [wl.sigma]):
+        P = make_plan(img, sg)
+        bvec = img.reshape(-1) * wl.alpha
+        row = {}
+        for nm, ar in (("mixed", nlh.SOLVE_MIXED), ("df32", nlh.SOLVE_DF32)):
+            P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
+            r = P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3)
+            row[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
+                       "outer": r.info["outer"], "rel_res_fp64": r.info["rel_res_true"]}
+        P.close()
+        solve_s["sigma=%g" % sg] = row
+    # plan creation alone
     t0 = time.perf_counter()
-    for _ in range(3):
-        Q = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                                n_os=wl.n_os, m=wl.m, precision=6)
+    for _ in range(2):
+        Q = make_plan(img, wl.sigma)
         Q.close()
     torch.cuda.synchronize()
-    solve_s["plan_seconds"] = (time.perf_counter() - t0) / 3
-    for nm, ar, pc in (("fp64", nlh.SOLVE_FP64, 0), ("df32", nlh.SOLVE_DF32, 0),
-                       ("mixed", nlh.SOLVE_MIXED, 0), ("mixed_pb", nlh.SOLVE_MIXED, 1)):
-        P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3, precond=pc)
-        r = P.solve(wl.alpha, bvec, tol=wl.tol, arith=ar, inner_tol=1e-3, precond=pc)
-        solve_s[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
-                       "rel_res_fp64": r.info["rel_res_true"]}
+    solve_s["plan_seconds"] = (time.perf_counter() - t0) / 2
     # kernel-only matvec throughput
+    P = make_plan(img, wl.sigma)
     x = torch.randn(N, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     mv_gpts = {}
-    for nm, prec in (("fp64", nlh.NLH_FP64), ("df32", nlh.NLH_DF32), ("fp32", nlh.NLH_FP32)):
+    for nm, prec in (("df32", nlh.NLH_DF32), ("fp32", nlh.NLH_FP32)):
         for _ in range(3):
             P.matvec(x, op=2, precision=prec, alpha=wl.alpha, out=y)
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(10):
+        for _ in range(5):
             P.matvec(x, op=2, precision=prec, alpha=wl.alpha, out=y)
         b_.record(stream)
         torch.cuda.synchronize()
-        mv_gpts[nm] = N * L / (a.elapsed_time(b_) / 10 * 1e-3) / 1e9
+        mv_gpts[nm] = {"gpts": N * L / (a.elapsed_time(b_) / 5 * 1e-3) / 1e9,
+                       "ms": a.elapsed_time(b_) / 5}
     pinfo = P.info()
     P.close()
-    learned_out = None if args.no_learned or world > 1 else learned_leg(args, dev)
-    mis_out = None if world > 1 or rank != 0 else mis_leg(dev)
+
+    side = {}
+    if not args.no_side and world == 1:
+        side["img512"] = small_line(args, dev, lib, flush)
+        side["sweep"] = sweep_leg(args)
+        if not args.no_learned:
+            side["learned"] = learned_leg(args, dev)
+        side["mis_windows"] = mis_leg(dev)
 
     if rank != 0:
         if world > 1:
@@ -410,19 +489,18 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f32 + df32 (FP32 NFFT inner solves; double-float NFFT for degrees and refinement residuals; FP64 Krylov vectors and dots)",
         "data": "synthetic (seeded piecewise-constant image + N(0,0.1^2) noise)",
-        "config": {"workload": "%s: %dx%d image (N=%d), %dx%d %s patches -> L=%d windows "
-                               "of 3 dims, sigma=%g, alpha=%g, M=%d, n_os=%d, m=%d, "
-                               "tol=%g" % (wl.name, wl.n1, wl.n2, N, 2 * wl.radius + 1,
-                                            2 * wl.radius + 1, wl.pad, L, wl.sigma, wl.alpha,
-                                            wl.M, wl.n_os, wl.m, wl.tol),
-                   "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "torus_fill": pinfo["torus_fill"], "work_items": pinfo["n_items"]},
+        "config": {"workload": describe(wl),
+                   "l2": "flushed between steps (256 MB write); the plan's data (~1 GB) exceeds L2",
+                   "parallelism": ("windows %s per rank, one NCCL all-reduce per matvec" % (wrange,)
+                                   if sharded else ("replicas" if world > 1 else "single GPU")),
+                   "torus_fill": pinfo["torus_fill"], "work_items": pinfo["n_items"],
+                   "plan_device_bytes": pinfo["device_bytes"]},
         "solve_seconds": solve_s,
-        "matvec_gpts_kernel_only": mv_gpts,
+        "matvec_kernel_only": mv_gpts,
         "iters_per_step": statistics.mean(i["iters"] for i in step_infos),
         "matvecs_per_step": statistics.mean(mv),
         "e2e": {"value": e2e_val, "unit": "Gpts/s", "h2d_bytes_per_step": N * 8,
@@ -431,14 +509,54 @@ def run_ours(args):
         "clocks": clk.summary(),
         "roofline": roof,
         "kernel_ms": prof,
-        "learned": learned_out,
-        "mis_windows": mis_out,
         "cpu_baseline": cpu,
     }
+    line.update(side)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def small_line(args, dev, lib, flush):
+    """The same step on the 512 x 512 workload (3x3 patches, L = 3, M = 32,
+    n_os = 64, m = 4): Gpts/s over the step, the roofline of its dominant
+    NFFT kernel, and FP64 / double-float / mixed solves to 1e-6."""
+    import torch
+
+    from paper_2407_06834_gb300 import nlh
+    wl = WORKLOADS["img512"]
+    img = torch.as_tensor(wl.image(), device=dev)
+    stream = torch.cuda.current_stream()
+    u = torch.empty(wl.N, dtype=torch.float64, device=dev)
+
+    def step():
+        P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                                n_os=wl.n_os, m=wl.m, precision=6, autotune=True)
+        r = P.solve(wl.alpha, img.reshape(-1) * wl.alpha, tol=wl.tol, arith=nlh.SOLVE_MIXED,
+                    inner_tol=1e-3, u=u)
+        P.close()
+        return r.info
+
+    infos, ms, launches = time_steps(step, args, dev, 1, lib, stream, flush, 10, 3,
+                                     torch.cuda.synchronize)
+    prof = read_profile(lib)
+    mv = [i["matvecs_fp64"] + i["matvecs_fp32"] + 2 for i in infos]
+    out = {"workload": describe(wl), "value": wl.N * wl.L * sum(mv) / (sum(ms) * 1e-3) / 1e9,
+           "unit": "Gpts/s", "ms_per_step": sum(ms) / len(ms), "gpu_launches": int(launches),
+           "roofline": roofline(prof, wl), "kernel_ms": prof}
+    P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                            n_os=wl.n_os, m=wl.m, precision=7)
+    b = img.reshape(-1) * wl.alpha
+    sv = {}
+    for nm, ar in (("fp64", nlh.SOLVE_FP64), ("df32", nlh.SOLVE_DF32), ("mixed", nlh.SOLVE_MIXED)):
+        P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=1e-3)
+        r = P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=1e-3)
+        sv[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
+                  "rel_res_fp64": r.info["rel_res_true"]}
+    P.close()
+    out["solve_seconds"] = sv
+    return out
 
 
 def net_flops_per_image(net, H, W):
@@ -554,19 +672,18 @@ def mis_leg(dev):
 
 
 def matvec_case(args):
-    """Small profiling case: one 512x512 plan with all three arithmetics and
-    the autotuned launch shapes of the bench step (FP32: default; double-
-    float: 2 warps x 4 teams), then 2 matvecs per arithmetic."""
+    """Small profiling case: one plan of --workload with the FP32 and
+    double-float arithmetics in the default tiling and launch shapes, then
+    2 matvecs per arithmetic."""
     import torch
 
     from paper_2407_06834_gb300 import nlh
     wl = WORKLOADS[args.workload]
     img = torch.as_tensor(wl.image(), device="cuda")
     P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                            n_os=wl.n_os, m=wl.m, precision=7, max_items_pts=128,
-                            unit_points=512, team=(0, 0, 2))
+                            n_os=wl.n_os, m=wl.m, precision=6)
     x = torch.randn(wl.N, dtype=torch.float64, device="cuda")
-    for prec in (nlh.NLH_FP64, nlh.NLH_FP32, nlh.NLH_DF32):
+    for prec in (nlh.NLH_FP32, nlh.NLH_DF32):
         for _ in range(2):
             P.matvec(x, op=2, precision=prec, alpha=wl.alpha)
     torch.cuda.synchronize()
@@ -607,7 +724,7 @@ def mis_case(args):
     torch.cuda.synchronize()
 
 
-def run_sweep(args):
+def sweep_leg(args):
     """64 solves over a log grid of sigma in [0.05, 1] x alpha in [0.01, 10] on 8
     synthetic images of uneven sizes (pair (i, j) -> image (i + j) mod 8), each
     with its own plan (NFFT parameters chosen for a 1e-7 per-dim error).
@@ -651,7 +768,7 @@ def run_sweep(args):
     t_batch = (time.perf_counter() - t0) / reps
     worst = max(i["rel_res_true"] for i in infos)
     px = sum(P.N for P in plans)
-    print(json.dumps({
+    out = {
         "metric": "batched bilevel sweep, solves/s (64 mixed-precision solves to 1e-6)",
         "value": len(plans) / t_batch, "unit": "solves/s", "higher_is_better": True,
         "loop_of_single_solves": len(plans) / t_loop, "speedup_vs_loop": t_loop / t_batch,
@@ -661,7 +778,14 @@ def run_sweep(args):
         "nfft": [{"M": P.info()["M"], "n_os": P.info()["n_os"], "m": P.info()["m"],
                   "fill": P.info()["torus_fill"]} for P in plans[:8]],
         "config": {"workload": "8 images %s, 64 (sigma, alpha) pairs" % SWEEP_SIZES,
-                   "reps": reps}}), flush=True)
+                   "reps": reps}}
+    for P in plans:
+        P.close()
+    return out
+
+
+def run_sweep(args):
+    print(json.dumps(sweep_leg(args)), flush=True)
 
 
 def run_bilevel(args):

@@ -107,7 +107,10 @@ typedef struct {
                                ranges add up to the plan of all windows      */
     nlh_reduce_fn reduce;   /* range plans: NULL, or the sum over ranks.
                                With it every op of nlh_matvec, the degrees
-                               and the solves are those of all L windows;
+                               and the solves are those of all L windows
+                               (their Krylov loops are then host-driven,
+                               checking every 4 iterations, since the
+                               callback runs when a matvec is issued);
                                without it only op 0 (the range's share of
                                Gamma_full x) is defined                      */
     void *reduce_ctx;       /* passed to reduce                              */

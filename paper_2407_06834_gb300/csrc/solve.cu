@@ -438,6 +438,10 @@ static void krylov_launch(Plan &P, int prec, double alpha, const double *rhs, co
                           const double *scale, int check_every, cudaStream_t s) {
     int deflate, precond;
     method_flags(method, deflate, precond);
+    // a plan whose matvecs call a reduce callback (a window range summed over
+    // ranks) runs the host-driven loop: the callback enqueues its collective
+    // when the matvec is issued, which a captured graph would not repeat
+    if (P.reduce_fn && check_every <= 0) check_every = 4;
     SolveState init{};
     init.tol = tol;
     init.maxit = maxit;

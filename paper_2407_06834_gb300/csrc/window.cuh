@@ -15,8 +15,8 @@
 // reaches the kernels as a small by-value kernel parameter read at
 // compile-time offsets only, so every coefficient is a constant operand of
 // the multiply-adds; the FP64 and double-float sets are staged from a table
-// in the plan's device memory into shared memory.  Per point and dim this is m pairs of short
-// Horner chains instead of a stored weight record.
+// in the plan's device memory into shared memory.  Per point and dim this
+// is m pairs of short Horner chains instead of a stored weight record.
 #pragma once
 #include <cstdint>
 
