@@ -260,6 +260,16 @@ template <int W2> struct Line<float, W2> {
 #pragma unroll
         for (int a = 0; a < W2 / 2; ++a) v[a] = pk_make(row[2 * a], row[2 * a + 1]);
     }
+    // 2m consecutive cells from a 16-byte aligned row (2m a multiple of 4)
+    __device__ __forceinline__ void load_cells_v4(const float *row) {
+        static_assert(W2 % 4 == 0, "whole 16-byte groups");
+#pragma unroll
+        for (int a = 0; a < W2 / 4; ++a) {
+            const ulonglong2 q = reinterpret_cast<const ulonglong2 *>(row)[a];
+            v[2 * a] = q.x;
+            v[2 * a + 1] = q.y;
+        }
+    }
 };
 
 template <int W2> struct Line<df32, W2> {
@@ -270,11 +280,13 @@ template <int W2> struct Line<df32, W2> {
         for (int a = 0; a < W2 / 2; ++a) h[a] = l[a] = 0ull;
     }
     // src: 2m high parts followed by 2m low parts (8-byte aligned)
-    __device__ __forceinline__ void load(const float *src) {
+    __device__ __forceinline__ void load(const float *src) { load2(src, src + W2); }
+    // high and low parts from separate rows (8-byte aligned)
+    __device__ __forceinline__ void load2(const float *hi, const float *lo) {
 #pragma unroll
         for (int a = 0; a < W2 / 2; ++a) {
-            h[a] = reinterpret_cast<const unsigned long long *>(src)[a];
-            l[a] = reinterpret_cast<const unsigned long long *>(src + W2)[a];
+            h[a] = reinterpret_cast<const unsigned long long *>(hi)[a];
+            l[a] = reinterpret_cast<const unsigned long long *>(lo)[a];
         }
     }
     __device__ __forceinline__ void from(const df32 (&w)[W2]) {
@@ -316,24 +328,37 @@ template <int W2> struct Line<df32, W2> {
     }
 };
 
-// (y, z) stencil pairs owned by one thread: pair p = tid + NT k.  When the
-// team size is a multiple of 2m every pair of a thread has the same y offset.
-template <int W2, int NT, int PPT>
+// (y, z) stencil pairs owned by one thread: pair p = q + NTP k, where q is
+// the thread's index among the NTP threads that share its x segment.  When
+// NTP is a multiple of 2m every pair of a thread has the same y offset.
+template <int W2, int NTP, int PPT>
 struct Pairs {
     int b0, bb[PPT], cc[PPT];
     bool ok[PPT];
-    static constexpr bool kSameB = (NT % W2) == 0;
-    __device__ __forceinline__ void init(int tid) {
-        b0 = tid % W2;
+    static constexpr bool kSameB = (NTP % W2) == 0;
+    __device__ __forceinline__ void init(int q) {
+        b0 = q % W2;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            int p = tid + NT * k;
+            int p = q + NTP * k;
             ok[k] = p < W2 * W2;
             bb[k] = kSameB ? b0 : (ok[k] ? p % W2 : 0);
             cc[k] = ok[k] ? p / W2 : 0;
         }
     }
 };
+
+// One x segment (WS = 2m / SPLIT consecutive cells) of a point's weight
+// line, from its staged record.
+template <typename T, int W2, int WS>
+__device__ __forceinline__ void load_segment(Line<T, WS> &w, const typename Num<T>::R *line,
+                                             int seg) {
+    if constexpr (Num<T>::kParts == 2) {
+        w.load2(line + seg * WS, line + W2 + seg * WS);
+    } else {
+        w.load(line + seg * WS);
+    }
+}
 
 // The offset y = 2 f - 1 of a point inside its grid cell (per dim), stored
 // as a float and the float remainder; each arithmetic reads what it needs.
@@ -414,18 +439,25 @@ struct SpreadSmem {
 // of an item every thread reads one point (its pixel through the sort
 // permutation, the input value there, its cell offsets), evaluates the
 // point's 3 x 2m window weights and stages them; then each thread adds the
-// chunk's points into its PPT (y, z) stencil pairs, each a full x line of 2m
-// accumulators in registers (all points of an item share the stencil).  An
-// item's accumulators are then added into the shared tile, and the tile into
-// the global grid once (non-zero entries only).
-template <typename T, int W2, int NW, int TPB, int MINB = 1>
+// chunk's points into its PPT (y, z) stencil pairs, each an x segment of
+// 2m / SPLIT accumulators in registers (all points of an item share the
+// stencil).  An item's accumulators are then added into the shared tile,
+// and the tile into the global grid once (non-zero entries only).
+//
+// SPLIT = 2 halves the x lines: a team of NT threads then covers the
+// 2m x 2m x 2 (pair, segment) units, NT / 2 threads per segment, which for
+// 2m = 12 and NT = 96 is exactly 3 units per thread (full lines leave a
+// quarter of a 64-thread team idle in the third pass).
+template <typename T, int W2, int NW, int TPB, int MINB = 1, int SPLIT = 1>
 __global__ void __launch_bounds__(32 * NW * TPB, MINB)
 k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__restrict__ x,
          typename Num<T>::G *__restrict__ grid, const int *__restrict__ done) {
     using R = typename Num<T>::R;
     using G = typename Num<T>::G;
     using SM = SpreadSmem<T, W2, NW, TPB>;
-    constexpr int NT = SM::NT, PPT = (W2 * W2 + NT - 1) / NT, PWP = SM::PWP;
+    constexpr int NT = SM::NT, NTP = NT / SPLIT, WS = W2 / SPLIT;
+    constexpr int PPT = (W2 * W2 + NTP - 1) / NTP, PWP = SM::PWP;
+    static_assert(NT % SPLIT == 0 && WS % 2 == 0, "x segments of an even number of cells");
     constexpr int E = SM::E, E3 = SM::E3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
@@ -437,11 +469,13 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
     // the interpolation of the previous matvec has finished (stream order)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.unit_ctr[1] = 0;
     const int team = threadIdx.x / NT, tid = threadIdx.x % NT;
+    const int seg = SPLIT == 1 ? 0 : tid / NTP;
     R *rec = reinterpret_cast<R *>(smem_raw + SM::teams_off + team * SM::team_bytes);
     int *s_slot = reinterpret_cast<int *>(smem_raw + SM::slots_off) + team;
-    Pairs<W2, NT, PPT> pr;
-    pr.init(tid);
+    Pairs<W2, NTP, PPT> pr;
+    pr.init(tid % NTP);
     const int msk = a.n - 1, m = a.m;
+    const int64_t n_pts = (int64_t)a.L * a.N;
     while (true) {
         __syncthreads();  // previous unit fully flushed
         if (threadIdx.x == 0) s_ctl[1] = atomicAdd(&a.unit_ctr[0], 1);
@@ -457,7 +491,7 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
         for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = a.items[it0 + e];
         if (threadIdx.x == 0) s_ctl[0] = TPB;
         __syncthreads();
-        Line<T, W2> acc[PPT];
+        Line<T, WS> acc[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) acc[k].zero();
         ChunkCursor cur = make_cursor(s_items, team, nit);
@@ -465,7 +499,7 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
             const int cn = min(NT, cur.cnt - cur.c0);
             if (tid < cn) {  // this thread's point: value, weights -> record
                 const int64_t sp = (int64_t)cur.start + cur.c0 + tid;
-                bool ok = idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N, 2, sp, 0);
+                bool ok = idx_ok(sp >= 0 && sp < n_pts, 2, sp, 0);
                 const int pix = ok ? __ldg(a.perm + sp) : 0;
                 ok = ok && idx_ok(pix >= 0 && pix < a.N, 3, pix, sp);
                 const T v = ok ? from_double<T>(__ldg(x + pix)) : T(0);
@@ -485,9 +519,9 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
             if (!idx_ok(cn >= 0 && cn <= NT, 6, cn, NT)) break;
             for (int j = 0; j < cn; ++j) {
                 const R *wpp = rec + j * PWP;
-                Line<T, W2> wx;
-                wx.load(rec_line<T, W2>(wpp, 0));
-                if (Pairs<W2, NT, PPT>::kSameB) {
+                Line<T, WS> wx;
+                load_segment<T, W2, WS>(wx, rec_line<T, W2>(wpp, 0), seg);
+                if (Pairs<W2, NTP, PPT>::kSameB) {
                     const T vb = rec_val<T, W2>(wpp, 1, pr.b0);  // v wy[b]
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
@@ -507,10 +541,11 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (pr.ok[k]) {
-                        const int ro = ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0;
+                        const int ro =
+                            ((lz0 + pr.cc[k]) * E + (ly0 + pr.bb[k])) * E + lx0 + seg * WS;
                         T *row = S + ro;
 #pragma unroll
-                        for (int q = 0; q < W2; ++q)
+                        for (int q = 0; q < WS; ++q)
                             if (idx_ok(ro + q >= 0 && ro + q < E3, 4, ro + q, E3)) atomicAdd(&row[q], acc[k].get(q));
                     }
                     acc[k].zero();
@@ -571,16 +606,40 @@ struct Epilogue {
 // may differ between calls); k_finish applies the epilogue.
 constexpr int kInterpThreads = 256;
 
+// Shared-memory layout of the interpolation tile.  FP32 with 2m a multiple
+// of 4 stages 4 copies of the tile region, copy c shifted left by c cells
+// (S_c[z][y][x] = S[z][y][x + c]) with rows padded to a multiple of 4
+// cells, so that the 2m cells of any row from any start x0 are 2m / 4
+// aligned 16-byte loads from copy x0 mod 4 (one shared load per 4
+// multiply-adds instead of one per multiply-add).  Other arithmetics keep
+// one unpadded copy.
+template <typename T, int W2>
+struct InterpTile {
+    static constexpr int E = kTile + W2 - 1;
+    static constexpr bool kVec = std::is_same<T, float>::value && W2 % 4 == 0;
+    static constexpr int NC = kVec ? 4 : 1;
+    static constexpr int EP = kVec ? ((kTile + W2 + 3) / 4) * 4 : E;  // row pitch
+    static constexpr int COPY = E * E * EP;                            // cells per copy
+    static constexpr size_t bytes = align16(sizeof(T) * NC * COPY);
+};
+// Threads of an interpolation CTA: 512 for the FP32 2m = 12 instance (its
+// 4-copy tile allows one CTA per SM), 256 otherwise.
+template <typename T, int W2>
+constexpr int interp_threads() {
+    return (std::is_same<T, float>::value && W2 == 12) ? 512 : kInterpThreads;
+}
+
 template <typename T, int W2, int NTH = kInterpThreads, int MINB = 1>
 __global__ void __launch_bounds__(NTH, MINB)
 k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
          const typename Num<T>::G *__restrict__ grid,
          const Epilogue ep, const int *__restrict__ done) {
     using G = typename Num<T>::G;
-    constexpr int E = kTile + W2 - 1, E3 = E * E * E;
+    using TL = InterpTile<T, W2>;
+    constexpr int E = TL::E, E3 = E * E * E, EP = TL::EP, NC = TL::NC, COPY = TL::COPY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
-    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + align16(sizeof(T) * E3));
+    int4 *s_items = reinterpret_cast<int4 *>(smem_raw + TL::bytes);
     int *s_ctl = reinterpret_cast<int *>(s_items + kUnitItems);
     float4 *s_coef = reinterpret_cast<float4 *>(s_ctl + 4);
     __shared__ double sh_red[33];
@@ -621,7 +680,16 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     const int e = base + u * blockDim.x;
-                    if (e < E3) S[e] = T(vals[u]);
+                    if (e < E3) {
+                        if constexpr (NC == 1) {
+                            S[e] = T(vals[u]);
+                        } else {
+                            const int ex = e % E, row = (e / E) * EP;
+#pragma unroll
+                            for (int c = 0; c < NC; ++c)
+                                if (ex >= c) S[c * COPY + row + ex - c] = T(vals[u]);
+                        }
+                    }
                 }
             }
         }
@@ -648,15 +716,23 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             T acc = T(0);
             // the z loop stays rolled (the unrolled y loop is the work; a
             // fully unrolled stencil makes the compile very long)
+            // the copy whose rows start 16-byte aligned at x = lx0 (one copy:
+            // the plain tile)
+            const int cx = NC == 1 ? 0 : (lx0 & 3);
+            const T *scopy = S + cx * COPY;
 #pragma unroll 1
             for (int z = 0; z < W2; ++z) {
                 t.zero();
-                const int so = ((lz0 + z) * E + ly0) * E + lx0;
-                if (!idx_ok(so >= 0 && so + (W2 - 1) * E + W2 - 1 < E3, 13, so, E3)) break;
-                const T *srow = S + so;
+                const int so = ((lz0 + z) * E + ly0) * EP + lx0 - cx;
+                if (!idx_ok(so >= 0 && so + (W2 - 1) * EP + W2 - 1 < COPY, 13, so, COPY)) break;
+                const T *srow = scopy + so;
 #pragma unroll
                 for (int y = 0; y < W2; ++y) {
-                    h.load_cells(srow + y * E);
+                    if constexpr (NC == 1) {
+                        h.load_cells(srow + y * EP);
+                    } else {
+                        h.load_cells_v4(srow + y * EP);
+                    }
                     t.axpy(wy[y], h);
                 }
                 // wz[z] by a select over the unrolled array (no local memory)
@@ -875,13 +951,13 @@ constexpr int spread_minb() {
     return (std::is_same<T, float>::value && W2 == 8 && NW == 1 && TPB == 4) ? 5 : 1;
 }
 
-template <typename T, int W2, int NW, int TPB>
+template <typename T, int W2, int NW, int TPB, int SPLIT = 1>
 static int spread_blocks() {
     static int blocks = 0;  // per template instance
     if (blocks == 0) {
         constexpr int NTH = 32 * NW * TPB;
         constexpr size_t smem = SpreadSmem<T, W2, NW, TPB>::bytes;
-        auto kern = k_spread<T, W2, NW, TPB, spread_minb<T, W2, NW, TPB>()>;
+        auto kern = k_spread<T, W2, NW, TPB, spread_minb<T, W2, NW, TPB>(), SPLIT>;
         NLH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
         NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem));
@@ -890,14 +966,14 @@ static int spread_blocks() {
     return blocks;
 }
 
-template <typename T, int W2, int NW, int TPB>
+template <typename T, int W2, int NW, int TPB, int SPLIT = 1>
 static void launch_spread_shape(Plan &P, const double *x, typename Num<T>::G *grid,
                                 const int *done, cudaStream_t s) {
     constexpr int NTH = 32 * NW * TPB;
     constexpr int MINB = spread_minb<T, W2, NW, TPB>();
     constexpr size_t smem = SpreadSmem<T, W2, NW, TPB>::bytes;
-    auto kern = k_spread<T, W2, NW, TPB, MINB>;
-    const int blocks = spread_blocks<T, W2, NW, TPB>();
+    auto kern = k_spread<T, W2, NW, TPB, MINB, SPLIT>;
+    const int blocks = spread_blocks<T, W2, NW, TPB, SPLIT>();
     ProfRange pr(spread_class<T>(), s);
     // grid bound: the unit count once known on the host, else its upper bound
     const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
@@ -907,11 +983,17 @@ static void launch_spread_shape(Plan &P, const double *x, typename Num<T>::G *gr
     NLH_CHECK_LAUNCH();
 }
 
-// Team shape (warps per team NW, teams per CTA TPB) of the spreading kernel:
-// fewer accumulator lines per thread (larger teams) against more independent
-// teams per SM.  Shape 0 is the default; shapes 1 and 2 are compiled for the
+// Team shape (warps per team NW, teams per CTA TPB, x segments SPLIT) of the
+// spreading kernel: fewer accumulators per thread (larger teams, split
+// lines) against more independent teams per SM and fewer shared loads per
+// multiply-add.  Shape 0 is the default; shapes 1 and 2 are compiled for the
 // stencil widths of the workloads (2m = 8, 12).  The autotuner picks one per
-// arithmetic (plan.team[]); other combinations run shape 0.
+// arithmetic (plan.team[]); other combinations run shape 0.  At 2m = 12
+// every arithmetic splits its lines by default: 3-warp teams with 3 half
+// lines per thread cover the 12 x 12 x 2 units without idle lanes (full
+// lines on 2-warp teams leave a quarter of the team idle in its third
+// pass); on the 2048 x 2048 workload this measured 11% faster for
+// double-float and 8% for FP32.
 template <typename T, int W2>
 static void launch_spread(Plan &P, const double *x, typename Num<T>::G *grid, const int *done,
                           cudaStream_t s) {
@@ -920,8 +1002,9 @@ static void launch_spread(Plan &P, const double *x, typename Num<T>::G *grid, co
         if (shape == 1) return launch_spread_shape<T, W2, 2, 2>(P, x, grid, done, s);
         if (shape == 2) return launch_spread_shape<T, W2, 2, 4>(P, x, grid, done, s);
     } else if constexpr (W2 == 12) {
-        if (shape == 1) return launch_spread_shape<T, W2, 4, 1>(P, x, grid, done, s);
-        if (shape == 2) return launch_spread_shape<T, W2, 2, 1>(P, x, grid, done, s);
+        if (shape == 1) return launch_spread_shape<T, W2, 3, 4, 2>(P, x, grid, done, s);
+        if (shape == 2) return launch_spread_shape<T, W2, 2, 2>(P, x, grid, done, s);
+        return launch_spread_shape<T, W2, 3, 2, 2>(P, x, grid, done, s);
     }
     constexpr int NW = W2 <= 8 ? 1 : 2, TPB = W2 <= 8 ? 4 : 2;
     launch_spread_shape<T, W2, NW, TPB>(P, x, grid, done, s);
@@ -933,13 +1016,12 @@ static void launch_spread(Plan &P, const double *x, typename Num<T>::G *grid, co
 template <typename T, int W2>
 constexpr int interp_minb() {
     return (std::is_same<T, df32>::value && W2 == 8) ? 3
-           : (W2 == 12 && !std::is_same<T, double>::value) ? 2
-                                                           : 1;
+           : (W2 == 12 && std::is_same<T, df32>::value) ? 2
+                                                        : 1;
 }
 template <typename T, int W2>
 constexpr size_t interp_smem() {
-    return align16(sizeof(T) * (kTile + W2 - 1) * (kTile + W2 - 1) * (kTile + W2 - 1)) +
-           sizeof(int4) * kUnitItems + 16 + kWinStageBytes;
+    return InterpTile<T, W2>::bytes + sizeof(int4) * kUnitItems + 16 + kWinStageBytes;
 }
 
 template <typename T, int W2>
@@ -947,10 +1029,11 @@ static int interp_blocks() {
     static int blocks = 0;
     if (blocks == 0) {
         constexpr size_t smem = interp_smem<T, W2>();
-        auto kern = k_interp<T, W2, kInterpThreads, interp_minb<T, W2>()>;
+        constexpr int NTH = interp_threads<T, W2>();
+        auto kern = k_interp<T, W2, NTH, interp_minb<T, W2>()>;
         NLH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
-        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kInterpThreads, smem));
+        NLH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem));
         blocks = std::min(sm_count() * std::max(1, b), kPqSlots);
     }
     return blocks;
@@ -961,7 +1044,8 @@ static void launch_interp(Plan &P, const typename Num<T>::G *grid, const Epilogu
                           const int *done, cudaStream_t s) {
     constexpr int MINB = interp_minb<T, W2>();
     constexpr size_t smem = interp_smem<T, W2>();
-    auto kern = k_interp<T, W2, kInterpThreads, MINB>;
+    constexpr int NTH = interp_threads<T, W2>();
+    auto kern = k_interp<T, W2, NTH, MINB>;
     const int blocks = interp_blocks<T, W2>();
     ProfRange pr(interp_class<T>(), s);
     const int64_t nu = P.n_units >= 0 ? P.n_units : P.units_cap;
@@ -969,7 +1053,7 @@ static void launch_interp(Plan &P, const typename Num<T>::G *grid, const Epilogu
         NLH_REQUIRE(false, "internal: plan without work units");
     }
     const unsigned g = (unsigned)std::min<int64_t>(blocks, nu);
-    kern<<<g, kInterpThreads, smem, s>>>(nfft_args<T>(P), win_poly<T>(P), grid, ep, done);
+    kern<<<g, NTH, smem, s>>>(nfft_args<T>(P), win_poly<T>(P), grid, ep, done);
     NLH_CHECK_LAUNCH();
 }
 
@@ -1004,8 +1088,8 @@ static void prepare_w() {
         spread_blocks<T, W2, 2, 2>();
         spread_blocks<T, W2, 2, 4>();
     } else if constexpr (W2 == 12) {
-        spread_blocks<T, W2, 4, 1>();
-        spread_blocks<T, W2, 2, 1>();
+        spread_blocks<T, W2, 3, 4, 2>();
+        spread_blocks<T, W2, 3, 2, 2>();
     }
     spread_blocks<T, W2, (W2 <= 8 ? 1 : 2), (W2 <= 8 ? 4 : 2)>();
     interp_blocks<T, W2>();

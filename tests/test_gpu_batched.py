@@ -58,6 +58,39 @@ def test_batched_equals_single(arith):
         assert rel(host(us[k]), host(single.u)) < 1e-9
 
 
+@pytest.mark.parametrize("arith", [nlh.SOLVE_MIXED, nlh.SOLVE_DF32])
+def test_batched_solutions_certified_by_oracle(arith):
+    """Batched solves on images of uneven sizes, each with its own plan at
+    tight NFFT parameters: every solution's residual under the oracle's
+    direct operator A = alpha I + diag(eta) - Gamma (Sec. 2.3,
+    Eq. discretized-state) is within 2e-6 of ||b||, and it agrees with the
+    oracle's deflated PCG (Sec. 4.3.2) within the bound that the
+    conditioning gives: A >= alpha I, so ||u - u_o|| <= (||r|| + ||r_o||) / alpha."""
+    shapes = [(16, 16), (24, 32), (40, 40)]
+    sig = [0.15, 0.2, 0.3]
+    alphas = [0.5, 0.1, 2.0]
+    imgs = [image(*sh, seed=60 + k) for k, sh in enumerate(shapes)]
+    plans = [make_plan(im, sigma=s, M=64, n_os=128, m=8, fill=0.5, precision=6)
+             for im, s in zip(imgs, sig)]
+    bs = [a * im.ravel() for im, a in zip(imgs, alphas)]
+    us, infos = nlh.solve_batched(plans, alphas, [cuda(b) for b in bs], tol=1e-6, arith=arith,
+                                  inner_tol=1e-3)
+    for k, (im, s, a, b) in enumerate(zip(imgs, sig, alphas, bs)):
+        assert infos[k]["status"] == 0 and infos[k]["rel_res_true"] <= 1e-6, infos[k]
+        coords = orc.image_coords(im, 1, raster_windows(1))
+        eta = orc.degrees(coords, s)
+        u = host(us[k])
+        r = b - orc.A_apply(coords, s, a, 1.0, u, eta)
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 2e-6, (k, np.linalg.norm(r) / np.linalg.norm(b))
+        o = orc.pcg_deflated(coords, s, a, 1.0, b, tol=1e-6, maxit=200)
+        assert o.status == 0
+        ro = b - orc.A_apply(coords, s, a, 1.0, o.u, eta)
+        bound = (np.linalg.norm(r) + np.linalg.norm(ro)) / a
+        assert np.linalg.norm(u - o.u) <= 1.01 * bound, (k, np.linalg.norm(u - o.u), bound)
+    for P in plans:
+        P.close()
+
+
 def test_batched_rejects_bad_arguments():
     img = image(16, 16, seed=4)
     P = _auto_plan(img, 0.2)
