@@ -187,10 +187,12 @@ nlh_status nlh_plan_autotune(nlh_plan plan, int precisions, int reps, int *best_
  *   op 2: y = (alpha I + L) x
  * precision: NLH_FP64, NLH_FP32 or NLH_DF32 (the NFFT stages; the output is
  * FP64).
- * A matvec is six kernel launches (spread, three convolution passes,
- * interpolation, and the epilogue over the pixels); the per-window
- * contributions of a pixel are summed with FP64 atomics, so results may
- * differ between calls in the last bits.
+ * A matvec is five kernel launches for n_os <= 128 (spread, the x and y
+ * convolution passes in one plane kernel, the z pass, interpolation, and
+ * the epilogue over the pixels; a one-window plan finishes the pixels
+ * inside the interpolation) and six for n_os = 256 (three separate
+ * convolution passes); the per-window contributions of a pixel are summed
+ * with FP64 atomics, so results may differ between calls in the last bits.
  * Errors: NLH_ERR_ARG (bad op, precision not built, NULL pointers, op 1 or
  * 2 on a window-range plan without a reduce callback).  The call does not
  * synchronise; the NFFT kernels validate the plan's work-unit, item and

@@ -772,61 +772,19 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
 }
 
 // ------------------------------------------------------------------ grid convolution
-// One CTA = 16 grid lines along `axis`, staged through shared memory so that
-// global loads and stores are contiguous rows.  Each warp takes two real
-// lines as one complex line of length n = 32 R (element e at lane e % 32,
-// register e / 32), runs a radix-2 decimation-in-frequency FFT (output in
-// bit-reversed order), multiplies by the bit-reversed multiplier table, and
-// runs the decimation-in-time inverse FFT (bit-reversed in, natural out).
-// Because the multiplier is real and even, the real and imaginary parts stay
-// the two independent convolved lines.  The first axis pass reads the spread
-// grid `src`, clears it for the next matvec and writes `dst`; the later
-// passes work in place on `dst`.
+// Circular convolution of one complex line of length n = 32 R held by a
+// warp (element e at lane e % 32, register e / 32) with the real, even
+// multiplier: a radix-2 decimation-in-frequency FFT (output in bit-reversed
+// order), the multiply by the bit-reversed multiplier table, and the
+// decimation-in-time inverse FFT (bit-reversed in, natural out).  Because
+// the multiplier is real and even, the real and imaginary parts stay two
+// independent convolved real lines.
 template <typename T, int R>
-__global__ void __launch_bounds__(256)
-k_conv(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ dst, int axis,
-       const T *__restrict__ tab, const typename Vec2<T>::type *__restrict__ tw,
-       int *__restrict__ ctr_reset, const int *__restrict__ done) {
-    using G = typename Num<T>::G;
+__device__ __forceinline__ void conv_line(typename Vec2<T>::type (&xv)[R], const T *__restrict__ tab,
+                                          const typename Vec2<T>::type *__restrict__ tw,
+                                          int lane) {
     using C = typename Vec2<T>::type;
-    constexpr int n = 32 * R, LPC = 16, PITCH = n + 1;
-    __shared__ T S[LPC * PITCH];
-    if (done && *done) return;
-    // the spreading of this matvec has finished (stream order)
-    if (ctr_reset && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ctr_reset = 0;
-    const bool clear = src != dst;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    G *gs = src + (int64_t)blockIdx.y * n * n * n;
-    G *gd = dst + (int64_t)blockIdx.y * n * n * n;
-    const int li0 = blockIdx.x * LPC;  // first line of the CTA
-    const int a0 = li0 % n, b0 = li0 / n;
-    // element (line j, position e) -> global offset
-    auto goff = [&](int j, int e) -> int64_t {
-        if (axis == 0) return ((int64_t)b0 * n + a0 + j) * n + e;          // lines (y, z)
-        if (axis == 1) return (int64_t)b0 * n * n + (int64_t)e * n + a0 + j;  // lines (x, z)
-        return (int64_t)e * n * n + (int64_t)b0 * n + a0 + j;                 // lines (x, y)
-    };
-    if (axis == 0) {
-        for (int q = tid; q < LPC * n; q += 256) {
-            int j = q / n, e = q % n;
-            const int64_t o = goff(j, e);
-            S[j * PITCH + e] = T(gs[o]);
-            if (clear) gs[o] = G(0);
-        }
-    } else {
-        for (int q = tid; q < LPC * n; q += 256) {
-            int j = q % LPC, e = q / LPC;
-            const int64_t o = goff(j, e);
-            S[j * PITCH + e] = T(gs[o]);
-            if (clear) gs[o] = G(0);
-        }
-    }
-    __syncthreads();
-
-    C xv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        xv[r] = {S[(2 * warp) * PITCH + 32 * r + lane], S[(2 * warp + 1) * PITCH + 32 * r + lane]};
+    constexpr int n = 32 * R;
     // forward DIF
 #pragma unroll
     for (int h = n / 2; h >= 32; h >>= 1) {
@@ -884,6 +842,59 @@ k_conv(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ ds
             }
         }
     }
+}
+
+// One axis pass: one CTA = 16 grid lines along `axis`, staged through shared
+// memory so that global loads and stores are contiguous rows; each warp
+// convolves two real lines as one complex line.  The first axis pass reads
+// the spread grid `src`, clears it for the next matvec and writes `dst`;
+// the later passes work in place on `dst`.
+template <typename T, int R>
+__global__ void __launch_bounds__(256)
+k_conv(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ dst, int axis,
+       const T *__restrict__ tab, const typename Vec2<T>::type *__restrict__ tw,
+       int *__restrict__ ctr_reset, const int *__restrict__ done) {
+    using G = typename Num<T>::G;
+    using C = typename Vec2<T>::type;
+    constexpr int n = 32 * R, LPC = 16, PITCH = n + 1;
+    __shared__ T S[LPC * PITCH];
+    if (done && *done) return;
+    // the spreading of this matvec has finished (stream order)
+    if (ctr_reset && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ctr_reset = 0;
+    const bool clear = src != dst;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    G *gs = src + (int64_t)blockIdx.y * n * n * n;
+    G *gd = dst + (int64_t)blockIdx.y * n * n * n;
+    const int li0 = blockIdx.x * LPC;  // first line of the CTA
+    const int a0 = li0 % n, b0 = li0 / n;
+    // element (line j, position e) -> global offset
+    auto goff = [&](int j, int e) -> int64_t {
+        if (axis == 0) return ((int64_t)b0 * n + a0 + j) * n + e;          // lines (y, z)
+        if (axis == 1) return (int64_t)b0 * n * n + (int64_t)e * n + a0 + j;  // lines (x, z)
+        return (int64_t)e * n * n + (int64_t)b0 * n + a0 + j;                 // lines (x, y)
+    };
+    if (axis == 0) {
+        for (int q = tid; q < LPC * n; q += 256) {
+            int j = q / n, e = q % n;
+            const int64_t o = goff(j, e);
+            S[j * PITCH + e] = T(gs[o]);
+            if (clear) gs[o] = G(0);
+        }
+    } else {
+        for (int q = tid; q < LPC * n; q += 256) {
+            int j = q % LPC, e = q / LPC;
+            const int64_t o = goff(j, e);
+            S[j * PITCH + e] = T(gs[o]);
+            if (clear) gs[o] = G(0);
+        }
+    }
+    __syncthreads();
+
+    C xv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        xv[r] = {S[(2 * warp) * PITCH + 32 * r + lane], S[(2 * warp + 1) * PITCH + 32 * r + lane]};
+    conv_line<T, R>(xv, tab, tw, lane);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         S[(2 * warp) * PITCH + 32 * r + lane] = xv[r].x;
@@ -900,6 +911,76 @@ k_conv(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ ds
             int j = q % LPC, e = q / LPC;
             gd[goff(j, e)] = (G)S[j * PITCH + e];
         }
+    }
+}
+
+// The x and y passes in one kernel: one CTA = one z plane of one window,
+// staged whole in shared memory (n (n + 1) elements, rows padded against
+// bank conflicts of the column pass), convolved along x (rows) and then
+// along y (columns) by the CTA's warps two lines at a time, and written
+// back once.  Reads the spread grid `src`, clears it for the next matvec
+// and writes `dst`; the z pass (k_conv, axis 2) follows in place.
+constexpr int kConvXYThreads = 512;
+template <typename T>
+constexpr size_t conv_xy_smem(int n) {
+    return sizeof(T) * (size_t)n * (n + 1);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kConvXYThreads)
+k_conv_xy(typename Num<T>::G *__restrict__ src, typename Num<T>::G *__restrict__ dst,
+          const T *__restrict__ tab, const typename Vec2<T>::type *__restrict__ tw,
+          int *__restrict__ ctr_reset, const int *__restrict__ done) {
+    using G = typename Num<T>::G;
+    using C = typename Vec2<T>::type;
+    constexpr int n = 32 * R, PITCH = n + 1, NWARP = kConvXYThreads / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    if (done && *done) return;
+    // the spreading of this matvec has finished (stream order)
+    if (ctr_reset && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ctr_reset = 0;
+    const bool clear = src != dst;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t plane = ((int64_t)blockIdx.y * n + blockIdx.x) * n * n;  // (window, z)
+    G *gs = src + plane;
+    G *gd = dst + plane;
+    for (int q = tid; q < n * n; q += kConvXYThreads) {
+        const int y = q / n, x = q % n;
+        S[y * PITCH + x] = T(gs[q]);
+        if (clear) gs[q] = G(0);
+    }
+    __syncthreads();
+    // x lines: rows 2 p and 2 p + 1 as one complex line
+    for (int p = warp; p < n / 2; p += NWARP) {
+        C xv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            xv[r] = {S[(2 * p) * PITCH + 32 * r + lane], S[(2 * p + 1) * PITCH + 32 * r + lane]};
+        conv_line<T, R>(xv, tab, tw, lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            S[(2 * p) * PITCH + 32 * r + lane] = xv[r].x;
+            S[(2 * p + 1) * PITCH + 32 * r + lane] = xv[r].y;
+        }
+    }
+    __syncthreads();
+    // y lines: columns 2 p and 2 p + 1 as one complex line
+    for (int p = warp; p < n / 2; p += NWARP) {
+        C xv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            xv[r] = {S[(32 * r + lane) * PITCH + 2 * p], S[(32 * r + lane) * PITCH + 2 * p + 1]};
+        conv_line<T, R>(xv, tab, tw, lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            S[(32 * r + lane) * PITCH + 2 * p] = xv[r].x;
+            S[(32 * r + lane) * PITCH + 2 * p + 1] = xv[r].y;
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < n * n; q += kConvXYThreads) {
+        const int y = q / n, x = q % n;
+        gd[q] = (G)S[y * PITCH + x];
     }
 }
 
@@ -1104,6 +1185,12 @@ static void prepare_t() {
     prepare_w<T, 12>();
     prepare_w<T, 14>();
     prepare_w<T, 16>();
+    NLH_CUDA(cudaFuncSetAttribute(k_conv_xy<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_xy_smem<T>(32)));
+    NLH_CUDA(cudaFuncSetAttribute(k_conv_xy<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_xy_smem<T>(64)));
+    NLH_CUDA(cudaFuncSetAttribute(k_conv_xy<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_xy_smem<T>(128)));
     cudaFuncAttributes fa;
     NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 1>));
     NLH_CUDA(cudaFuncGetAttributes(&fa, k_conv<T, 2>));
@@ -1117,6 +1204,23 @@ static void convolve(Plan &P, typename Num<T>::G *src, typename Num<T>::G *dst, 
     const int n = P.n;
     dim3 gdim((unsigned)(n * n / 16), (unsigned)P.L);
     ProfRange pr(sizeof(T) == 4 ? NLH_K_CONV32 : NLH_K_CONV64, s);
+    if (n <= 128) {  // x and y in one plane kernel, then z: 2 launches
+        const size_t smem = conv_xy_smem<T>(n);
+        const dim3 pdim((unsigned)n, (unsigned)P.L);
+        switch (n) {
+            case 32: k_conv_xy<T, 1><<<pdim, kConvXYThreads, smem, s>>>(src, dst, tab, tw, P.unit_ctr, done); break;
+            case 64: k_conv_xy<T, 2><<<pdim, kConvXYThreads, smem, s>>>(src, dst, tab, tw, P.unit_ctr, done); break;
+            default: k_conv_xy<T, 4><<<pdim, kConvXYThreads, smem, s>>>(src, dst, tab, tw, P.unit_ctr, done); break;
+        }
+        NLH_CHECK_LAUNCH();
+        switch (n) {
+            case 32: k_conv<T, 1><<<gdim, 256, 0, s>>>(dst, dst, 2, tab, tw, nullptr, done); break;
+            case 64: k_conv<T, 2><<<gdim, 256, 0, s>>>(dst, dst, 2, tab, tw, nullptr, done); break;
+            default: k_conv<T, 4><<<gdim, 256, 0, s>>>(dst, dst, 2, tab, tw, nullptr, done); break;
+        }
+        NLH_CHECK_LAUNCH();
+        return;
+    }
     for (int axis = 0; axis < 3; ++axis) {
         using G = typename Num<T>::G;
         G *in = axis == 0 ? src : dst;
