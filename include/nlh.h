@@ -277,13 +277,22 @@ nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, double *u,
 
 /* Many solves at once (the batched form of the bilevel sweep): solve i is
  * (alphas[i] I + L_i) u[i] = b[i] with the operator of plans[i] (each plan
- * carries its own image, sigma and NFFT parameters).  Solves on distinct
- * plans run concurrently on internal streams, each solve as one CUDA graph
- * (or, for NLH_SOLVE_MIXED, one graph per refinement step); solves that
- * share a plan run one after another.  opts applies to every solve; x0 and
- * diag_scale must be NULL.  b[i], u[i] are device vectors of the plan's N.
- * Work is ordered after `stream`; the call synchronises and fills infos[i]
- * (seconds = wall time of the whole batch).  Returns the worst status. */
+ * carries its own image, sigma and NFFT parameters).  The whole batch is
+ * one CUDA graph, launched once on `stream`: each solve is a branch that
+ * runs its complete solve on the device (for NLH_SOLVE_MIXED the refinement
+ * loop is a device-side WHILE over steps, each an inner FP32 Krylov solve
+ * (itself a WHILE over CG iterations), the FP64-accurate residual and a
+ * decision kernel), branches of distinct plans run concurrently and solves
+ * that share a plan follow one another in one branch.  The graph is cached
+ * for the sequence of plans and options (at most 4 kept); it owns staging
+ * buffers for the right-hand sides and solutions (2 x the sum of N doubles),
+ * so the call copies b[i] in and u[i] out around the launch.  Plans with a
+ * reduce callback run round by round instead (one graph per solve and
+ * refinement step, on a pool of internal streams).  opts applies to every
+ * solve; x0 and diag_scale must be NULL.  b[i], u[i] are device vectors of
+ * the plan's N.  Work is ordered after `stream`; the call synchronises and
+ * fills infos[i] (seconds = wall time of the whole batch).  Returns the
+ * worst status. */
 nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, const double *alphas,
                              const double *const *b, double *const *u,
                              const nlh_solve_opts *opts, nlh_solve_info *infos,

@@ -156,6 +156,8 @@ struct Plan {
     SolveState *st_host = nullptr; // pinned mirror
     double *red_host = nullptr;   // pinned, 3 * kRedBlocks residual partials
     std::map<int, cudaGraphExec_t> graphs;  // solve graphs (see solve.cu)
+    uint64_t serial = 0;          // unique per plan creation (batch graph keys)
+    unsigned graph_epoch = 0;     // incremented whenever the solve graphs are dropped
     cudaStream_t capture_stream = nullptr;
     int device = 0;               // the device the plan was built on
     double *hist = nullptr;       // device, kMaxHist
@@ -240,6 +242,7 @@ void retain_pool_memory();
 // (synchronises s).
 void check_device_error(Plan &P, cudaStream_t s);
 cudaStream_t take_capture_stream(int device);
+void give_capture_stream(int device, cudaStream_t s);
 void plan_degrees(Plan &P, cudaStream_t s);
 // Destroy the cached solve graphs (after a change of tiling or launch shape).
 void drop_graphs(Plan &P);

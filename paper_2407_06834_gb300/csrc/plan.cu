@@ -8,6 +8,7 @@
 #include "df32.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <cmath>
 #include <cstdarg>
@@ -73,6 +74,12 @@ cudaStream_t take_capture_stream(int device) {
     return s;
 }
 
+void give_capture_stream(int device, cudaStream_t s) {
+    HostPool &hp = host_pool();
+    std::lock_guard<std::mutex> lk(hp.mu);
+    hp.streams[device].push_back(s);
+}
+
 Plan::~Plan() {
     cudaStreamSynchronize(stream);
     for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -87,6 +94,7 @@ Plan::~Plan() {
 // Destroy the plan's cached solve graphs (they hold the work-item and unit
 // arrays and the kernels' launch shapes); the next solve captures afresh.
 void drop_graphs(Plan &P) {
+    ++P.graph_epoch;  // batch graphs that hold this plan's solve are stale too
     if (P.graphs.empty()) return;
     NLH_CUDA(cudaStreamSynchronize(P.stream));
     for (auto &kv : P.graphs) cudaGraphExecDestroy(kv.second);
@@ -1139,6 +1147,8 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
         retain_pool_memory();
         prepare_nfft_kernels();
         P = new nlh_plan_s();
+        static std::atomic<uint64_t> serials{0};
+        P->serial = ++serials;
         P->stream = (cudaStream_t)stream;
         build_plan(*P, d, features, (cudaStream_t)stream);
         *out = P;

@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <mutex>
 
 namespace nlh {
@@ -427,9 +428,9 @@ static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, b
 // being about where the FP32 operator's rounding stops a solve) runs to
 // exactly that reduction, capped at 0.1, so that it is the last step; any
 // other step runs to the caller's inner tolerance.
-static double inner_tolerance(double inner, double tol, double rel) {
+__host__ __device__ static double inner_tolerance(double inner, double tol, double rel) {
     const double need = 0.5 * tol / rel;
-    if (need >= std::max(0.25 * inner, 1e-4)) return std::min(need, 0.1);
+    if (need >= fmax(0.25 * inner, 1e-4)) return fmin(need, 0.1);
     return inner;
 }
 
@@ -681,6 +682,324 @@ static void pool_reserve(int n) {
     }
 }
 
+// ---------------------------------------------------------- a batch as one graph
+// Every solve of a batch is one branch of a single CUDA graph, launched
+// once per call: the branch stages its right-hand side, then runs the whole
+// mixed-precision refinement on the device, a WHILE node over refinement
+// steps whose body is the inner FP32 Krylov solve (itself a WHILE node over
+// CG iterations), the accumulation of the correction, the FP64-accurate
+// residual b - A u and a decision kernel that records the step and sets the
+// outer loop's condition.  Solves that share a plan are chained one after
+// another in the same branch (a plan's workspace serves one solve at a
+// time).  The per-solve parameters (alpha, tolerances) live in device
+// memory uploaded before each launch, the right-hand sides and solutions in
+// buffers the graph owns, so a cached graph serves any call on the same
+// plans.
+
+// Parameters of one solve of a batch graph (device; uploaded per call).
+struct BatchParams {
+    double alpha, tol, inner;
+    int maxit, max_outer, mixed, pad;
+};
+// Result of one solve of a batch graph (device; read back per call).
+struct OuterState {
+    int outer, status, iters, mv32, mv64, pad;
+    double rel, rel_krylov;
+};
+
+__global__ void k_batch_start(OuterState *os) {
+    OuterState o{};
+    o.status = 1;
+    o.rel = 1.0;
+    o.rel_krylov = 1.0;
+    *os = o;
+}
+
+// The Krylov state of the next inner solve: the tolerance of the refinement
+// step from the current FP64-accurate residual (mixed), or the caller's.
+__global__ void k_batch_state(const BatchParams *bp, const OuterState *os, SolveState *st) {
+    SolveState v{};
+    v.tol = bp->mixed ? inner_tolerance(bp->inner, bp->tol, os->rel) : bp->tol;
+    v.maxit = bp->maxit;
+    v.rz_old = 1.0;
+    v.alpha = bp->alpha;
+    *st = v;
+}
+
+// After an inner solve and the residual's partial sums (k_residual): record
+// the step; the outer WHILE continues unless the solve converged, broke
+// down or ran out of refinement steps.
+__global__ void __launch_bounds__(kRedThreads)
+k_batch_step(const BatchParams *bp, const SolveState *st, const double *partials,
+             OuterState *os, unsigned long long cond) {
+    __shared__ double sh[33];
+    const double rr = reduce_partials(partials, kRedBlocks, 3, 0, sh);
+    const double bb = reduce_partials(partials, kRedBlocks, 3, 1, sh);
+    if (threadIdx.x != 0) return;
+    const double rel = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    OuterState o = *os;
+    o.iters += st->k;
+    o.outer += 1;
+    o.rel_krylov = sqrt(st->rr) / (st->bnorm > 0.0 ? st->bnorm : 1.0);
+    bool stop = true;
+    if (bp->mixed) {
+        o.mv32 += st->k;
+        if (st->status == -4) {
+            o.status = -4;
+        } else {
+            o.mv64 += 1;
+            o.rel = rel;
+            if (rel <= bp->tol) o.status = 0;
+            else if (o.outer >= bp->max_outer) o.status = 1;
+            else stop = false;
+        }
+    } else {
+        o.mv64 += st->k + 1;
+        o.rel = rel;
+        o.status = st->status == -4 ? -4 : (o.rel_krylov <= st->tol ? 0 : 1);
+    }
+    *os = o;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, stop ? 0u : 1u);
+}
+
+// Captures what fn enqueues into graph g after deps; returns the new leaves.
+template <typename F>
+static std::vector<cudaGraphNode_t> capture_into(cudaStream_t cs, cudaGraph_t g,
+                                                 const std::vector<cudaGraphNode_t> &deps,
+                                                 F &&fn) {
+    NLH_CUDA(cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                           deps.size(), cudaStreamCaptureModeThreadLocal));
+    try {
+        fn(cs);
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        throw;
+    }
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *leaf = nullptr;
+    size_t nl = 0;
+    NLH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &leaf, nullptr, &nl));
+    std::vector<cudaGraphNode_t> out(leaf, leaf + nl);
+    cudaGraph_t g_out = g;
+    NLH_CUDA(cudaStreamEndCapture(cs, &g_out));
+    return out;
+}
+
+static cudaGraphNode_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                                 cudaGraphConditionalHandle h, cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    NLH_CUDA(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                              deps.size(), &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return node;
+}
+
+struct BatchGraph {
+    std::vector<std::pair<uint64_t, unsigned>> key;  // (plan serial, graph epoch) per solve
+    int arith = 0, method = 0, precond = 0, device = 0;
+    int n = 0;
+    cudaGraphExec_t exec = nullptr;
+    double *bbuf = nullptr, *ubuf = nullptr;  // staged right-hand sides / solutions
+    std::vector<int64_t> off;
+    BatchParams *bp = nullptr, *bp_host = nullptr;
+    OuterState *os = nullptr, *os_host = nullptr;
+    ~BatchGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (bbuf) cudaFree(bbuf);
+        if (ubuf) cudaFree(ubuf);
+        if (bp) cudaFree(bp);
+        if (os) cudaFree(os);
+        if (bp_host) cudaFreeHost(bp_host);
+        if (os_host) cudaFreeHost(os_host);
+    }
+};
+static std::mutex g_batch_mu;
+static std::vector<std::unique_ptr<BatchGraph>> g_batch;  // most recently used last
+constexpr size_t kBatchGraphsKept = 4;
+
+// The branch of solve i: stage, then the refinement loop (mixed) or one
+// Krylov solve and its residual.
+static std::vector<cudaGraphNode_t> batch_branch(Plan &P, cudaStream_t cs, cudaGraph_t top,
+                                                 const std::vector<cudaGraphNode_t> &deps,
+                                                 const double *bi, double *ui,
+                                                 const BatchParams *bp, OuterState *os,
+                                                 int arith, int method) {
+    int deflate, precond;
+    method_flags(method, deflate, precond);
+    const bool mixed = arith == NLH_SOLVE_MIXED;
+    const int accurate = (P.precision & 4) ? NLH_DF32 : NLH_FP64;
+    const int prec = mixed ? NLH_FP32 : (arith == NLH_SOLVE_FP64 ? NLH_FP64 : NLH_DF32);
+    const int rprec = mixed ? accurate : prec;
+    const int64_t N = P.N;
+    auto stage = [&](cudaStream_t c) {
+        if (mixed) NLH_CUDA(cudaMemsetAsync(ui, 0, sizeof(double) * N, c));
+        NLH_CUDA(cudaMemcpyAsync(P.rhs, bi, sizeof(double) * N, cudaMemcpyDeviceToDevice, c));
+        k_batch_start<<<1, 1, 0, c>>>(os);
+        NLH_CHECK_LAUNCH();
+    };
+    // one inner solve + residual + decision into graph g (cond: the outer
+    // loop's handle, 0 for a single step)
+    auto step = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t> &d0,
+                    unsigned long long cond) {
+        cudaGraphConditionalHandle hi;
+        NLH_CUDA(cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault));
+        auto lv = capture_into(cs, g, d0, [&](cudaStream_t c) {
+            k_batch_state<<<1, 1, 0, c>>>(bp, os, P.st);
+            NLH_CHECK_LAUNCH();
+            enqueue_init(P, prec, method, false, false, (unsigned long long)hi, c);
+        });
+        cudaGraph_t body;
+        cudaGraphNode_t w = add_while(g, lv, hi, &body);
+        capture_into(cs, body, {}, [&](cudaStream_t c) {
+            enqueue_iteration(P, prec, method, (unsigned long long)hi, c);
+        });
+        return capture_into(cs, g, {w}, [&](cudaStream_t c) {
+            k_finish<<<kRedBlocks, kRedThreads, 0, c>>>(P.w, N, P.st, deflate, mixed ? 1 : 0, ui);
+            NLH_CHECK_LAUNCH();
+            matvec(P, 2, rprec, 0.0, ui, P.q, nullptr, nullptr, c, &P.st->alpha);
+            k_residual<<<kRedBlocks, kRedThreads, 0, c>>>(bi, P.q, N, mixed ? P.rhs : nullptr,
+                                                          P.partials);
+            NLH_CHECK_LAUNCH();
+            k_batch_step<<<1, kRedThreads, 0, c>>>(bp, P.st, P.partials, os, cond);
+            NLH_CHECK_LAUNCH();
+        });
+    };
+    auto lv = capture_into(cs, top, deps, stage);
+    if (!mixed) return step(top, lv, 0ull);
+    cudaGraphConditionalHandle ho;
+    NLH_CUDA(cudaGraphConditionalHandleCreate(&ho, top, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t body;
+    cudaGraphNode_t w = add_while(top, lv, ho, &body);
+    step(body, {}, (unsigned long long)ho);
+    return {w};
+}
+
+static BatchGraph &batch_graph(int n, const nlh_plan *plans, int arith, int method,
+                               int precond, int device) {
+    std::vector<std::pair<uint64_t, unsigned>> key(n);
+    for (int i = 0; i < n; ++i) key[i] = {plans[i]->serial, plans[i]->graph_epoch};
+    for (size_t k = 0; k < g_batch.size(); ++k) {
+        BatchGraph &G = *g_batch[k];
+        if (G.key == key && G.arith == arith && G.method == method && G.precond == precond &&
+            G.device == device) {
+            std::unique_ptr<BatchGraph> keep = std::move(g_batch[k]);
+            g_batch.erase(g_batch.begin() + k);
+            g_batch.push_back(std::move(keep));
+            return *g_batch.back();
+        }
+    }
+    std::unique_ptr<BatchGraph> G(new BatchGraph());
+    G->key = key;
+    G->arith = arith;
+    G->method = method;
+    G->precond = precond;
+    G->device = device;
+    G->n = n;
+    G->off.resize(n + 1, 0);
+    for (int i = 0; i < n; ++i) G->off[i + 1] = G->off[i] + plans[i]->N;
+    NLH_CUDA(cudaMalloc(&G->bbuf, sizeof(double) * G->off[n]));
+    NLH_CUDA(cudaMalloc(&G->ubuf, sizeof(double) * G->off[n]));
+    NLH_CUDA(cudaMalloc(&G->bp, sizeof(BatchParams) * n));
+    NLH_CUDA(cudaMalloc(&G->os, sizeof(OuterState) * n));
+    NLH_CUDA(cudaMallocHost(&G->bp_host, sizeof(BatchParams) * n));
+    NLH_CUDA(cudaMallocHost(&G->os_host, sizeof(OuterState) * n));
+    cudaStream_t cs = take_capture_stream(device);
+    cudaGraph_t top = nullptr;
+    NLH_CUDA(cudaGraphCreate(&top, 0));
+    try {
+        std::map<nlh_plan, std::vector<cudaGraphNode_t>> tail;  // last nodes of each plan's chain
+        for (int i = 0; i < n; ++i) {
+            Plan &P = *plans[i];
+            tail[plans[i]] = batch_branch(P, cs, top, tail[plans[i]], G->bbuf + G->off[i],
+                                          G->ubuf + G->off[i], G->bp + i, G->os + i, arith,
+                                          method);
+        }
+        NLH_CUDA(cudaGraphInstantiate(&G->exec, top, 0));
+    } catch (...) {
+        cudaGraphDestroy(top);
+        give_capture_stream(device, cs);
+        throw;
+    }
+    cudaGraphDestroy(top);
+    give_capture_stream(device, cs);
+    if (g_batch.size() >= kBatchGraphsKept) g_batch.erase(g_batch.begin());
+    g_batch.push_back(std::move(G));
+    return *g_batch.back();
+}
+
+// Validated batch (see nlh_solve_batched) through its graph: upload the
+// parameters and right-hand sides, one launch, copy the solutions out.
+static nlh_status solve_batched_graph(int n, const nlh_plan *plans, const double *alphas,
+                                      const double *const *b, double *const *u,
+                                      const nlh_solve_opts *opts, nlh_solve_info *infos,
+                                      cudaStream_t s,
+                                      std::chrono::steady_clock::time_point t0) {
+    int device = 0;
+    NLH_CUDA(cudaGetDevice(&device));
+    for (int i = 0; i < n; ++i) {
+        NLH_REQUIRE(plans[i]->device == device, "nlh_solve_batched: plan %d is on device %d", i,
+                    plans[i]->device);
+        NLH_REQUIRE(b[i] != u[i], "nlh_solve_batched: b and u of solve %d alias", i);
+    }
+    for (int i = 0; i < n; ++i) {
+        Plan &P = *plans[i];
+        P.stream = s;
+        P.pc_kind = opts->precond;  // captured into the graph (part of its key)
+        if (P.pc_kind == 1) ensure_pb2(P, s);
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    const bool mixed = opts->arith == NLH_SOLVE_MIXED;
+    BatchGraph &G = batch_graph(n, plans, opts->arith, opts->method, opts->precond, device);
+    for (int i = 0; i < n; ++i) {
+        BatchParams &q = G.bp_host[i];
+        q.alpha = alphas[i];
+        q.tol = opts->tol;
+        q.inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        q.maxit = opts->maxit;
+        q.max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
+        q.mixed = mixed ? 1 : 0;
+        q.pad = 0;
+    }
+    NLH_CUDA(cudaMemcpyAsync(G.bp, G.bp_host, sizeof(BatchParams) * n, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < n; ++i)
+        NLH_CUDA(cudaMemcpyAsync(G.bbuf + G.off[i], b[i], sizeof(double) * plans[i]->N,
+                                 cudaMemcpyDeviceToDevice, s));
+    NLH_CUDA(cudaGraphLaunch(G.exec, s));
+    count_launch();
+    for (int i = 0; i < n; ++i)
+        NLH_CUDA(cudaMemcpyAsync(u[i], G.ubuf + G.off[i], sizeof(double) * plans[i]->N,
+                                 cudaMemcpyDeviceToDevice, s));
+    NLH_CUDA(cudaMemcpyAsync(G.os_host, G.os, sizeof(OuterState) * n, cudaMemcpyDeviceToHost, s));
+    NLH_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) check_device_error(*plans[i], s);
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    nlh_status worst = NLH_OK;
+    for (int i = 0; i < n; ++i) {
+        const OuterState &o = G.os_host[i];
+        nlh_solve_info inf{};
+        inf.iters = o.iters;
+        inf.outer = o.outer;
+        inf.matvecs_fp32 = o.mv32;
+        inf.matvecs_fp64 = o.mv64;
+        inf.rel_res = mixed ? o.rel : o.rel_krylov;
+        inf.rel_res_true = o.rel;
+        inf.status = o.status == 0 ? NLH_OK
+                                   : (o.status == -4 ? NLH_ERR_BREAKDOWN : NLH_ERR_NOT_CONVERGED);
+        inf.seconds = secs;
+        if (infos) infos[i] = inf;
+        if (inf.status == NLH_ERR_BREAKDOWN) worst = NLH_ERR_BREAKDOWN;
+        else if (inf.status == NLH_ERR_NOT_CONVERGED && worst == NLH_OK)
+            worst = NLH_ERR_NOT_CONVERGED;
+    }
+    return worst;
+}
+
 }  // namespace nlh
 
 extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, const double *alphas,
@@ -703,6 +1022,16 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                     "nlh_solve_batched: arith=%d", opts->arith);
         NLH_REQUIRE(opts->x0 == nullptr && opts->diag_scale == nullptr,
                     "nlh_solve_batched: x0 and diag_scale are per-solve; use nlh_solve");
+        // one graph for the whole batch, unless a plan's matvecs call a
+        // reduce callback (its collective is enqueued per call, which a
+        // captured graph would not repeat): those run the round-based path
+        bool any_reduce = false;
+        for (int i = 0; i < nsolves; ++i) {
+            NLH_REQUIRE(plans[i] && b[i] && u[i], "nlh_solve_batched: NULL in solve %d", i);
+            any_reduce = any_reduce || plans[i]->reduce_fn != nullptr;
+        }
+        if (!any_reduce) return solve_batched_graph(nsolves, plans, alphas, b, u, opts, infos,
+                                                    (cudaStream_t)stream, t0);
         // group the solves by plan (a plan's workspace serves one solve at a time)
         std::map<nlh_plan, std::vector<int>> by_plan;
         for (int i = 0; i < nsolves; ++i) {

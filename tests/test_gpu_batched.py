@@ -91,6 +91,29 @@ def test_batched_solutions_certified_by_oracle(arith):
         P.close()
 
 
+def test_batched_graph_reused_with_new_parameters_and_rebuilt_after_retile():
+    """The batch graph is cached per sequence of plans: a second call with
+    other alphas and right-hand sides reuses it (parameters and vectors are
+    staged per call) and still equals single solves; retiling a plan makes
+    the next call capture a new graph for the new tiling."""
+    imgs = [image(20, 28, seed=7), image(32, 32, seed=8)]
+    plans = [_auto_plan(im, s) for im, s in zip(imgs, [0.2, 0.4])]
+    for step, alphas in enumerate(([0.5, 1.0], [0.05, 3.0], [0.2, 0.2])):
+        if step == 2:
+            plans[0].retile(32, 256)
+        bs = [cuda(a * im.ravel()) for im, a in zip(imgs, alphas)]
+        us, infos = nlh.solve_batched(plans, alphas, bs, tol=1e-6, arith=nlh.SOLVE_MIXED,
+                                      inner_tol=1e-3)
+        for k, a in enumerate(alphas):
+            single = plans[k].solve(a, bs[k], tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+            assert infos[k]["status"] == 0 and infos[k]["rel_res_true"] <= 1e-6
+            assert infos[k]["iters"] == single.info["iters"]
+            assert infos[k]["outer"] == single.info["outer"]
+            assert rel(host(us[k]), host(single.u)) < 1e-9
+    for P in plans:
+        P.close()
+
+
 def test_batched_rejects_bad_arguments():
     img = image(16, 16, seed=4)
     P = _auto_plan(img, 0.2)
