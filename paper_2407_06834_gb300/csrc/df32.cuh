@@ -131,7 +131,10 @@ __device__ __forceinline__ unsigned long long pk_fma(unsigned long long a, unsig
 
 // (h, l) += (a.hi, a.lo) * (wh, wl) for two cells at once.  nah, nal are
 // the negated (duplicated) parts of a; the product's error term is formed
-// negated, e = p - a*w, so that it only needs fused multiply-adds.
+// negated, e = p - a*w = fma(-a, w, p), so that it only needs fused
+// multiply-adds.  (The other form, fma(a, w, 0 - p) on the packed
+// instructions, measured on sm_103a with CUDA 13.0 as if the product's
+// rounding error were zero; the negated-operand form is exact.)
 __device__ __forceinline__ void pk_df_axpy(unsigned long long &h, unsigned long long &l,
                                            unsigned long long ah, unsigned long long nah,
                                            unsigned long long nal, unsigned long long wh,

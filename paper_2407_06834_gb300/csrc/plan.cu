@@ -956,7 +956,7 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         P.wp64 = ws.f64;
         P.wpdf = ws.fdf;
         // staged tables for the kernels' shared-memory copies: FP64 {E_k, O_k}
-        // per (j, k), then double-float {E hi, E lo, O hi, O lo} per (j, k)
+        // per (j, k), then double-float {E hi, O hi, E lo, O lo} per (j, k)
         std::vector<float4> st(2 * kWinStageBytes / 16, make_float4(0.f, 0.f, 0.f, 0.f));
         double2 *st64 = reinterpret_cast<double2 *>(st.data());
         for (int j = 0; j < kWinHalfMax; ++j)
@@ -965,8 +965,8 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         float4 *stdf = st.data() + kWinStageBytes / 16;
         for (int j = 0; j < kWinHalfMax; ++j)
             for (int k = 0; k < kWinK64; ++k)
-                stdf[j * kWinK64 + k] = make_float4(ws.fdf.hi[j][0][k], ws.fdf.lo[j][0][k],
-                                                    ws.fdf.hi[j][1][k], ws.fdf.lo[j][1][k]);
+                stdf[j * kWinK64 + k] = make_float4(ws.fdf.hi[j][0][k], ws.fdf.hi[j][1][k],
+                                                    ws.fdf.lo[j][0][k], ws.fdf.lo[j][1][k]);
         P.wstage = P.alloc<float4>(st.size());
         NLH_CUDA(cudaMemcpyAsync(P.wstage, st.data(), sizeof(float4) * st.size(),
                                  cudaMemcpyHostToDevice, s));

@@ -82,13 +82,15 @@ __device__ __forceinline__ void win_weights(const double2 *sc, double y, double 
 }
 
 // Double-float: the leading coefficients in FP32, the rest as Horner steps
-// w = w u + c with TwoProduct / TwoSum (df32.cuh).  TwoSum reads each
+// w = w u + c with TwoProduct / TwoSum (df32.cuh).  The even and odd chains
+// of a pair run side by side in packed f32x2 registers (both multiply by the
+// same u), one instruction per step for both.  TwoSum reads each
 // coefficient several times, and a compiler that keeps all of them in
 // registers across a kernel's loops runs out of registers, so the
 // coefficients come from a shared-memory copy of the plan's staged table,
-// one broadcast 16-byte load per step: sc[j][k] = {E hi, E lo, O hi, O lo}.
+// one broadcast 16-byte load per step: sc[j][k] = {E hi, O hi, E lo, O lo}.
 // Bytes of one staged table: kWinK64 16-byte entries per j, {E_k, O_k} as
-// doubles (FP64) or {E hi, E lo, O hi, O lo} as floats (double-float).
+// doubles (FP64) or {E hi, O hi, E lo, O lo} as floats (double-float).
 constexpr int kWinStageBytes = 16 * kWinHalfMax * kWinK64;
 
 // Copies a staged table (global memory, kWinStageBytes) into shared memory.
@@ -99,24 +101,38 @@ __device__ __forceinline__ void win_stage(const float4 *__restrict__ src, float4
 template <int W2>
 __device__ __forceinline__ void win_weights(const float4 *sc, df32 y, df32 (&w)[W2]) {
     const df32 u = y * y;
+    // u and its negation, duplicated into both halves; the product errors are
+    // formed negated, p - h u, with the negated u as an operand (as in
+    // pk_df_axpy), so that they need fused multiply-adds only
+    const unsigned long long uh = pk_dup(u.hi), nuh = pk_dup(-u.hi), nul = pk_dup(-u.lo);
+    const ulonglong2 *sq = reinterpret_cast<const ulonglong2 *>(sc);
 #pragma unroll
     for (int j = 0; j < W2 / 2; ++j) {
-        const float4 t = sc[j * kWinK64 + kWinK64 - 1];
-        float e32 = t.x, o32 = t.z;
+        // h = (E hi, O hi), l = (E lo, O lo)
+        unsigned long long h = sq[j * kWinK64 + kWinK64 - 1].x, l = 0ull;
 #pragma unroll
-        for (int k = kWinK64 - 2; k >= kWinDfSplit; --k) {
-            const float4 q = sc[j * kWinK64 + k];
-            e32 = fmaf(e32, u.hi, q.x);
-            o32 = fmaf(o32, u.hi, q.z);
-        }
-        df32 e(e32, 0.f), o(o32, 0.f);
+        for (int k = kWinK64 - 2; k >= kWinDfSplit; --k) h = pk_fma(h, uh, sq[j * kWinK64 + k].x);
 #pragma unroll
         for (int k = kWinDfSplit - 1; k >= 0; --k) {
-            const float4 q = sc[j * kWinK64 + k];
-            e = e * u + df32(q.x, q.y);
-            o = o * u + df32(q.z, q.w);
+            const ulonglong2 q = sq[j * kWinK64 + k];
+            // (h, l) * (u hi, u lo): product p and its negated error ne with the
+            // cross terms
+            const unsigned long long p = pk_mul(h, uh);
+            unsigned long long ne = pk_fma(h, nuh, p);
+            ne = pk_fma(h, nul, ne);
+            ne = pk_fma(l, nuh, ne);
+            // + (c hi, c lo): TwoSum of the high parts, low parts in FP32
+            const unsigned long long s2 = pk_add(p, q.x);
+            const unsigned long long bp = pk_sub(s2, p);
+            const unsigned long long t = pk_add(pk_sub(p, pk_sub(s2, bp)), pk_sub(q.x, bp));
+            l = pk_add(t, pk_sub(q.y, ne));
+            h = s2;
         }
-        const df32 yo = y * o;
+        float eh, oh, el, ol;
+        pk_split(h, eh, oh);
+        pk_split(l, el, ol);
+        const df32 yo = y * df32(oh, ol);
+        const df32 e = df32(eh, el);
         w[j] = e + yo;
         w[W2 - 1 - j] = e - yo;
     }
