@@ -416,6 +416,36 @@ __device__ __forceinline__ bool idx_ok(bool cond, int id, long long idx, long lo
     return false;
 }
 
+// Prefetch of the byte range [b0, b1) of an array of total_bytes bytes
+// (16-byte aligned base) into L2 with one bulk prefetch, the range widened
+// to 16-byte boundaries and clipped to the array.
+__device__ __forceinline__ void prefetch_l2(const void *base, int64_t b0, int64_t b1,
+                                            int64_t total_bytes) {
+    const int64_t lo = b0 & ~(int64_t)15;
+    int64_t hi = (b1 + 15) & ~(int64_t)15;
+    const int64_t cap = total_bytes & ~(int64_t)15;
+    if (hi > cap) hi = cap;
+    if (lo < 0 || hi <= lo) return;
+    const char *p = static_cast<const char *>(base) + lo;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)(hi - lo))
+                 : "memory");
+}
+
+// The point data of a unit's sorted range (permutation entries and cell
+// offsets), prefetched into L2 once the unit's items are staged, so that the
+// spreading teams' later chunks find it there (4% on FP32 spreading at
+// 2m = 12; the interpolation, which reads each point once per lane right
+// after staging its tile, measured no gain).  One thread, once per unit.
+__device__ __noinline__ void prefetch_unit(const NfftArgs &a, const int4 *s_items, int nit,
+                                              bool lo_parts) {
+    const int64_t first = s_items[0].z, end = (int64_t)s_items[nit - 1].z + s_items[nit - 1].w;
+    const int64_t total = (int64_t)a.L * a.N;
+    if (first < 0 || end > total || end <= first) return;
+    prefetch_l2(a.perm, 4 * first, 4 * end, 4 * total);
+    prefetch_l2(a.yhi, 12 * first, 12 * end, 12 * total);
+    if (lo_parts) prefetch_l2(a.ylo, 12 * first, 12 * end, 12 * total);
+}
+
 // ------------------------------------------------------------------ spreading
 // Shared memory of a spreading CTA: the tile region (kTile + 2m - 1)^3, the
 // unit's items, control words, one broadcast slot per team, and per team the
@@ -491,6 +521,7 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
         for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = a.items[it0 + e];
         if (threadIdx.x == 0) s_ctl[0] = TPB;
         __syncthreads();
+        if (threadIdx.x == 0) prefetch_unit(a, s_items, nit, !std::is_same<T, float>::value);
         Line<T, WS> acc[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) acc[k].zero();
