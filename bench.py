@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--workload", default="img2048", choices=sorted(WORKLOADS))
     ap.add_argument("--shard", choices=["windows", "replicas"], default="windows",
                     help="N > 1: windows over ranks (one all-reduce per matvec) or replicas")
+    ap.add_argument("--coords", choices=["stored", "image"], default="stored",
+                    help="plans store each point's cell offsets (default) or recompute "
+                         "the coordinates from the image")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle row sample (0 = auto)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form leg")
@@ -277,7 +280,7 @@ def read_profile(lib):
     return prof
 
 
-def roofline(prof, wl):
+def roofline(prof, wl, coords="stored"):
     """The dominant NFFT kernel class of the timed region against its
     rooflines.  Method work per point-window and direction: (2m)^3 stencil
     multiply-adds (2m window points per dim), 2 FLOP each, in the kernel's
@@ -303,15 +306,20 @@ def roofline(prof, wl):
                 "update" if dom.endswith("df32") else ""))
     hbm_peak, hbm_src = measured_peaks()
     alg_bytes = 0.5 * (wl.N * 20.0 + wl.N * wl.L * 8.0)
-    # what these kernels read given the stored per-point data: permutation and
-    # cell offsets per point-window, the input or output per pixel, the grid
+    # what these kernels read with the plan's data: the permutation entry and
+    # the stored cell offsets per point-window (12 B FP32, + 12 B low parts
+    # for FP64 and double-float; the image per pixel instead when the
+    # coordinates are recomputed from it), the input or output per pixel,
+    # the grid
     parts = 2 if dom.endswith(("64", "df32")) else 1
     gbytes = 8 if dom.endswith(("64", "df32")) else 4
-    data_bytes = (wl.N * wl.L * (4.0 + 12.0 * parts) + wl.N * 8.0 +
-                  wl.L * wl.n_os ** 3 * float(gbytes))
+    per_pw = 4.0 + (0.0 if coords == "image" else 12.0 * parts)
+    data_bytes = (wl.N * wl.L * per_pw + wl.N * 8.0 + (wl.N * 8.0 if coords == "image" else 0.0)
+                  + wl.L * wl.n_os ** 3 * float(gbytes))
     traffic, tnote = None, None
     sha = kernel_sources_sha16()
-    if NCU_TRAFFIC.get("sources_sha16") == sha and NCU_TRAFFIC.get("workload") == wl.name:
+    if (NCU_TRAFFIC.get("sources_sha16") == sha and NCU_TRAFFIC.get("workload") == wl.name
+            and NCU_TRAFFIC.get("coords", "stored") == coords):
         traffic = NCU_TRAFFIC["bytes_per_launch"].get(dom)
         tnote = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, same kernel sources"
     else:
@@ -384,7 +392,8 @@ def run_ours(args):
             autotune = False
         return nlh.Plan.from_image(image, wl.radius, wl.windows, sigma, pad=wl.pad, M=wl.M,
                                    n_os=wl.n_os, m=wl.m, precision=precision,
-                                   autotune=autotune, **kw)
+                                   autotune=autotune, coords_from_image=args.coords == "image",
+                                   **kw)
 
     def step_on(image, u):
         P = make_plan(image, wl.sigma)
@@ -409,7 +418,7 @@ def run_ours(args):
     mv = [i["matvecs_fp64"] + i["matvecs_fp32"] + 2 for i in step_infos]
     pts = float(N * L * sum(mv))
     value = combine_ranks(total_ms, pts, dev, sum_work=not sharded)
-    roof = roofline(prof, wl) if not sharded else None
+    roof = roofline(prof, wl, args.coords) if not sharded else None
 
     # ---- end to end through the public API with host buffers
     img_h = torch.empty((wl.n1, wl.n2), dtype=torch.float64, pin_memory=True)
@@ -500,7 +509,9 @@ def run_ours(args):
                    "parallelism": ("windows %s per rank, one NCCL all-reduce per matvec" % (wrange,)
                                    if sharded else ("replicas" if world > 1 else "single GPU")),
                    "torus_fill": pinfo["torus_fill"], "work_items": pinfo["n_items"],
-                   "plan_device_bytes": pinfo["device_bytes"]},
+                   "plan_device_bytes": pinfo["device_bytes"],
+                   "coordinates": ("recomputed from the image" if args.coords == "image"
+                                   else "stored cell offsets per point-window")},
         "solve_seconds": solve_s,
         "matvec_kernel_only": mv_gpts,
         "iters_per_step": statistics.mean(i["iters"] for i in step_infos),
@@ -683,7 +694,8 @@ def matvec_case(args):
     wl = WORKLOADS[args.workload]
     img = torch.as_tensor(wl.image(), device="cuda")
     P = nlh.Plan.from_image(img, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
-                            n_os=wl.n_os, m=wl.m, precision=6)
+                            n_os=wl.n_os, m=wl.m, precision=6,
+                            coords_from_image=args.coords == "image")
     x = torch.randn(wl.N, dtype=torch.float64, device="cuda")
     for prec in (nlh.NLH_FP32, nlh.NLH_DF32):
         for _ in range(2):

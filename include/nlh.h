@@ -114,6 +114,24 @@ typedef struct {
                                without it only op 0 (the range's share of
                                Gamma_full x) is defined                      */
     void *reduce_ctx;       /* passed to reduce                              */
+    const double *image;    /* device n1 x n2 FP64 image the features are the
+                               patches of (nlh_patch_features with
+                               patch_radius, patch_pad; D = (2 r + 1)^2,
+                               N = n1 n2), or NULL.  With it the plan keeps a
+                               copy of the image instead of every point's
+                               cell offsets, and the NFFT kernels recompute
+                               each point's torus coordinates from the image
+                               (FP64 arithmetic for the FP64 and
+                               double-float paths, double-float for FP32):
+                               12 B (FP32) or 24 B per point-window less
+                               memory and traffic, at the cost of the
+                               recomputation (measured 3-21 % slower
+                               kernels: they are bound by arithmetic, not
+                               by DRAM).  The caller guarantees that
+                               features are those patches                 */
+    int image_n1, image_n2; /* image rows, columns                           */
+    int patch_radius;       /* >= 0                                          */
+    int patch_pad;          /* 0 zero, 1 reflect (as nlh_patch_features)     */
 } nlh_plan_desc;
 
 /* Build a plan from a feature matrix (Sec. 3 / Sec. 5): window coordinates,
@@ -146,6 +164,8 @@ typedef struct {
     int max_items_pts, unit_points;  /* current tiling of the work           */
     int team[3];                     /* current launch shapes (see desc)     */
     int window_first, window_count;  /* the plan's window range              */
+    int coords_from_image;           /* 1: coordinates recomputed from the
+                                        image (desc.image), 0: stored        */
 } nlh_plan_info;
 
 nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info);

@@ -156,6 +156,20 @@ struct Plan {
     SolveState *st_host = nullptr; // pinned mirror
     double *red_host = nullptr;   // pinned, 3 * kRedBlocks residual partials
     std::map<int, cudaGraphExec_t> graphs;  // solve graphs (see solve.cu)
+    // coordinates from the image (nlh_plan_desc.image) instead of stored
+    // offsets: a copy of the image (FP64 for the FP64 and double-float
+    // paths, a (hi, lo) float pair per pixel for FP32), per (window, dim)
+    // the patch offset {zero dim, dr, dc, 0} and the torus map as
+    // u = A x + B[l][t] (grid coordinate of a feature value x)
+    int coords_image = 0;
+    double *img64 = nullptr;
+    float2 *img2 = nullptr;
+    int img_n1 = 0, img_n2 = 0, img_pad = 0;
+    int4 *coff = nullptr;
+    double cA = 0.0;
+    float2 cAdf = {0.f, 0.f};
+    double *cB = nullptr;
+    float2 *cBdf = nullptr;
     uint64_t serial = 0;          // unique per plan creation (batch graph keys)
     unsigned graph_epoch = 0;     // incremented whenever the solve graphs are dropped
     cudaStream_t capture_stream = nullptr;

@@ -394,7 +394,92 @@ struct NfftArgs {
     int L;               // windows of the plan (units' window index < L)
     int64_t N;           // pixels (permutation entries < N; sorted positions < L N)
     const float4 *wstage;  // staged window coefficients of the arithmetic (FP64, df32)
+    // coordinates from the image (img64 or img2 non-NULL) instead of yhi, ylo
+    const double *img64;   // FP64 image (FP64 and double-float paths)
+    const float2 *img2;    // (hi, lo) pairs of the image (FP32 path)
+    int n1, n2, pad;       // image rows, columns; 1 reflect, 0 zero padding
+    const int4 *coff;      // [window][dim] {zero dim, dr, dc, 0}
+    const double *cB;      // [window][dim] B of u = A x + B
+    const float2 *cBdf;
+    double cA;
+    float2 cAdf;
 };
+
+// ---- the cell offset y = 2 (u - c) - 1 of a point in dim t, recomputed from
+// the image: the patch value x of pixel `pix` at the window's dim offset
+// (reflect or zero padding, as the patch features), its grid coordinate
+// u = A x + B[l][t] (the torus map of the plan), and its cell c along t (the
+// item's cell; a difference of more than half the grid is the torus
+// wrap).  FP64 arithmetic for the FP64 and double-float paths (the result
+// matches the plan's stored FP64 offsets to ~1e-14), double-float for FP32.
+// Row and column of a pixel (one 32-bit division per point).
+struct PixRC {
+    int r, c;
+};
+__device__ __forceinline__ PixRC pix_rc(const NfftArgs &a, int pix) {
+    const unsigned r = (unsigned)pix / (unsigned)a.n2;
+    return PixRC{(int)r, pix - (int)r * a.n2};
+}
+
+__device__ __forceinline__ int patch_pixel(const NfftArgs &a, PixRC p, int4 o, bool &zero) {
+    int rr = p.r + o.y, cc = p.c + o.z;
+    zero = o.x != 0;
+    if (a.pad == 1) {
+        rr = reflect_index(rr, a.n1);
+        cc = reflect_index(cc, a.n2);
+    } else if (rr < 0 || rr >= a.n1 || cc < 0 || cc >= a.n2) {
+        zero = true;
+    }
+    return zero ? 0 : rr * a.n2 + cc;
+}
+
+__device__ __forceinline__ double torus_frac(double f, int n) {
+    if (f > 0.5 * n) return f - n;
+    if (f < -0.5 * n) return f + n;
+    return f;
+}
+
+template <typename T> struct ImageOffs;
+template <> struct ImageOffs<double> {
+    static __device__ __forceinline__ double get(const NfftArgs &a, int l, int t, PixRC p,
+                                                 int cell) {
+        bool zero;
+        const int q = patch_pixel(a, p, __ldg(a.coff + 3 * l + t), zero);
+        const double x = zero ? 0.0 : __ldg(a.img64 + q);
+        const double u = fma(a.cA, x, __ldg(a.cB + 3 * l + t));
+        return fma(2.0, torus_frac(u - (double)cell, a.n), -1.0);
+    }
+};
+template <> struct ImageOffs<df32> {
+    static __device__ __forceinline__ df32 get(const NfftArgs &a, int l, int t, PixRC p,
+                                               int cell) {
+        return df32(ImageOffs<double>::get(a, l, t, p, cell));
+    }
+};
+template <> struct ImageOffs<float> {
+    static __device__ __forceinline__ float get(const NfftArgs &a, int l, int t, PixRC p,
+                                                int cell) {
+        bool zero;
+        const int q = patch_pixel(a, p, __ldg(a.coff + 3 * l + t), zero);
+        const float2 xv = zero ? make_float2(0.f, 0.f) : __ldg(a.img2 + q);
+        const float2 bv = __ldg(a.cBdf + 3 * l + t);
+        const df32 u = df32(a.cAdf.x, a.cAdf.y) * df32(xv.x, xv.y) + df32(bv.x, bv.y);
+        // u hi - c is exact (c and u hi are close); the low part follows
+        float f = __fadd_rn(__fsub_rn(u.hi, (float)cell), u.lo);
+        if (f > 0.5f * a.n) f -= (float)a.n;
+        else if (f < -0.5f * a.n) f += (float)a.n;
+        return __fmaf_rn(2.f, f, -1.f);
+    }
+};
+
+// The offset of point-window `sp` (pixel at p, window l, cell c along dim
+// t): stored, or recomputed from the image.
+template <typename T>
+__device__ __forceinline__ T point_offset(const NfftArgs &a, int64_t sp, int t, int l, PixRC p,
+                                          int cell) {
+    if (a.coff) return ImageOffs<T>::get(a, l, t, p, cell);
+    return Offs<T>::get(a.yhi, a.ylo, 3 * sp + t);
+}
 
 // Index checks on the plan data the NFFT kernels read from memory (unit and
 // item records, permutation entries) and on the shared-memory rows they
@@ -442,6 +527,7 @@ __device__ __noinline__ void prefetch_unit(const NfftArgs &a, const int4 *s_item
     const int64_t total = (int64_t)a.L * a.N;
     if (first < 0 || end > total || end <= first) return;
     prefetch_l2(a.perm, 4 * first, 4 * end, 4 * total);
+    if (a.coff) return;  // coordinates from the image: no stored offsets
     prefetch_l2(a.yhi, 12 * first, 12 * end, 12 * total);
     if (lo_parts) prefetch_l2(a.ylo, 12 * first, 12 * end, 12 * total);
 }
@@ -461,7 +547,13 @@ struct SpreadSmem {
     static constexpr size_t slots_off = stage_off + kWinStageBytes;
     static constexpr size_t team_bytes = align16(sizeof(typename Num<T>::R) * NT * PWP);
     static constexpr size_t teams_off = slots_off + align16(sizeof(int) * TPB);
-    static constexpr size_t bytes = teams_off + TPB * team_bytes;
+    // FP32 with coordinates from the image: the three offsets of each
+    // thread's point (per team); none for the other arithmetics, whose
+    // larger tiles and records must leave room for 2 CTAs per SM
+    static constexpr size_t offs_bytes =
+        std::is_same<T, float>::value ? align16(sizeof(T) * 3 * NT) : 0;
+    static constexpr size_t offs_off = teams_off + TPB * team_bytes;
+    static constexpr size_t bytes = offs_off + TPB * offs_bytes;
 };
 
 // Persistent CTAs take units from a global counter (units are stored in
@@ -501,6 +593,7 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
     const int team = threadIdx.x / NT, tid = threadIdx.x % NT;
     const int seg = SPLIT == 1 ? 0 : tid / NTP;
     R *rec = reinterpret_cast<R *>(smem_raw + SM::teams_off + team * SM::team_bytes);
+    T *s_offs = reinterpret_cast<T *>(smem_raw + SM::offs_off + team * SM::offs_bytes);
     int *s_slot = reinterpret_cast<int *>(smem_raw + SM::slots_off) + team;
     Pairs<W2, NTP, PPT> pr;
     pr.init(tid % NTP);
@@ -535,12 +628,37 @@ k_spread(const NfftArgs a, const typename PolyArg<T>::type wp, const double *__r
                 ok = ok && idx_ok(pix >= 0 && pix < a.N, 3, pix, sp);
                 const T v = ok ? from_double<T>(__ldg(x + pix)) : T(0);
                 R *mine = rec + tid * PWP;
+                int lx0, ly0, lz0;  // the point's cell (for offsets from the image)
+                item_local(cur.local, lx0, ly0, lz0);
+                const PixRC prc = pix_rc(a, ok ? pix : 0);
+                const int64_t spo = ok ? sp : 0;
+                if constexpr (std::is_same<T, float>::value) {
+                    // FP32: the three offsets first, their loads in flight
+                    // together, into this thread's shared slot
+                    const T o0 = point_offset<T>(a, spo, 0, l, prc, tx0 + lx0);
+                    const T o1 = point_offset<T>(a, spo, 1, l, prc, ty0 + ly0);
+                    const T o2 = point_offset<T>(a, spo, 2, l, prc, tz0 + lz0);
+                    T *so = s_offs + 3 * tid;
+                    so[0] = o0;
+                    so[1] = o1;
+                    so[2] = o2;
+                }
                 // one dim at a time (keeps the Horner chains of the three
-                // dims out of each other's registers)
+                // dims out of each other's registers; for the FP64-accurate
+                // arithmetics the offset is formed inside the loop, which
+                // keeps the compiler from holding the staged coefficients
+                // in registers across it)
 #pragma unroll 1
                 for (int t = 0; t < 3; ++t) {
                     T w[W2];
-                    win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, ok ? 3 * sp + t : 0), w);
+                    T off;
+                    if constexpr (std::is_same<T, float>::value) {
+                        off = s_offs[3 * tid + t];
+                    } else {
+                        const int cell = t == 0 ? tx0 + lx0 : (t == 1 ? ty0 + ly0 : tz0 + lz0);
+                        off = point_offset<T>(a, spo, t, l, prc, cell);
+                    }
+                    win_weights<W2>(wp, s_coef, off, w);
                     const T sc = t == 1 ? v : T(1);
 #pragma unroll
                     for (int j = 0; j < W2; ++j) rec_put<T, W2>(mine, t, j, sc * w[j]);
@@ -738,10 +856,16 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             int lx0, ly0, lz0;
             item_local(s_items[lo].x, lx0, ly0, lz0);
             if (!idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N && lo >= 0 && lo < nit, 12, sp, lo)) continue;
+            const int i = __ldg(a.perm + sp);
+            if (!idx_ok(i >= 0 && i < a.N, 14, i, sp)) continue;
             T wxa[W2], wy[W2], wz[W2];
-            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 0), wxa);
-            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 1), wy);
-            win_weights<W2>(wp, s_coef, Offs<T>::get(a.yhi, a.ylo, 3 * (int64_t)sp + 2), wz);
+            const PixRC prc = pix_rc(a, i);
+            const T o0 = point_offset<T>(a, sp, 0, l, prc, tx0 + lx0);
+            const T o1 = point_offset<T>(a, sp, 1, l, prc, ty0 + ly0);
+            const T o2 = point_offset<T>(a, sp, 2, l, prc, tz0 + lz0);
+            win_weights<W2>(wp, s_coef, o0, wxa);
+            win_weights<W2>(wp, s_coef, o1, wy);
+            win_weights<W2>(wp, s_coef, o2, wz);
             Line<T, W2> wx, t, h;
             wx.from(wxa);
             T acc = T(0);
@@ -776,8 +900,6 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             // epilogue: one window alone finishes the pixel here; with several
             // windows the value is added into the pixel's sum, which
             // k_finish turns into the output after every window is in
-            const int i = __ldg(a.perm + sp);
-            if (!idx_ok(i >= 0 && i < a.N, 14, i, sp)) continue;
             const double val = (double)acc;
             if (ep.L > 1) {
                 atomicAdd(&ep.yacc[i], val);
@@ -1033,6 +1155,16 @@ static NfftArgs nfft_args(const Plan &P) {
     a.perm = P.perm;
     a.yhi = P.yhi;
     a.ylo = P.ylo;
+    a.img64 = P.img64;
+    a.img2 = P.img2;
+    a.n1 = P.img_n1;
+    a.n2 = P.img_n2;
+    a.pad = P.img_pad;
+    a.coff = P.coords_image ? P.coff : nullptr;
+    a.cB = P.cB;
+    a.cBdf = P.cBdf;
+    a.cA = P.cA;
+    a.cAdf = P.cAdf;
     a.n = P.n;
     a.m = P.m;
     a.L = P.L;

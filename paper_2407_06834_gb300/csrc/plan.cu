@@ -491,6 +491,18 @@ static WinSets fit_window(int m, double beta) {
     return w;
 }
 
+// (hi, lo) float pair of each pixel value (FP32 path of a plan that
+// recomputes coordinates from the image).
+__global__ void k_split_image(const double *__restrict__ img, int64_t N,
+                              float2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = img[i];
+        const float hi = (float)v;
+        out[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
 // Cell offsets of the sorted points: y = 2 (u - floor u) - 1 per dim (u the
 // grid coordinate of k_cell_keys), as a float and the float remainder.
 __global__ void k_offsets(const int *__restrict__ perm, const double *__restrict__ u, int64_t N,
@@ -1018,11 +1030,57 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
         k_emit_items<<<gb, 256, 0, s>>>(hist, start, ioff, ncells, n, P.kmax, P.items);
         NLH_CHECK_LAUNCH();
         build_units(P, s);
-        // cell offsets in sorted order (the low parts for the FP64-accurate paths)
-        P.yhi = P.alloc<float>((size_t)LN * 3);
-        if (P.precision & 5) P.ylo = P.alloc<float>((size_t)LN * 3);
-        k_offsets<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.yhi, P.ylo);
-        NLH_CHECK_LAUNCH();
+        if (desc.image) {
+            // coordinates from the image: its copy, the patch offsets and the
+            // torus map of the plan's windows (u = A x + B, the map
+            // (s (x - c) + 0.5) n of k_cell_keys expanded)
+            const int Pw = 2 * desc.patch_radius + 1;
+            P.coords_image = 1;
+            P.img_n1 = desc.image_n1;
+            P.img_n2 = desc.image_n2;
+            P.img_pad = desc.patch_pad;
+            if (P.precision & 5) {
+                P.img64 = P.alloc<double>(N);
+                NLH_CUDA(cudaMemcpyAsync(P.img64, desc.image, sizeof(double) * N,
+                                         cudaMemcpyDeviceToDevice, s));
+            }
+            if (P.precision & 2) {
+                P.img2 = P.alloc<float2>(N);
+                k_split_image<<<gb, 256, 0, s>>>(desc.image, N, P.img2);
+                NLH_CHECK_LAUNCH();
+            }
+            std::vector<int4> off(3 * L);
+            std::vector<double> hB(3 * L);
+            std::vector<float2> hBdf(3 * L);
+            P.cA = P.scale * n;
+            P.cAdf = make_float2((float)P.cA, (float)(P.cA - (double)(float)P.cA));
+            for (int l = 0; l < L; ++l)
+                for (int t = 0; t < 3; ++t) {
+                    const int k = P.windows[3 * (wf + l) + t];
+                    off[3 * l + t] = k < 0 ? make_int4(1, 0, 0, 0)
+                                           : make_int4(0, k / Pw - desc.patch_radius,
+                                                       k % Pw - desc.patch_radius, 0);
+                    const double B = (0.5 - P.scale * center[3 * (wf + l) + t]) * n;
+                    hB[3 * l + t] = B;
+                    hBdf[3 * l + t] = make_float2((float)B, (float)(B - (double)(float)B));
+                }
+            P.coff = P.alloc<int4>(3 * L);
+            P.cB = P.alloc<double>(3 * L);
+            P.cBdf = P.alloc<float2>(3 * L);
+            NLH_CUDA(cudaMemcpyAsync(P.coff, off.data(), sizeof(int4) * 3 * L,
+                                     cudaMemcpyHostToDevice, s));
+            NLH_CUDA(cudaMemcpyAsync(P.cB, hB.data(), sizeof(double) * 3 * L,
+                                     cudaMemcpyHostToDevice, s));
+            NLH_CUDA(cudaMemcpyAsync(P.cBdf, hBdf.data(), sizeof(float2) * 3 * L,
+                                     cudaMemcpyHostToDevice, s));
+            NLH_CUDA(cudaStreamSynchronize(s));  // the host tables are locals
+        } else {
+            // cell offsets in sorted order (the low parts for the FP64-accurate paths)
+            P.yhi = P.alloc<float>((size_t)LN * 3);
+            if (P.precision & 5) P.ylo = P.alloc<float>((size_t)LN * 3);
+            k_offsets<<<gb, 256, 0, s>>>(P.perm, u, N, L, P.yhi, P.ylo);
+            NLH_CHECK_LAUNCH();
+        }
         P.occupied = occ;
     } catch (...) {
         for (void *ptr : tmp) cudaFreeAsync(ptr, s);
@@ -1134,6 +1192,15 @@ nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc, const doubl
                     d.precision);
         NLH_REQUIRE(d.torus_fill >= 0.0 && d.torus_fill < 1.0, "nlh_plan_create: torus_fill=%g",
                     d.torus_fill);
+        if (d.image)
+            NLH_REQUIRE(d.image_n1 >= 1 && d.image_n2 >= 1 &&
+                            (int64_t)d.image_n1 * d.image_n2 == d.N && d.patch_radius >= 0 &&
+                            (d.patch_pad == 0 || d.patch_pad == 1) &&
+                            (int64_t)(2 * d.patch_radius + 1) * (2 * d.patch_radius + 1) == d.D,
+                        "nlh_plan_create: image %dx%d, radius %d, pad %d do not match N=%lld, "
+                        "D=%d",
+                        d.image_n1, d.image_n2, d.patch_radius, d.patch_pad, (long long)d.N,
+                        d.D);
         NLH_REQUIRE(d.window_count >= 0 && d.window_first >= 0 &&
                         (d.window_count == 0 || d.window_first + d.window_count <= d.L),
                     "nlh_plan_create: window range [%d, %d + %d) outside the %d windows",
@@ -1215,6 +1282,7 @@ nlh_status nlh_plan_get_info(nlh_plan plan, nlh_plan_info *info) {
         info->unit_points = plan->unit_points;
         for (int a = 0; a < 3; ++a) info->team[a] = plan->team[a];
         info->window_first = plan->window_first;
+        info->coords_from_image = plan->coords_image;
         info->window_count = plan->L;
         info->occupied_cells = plan->occupied;
         error_estimates(plan->sigma, plan->R, plan->fill, plan->M, &info->est_trunc_err,

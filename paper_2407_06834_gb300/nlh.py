@@ -40,7 +40,8 @@ class PlanDesc(C.Structure):
                 ("torus_fill", C.c_double), ("max_items_pts", C.c_int),
                 ("nfft_eps", C.c_double), ("unit_points", C.c_int), ("team", C.c_int * 3),
                 ("window_first", C.c_int), ("window_count", C.c_int), ("reduce", REDUCE_FN),
-                ("reduce_ctx", C.c_void_p)]
+                ("reduce_ctx", C.c_void_p), ("image", C.c_void_p), ("image_n1", C.c_int),
+                ("image_n2", C.c_int), ("patch_radius", C.c_int), ("patch_pad", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -51,7 +52,8 @@ class PlanInfo(C.Structure):
                 ("occupied_cells", C.c_int64), ("est_trunc_err", C.c_double),
                 ("est_alias_err", C.c_double), ("device_bytes", C.c_int64),
                 ("n_units", C.c_int64), ("max_items_pts", C.c_int), ("unit_points", C.c_int),
-                ("team", C.c_int * 3), ("window_first", C.c_int), ("window_count", C.c_int)]
+                ("team", C.c_int * 3), ("window_first", C.c_int), ("window_count", C.c_int),
+                ("coords_from_image", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -266,7 +268,9 @@ class Plan:
     def __init__(self, features, windows, sigma: float, M: int = 32, n_os: int = 64, m: int = 4,
                  precision: int = 3, torus_fill: float = 0.0, max_items_pts: int = 0,
                  nfft_eps: float = 0.0, unit_points: int = 0, autotune: bool = False,
-                 team=None, window_range=None, reduce=None, stream=None):
+                 team=None, window_range=None, reduce=None, image=None, stream=None):
+        """image: None, or (image, radius, pad) when the features are that
+        image's patches; the plan then recomputes coordinates from it."""
         lib = load()
         N, D = features.shape
         win = np.ascontiguousarray(np.asarray(windows, dtype=np.int32).reshape(-1, 3))
@@ -297,6 +301,13 @@ class Plan:
                         window_count=int(wc),
                         reduce=self._reduce if self._reduce is not None else REDUCE_FN(),
                         reduce_ctx=None)
+        if image is not None:
+            img, radius, pad = image
+            n1, n2 = img.shape
+            desc.image = _dptr(img, n1 * n2)
+            desc.image_n1, desc.image_n2 = int(n1), int(n2)
+            desc.patch_radius = int(radius)
+            desc.patch_pad = 1 if pad == "reflect" else 0
         h = C.c_void_p()
         _check(lib.nlh_plan_create(C.byref(h), C.byref(desc), _dptr(features),
                                    _stream_ptr(stream)))
@@ -319,9 +330,14 @@ class Plan:
 
     @classmethod
     def from_image(cls, image, radius: int, windows, sigma: float, pad: str = "reflect",
-                   **kw):
+                   coords_from_image: bool = False, **kw):
+        """Plan of the image's patch features.  coords_from_image: the NFFT
+        kernels recompute the points' coordinates from the image instead of
+        reading stored offsets (less memory and DRAM traffic, slower)."""
         feats = patch_features(image, radius, pad, kw.get("stream"))
-        return cls(feats, windows, sigma, **kw)
+        img = image.contiguous() if coords_from_image else None
+        return cls(feats, windows, sigma, image=(img, radius, pad) if coords_from_image else None,
+                   **kw)
 
     @property
     def handle(self) -> int:

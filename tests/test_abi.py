@@ -48,12 +48,13 @@ def test_version_and_error_without_gpu():
 def test_struct_layouts_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "nlh_net.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(nlh_plan_desc),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(nlh_plan_desc),'
                    ' sizeof(nlh_plan_info), sizeof(nlh_solve_opts), sizeof(nlh_solve_info),'
                    ' offsetof(nlh_plan_desc, torus_fill), offsetof(nlh_solve_opts, x0), offsetof(nlh_solve_opts, x0_check), offsetof(nlh_solve_opts, precond),'
                    ' sizeof(nlh_net_batch), offsetof(nlh_net_batch, beta), offsetof(nlh_solve_info, x0_rejected),'
                    ' offsetof(nlh_plan_desc, window_first), offsetof(nlh_plan_desc, reduce), offsetof(nlh_plan_desc, reduce_ctx),'
-                   ' offsetof(nlh_plan_info, window_count));'
+                   ' offsetof(nlh_plan_info, window_count), offsetof(nlh_plan_desc, image),'
+                   ' offsetof(nlh_plan_desc, patch_pad), offsetof(nlh_plan_info, coords_from_image));'
                    ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -65,4 +66,6 @@ def test_struct_layouts_match_c(tmp_path):
                    nlh.SolveOpts.x0.offset, nlh.SolveOpts.x0_check.offset, nlh.SolveOpts.precond.offset, C.sizeof(nlh.NetBatch),
                    nlh.NetBatch.beta.offset, nlh.SolveInfo.x0_rejected.offset,
                    nlh.PlanDesc.window_first.offset, nlh.PlanDesc.reduce.offset,
-                   nlh.PlanDesc.reduce_ctx.offset, nlh.PlanInfo.window_count.offset]
+                   nlh.PlanDesc.reduce_ctx.offset, nlh.PlanInfo.window_count.offset,
+                   nlh.PlanDesc.image.offset, nlh.PlanDesc.patch_pad.offset,
+                   nlh.PlanInfo.coords_from_image.offset]

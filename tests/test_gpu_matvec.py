@@ -130,6 +130,39 @@ def test_fp32_configured_5x5_windows_match_truncated_fourier_sum():
     assert relmax(y32, ref) < 10 * est * scale + 1e-5
 
 
+@pytest.mark.parametrize("radius,pad,shape", [(1, "reflect", (33, 29)), (2, "zero", (20, 24)),
+                                              (2, "reflect", (1, 40))])
+def test_image_coordinates_match_stored_offsets(radius, pad, shape):
+    """A plan that recomputes the points' coordinates from the image
+    against one that stores each point's cell offsets (the default): the same operator in every arithmetic (FP64 and double-float
+    coordinates agree to ~1e-14, the FP32 path's to FP32 rounding), with
+    less device memory; reflect and zero padding, a one-row image."""
+    img = image(*shape, seed=radius)
+    win = raster_windows(radius)
+    f = cuda(img)
+    kw = dict(pad=pad, M=32, n_os=64, m=4, precision=7)
+    a = nlh.Plan.from_image(f, radius, win, SIGMA, coords_from_image=True, **kw)
+    b = nlh.Plan.from_image(f, radius, win, SIGMA, **kw)
+    ia, ib = a.info(), b.info()
+    assert ia["coords_from_image"] == 1 and ib["coords_from_image"] == 0
+    assert ia["device_bytes"] < ib["device_bytes"]
+    assert ia["n_items"] == ib["n_items"] and ia["scale"] == ib["scale"]
+    v = cuda(random_vector(img.size, 9))
+    for prec, tol in ((nlh.NLH_FP64, 1e-12), (nlh.NLH_DF32, 1e-12), (nlh.NLH_FP32, 1e-5)):
+        for op in (0, 2):
+            ya = host(a.matvec(v, op=op, alpha=0.5, precision=prec))
+            yb = host(b.matvec(v, op=op, alpha=0.5, precision=prec))
+            assert relmax(ya, yb) < tol, (prec, op, relmax(ya, yb))
+    assert relmax(host(a.degrees()), host(b.degrees())) < 1e-12
+    coords = orc.image_coords(img, radius, win, pad)
+    ref = orc.gamma_full_matvec(coords, SIGMA, host(v))
+    y32 = host(a.matvec(v, op=0, precision=nlh.NLH_FP32))
+    y64 = host(a.matvec(v, op=0, precision=nlh.NLH_FP64))
+    assert relmax(y32, y64) < 1e-5
+    est = max(ia["est_trunc_err"], ia["est_alias_err"])
+    assert relmax(y64, ref) < 10 * est * np.abs(host(v)).sum() / np.max(np.abs(ref)) + 1e-6
+
+
 def test_fp64_ragged_image_tight(img64):
     img = image(37, 53, seed=3)
     coords = orc.image_coords(img, 1, raster_windows(1))
