@@ -54,12 +54,16 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch of the NFFT kernels, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 2048 x 2048
-# workload, keyed by a hash of the kernel sources at capture time: when the
+# workload per coordinate mode (stored cell offsets, or recomputed from the
+# image), keyed by a hash of the kernel sources at capture time: when the
 # sources change, the figures no longer describe the kernels and the bench
 # reports traffic null.
-NCU_TRAFFIC = {"sources_sha16": "00e9d02b310c3708", "workload": "img2048",
-               "bytes_per_launch": {"spread32": 776477440, "interp32": 725344512,
-                                    "spread_df32": 1420672256, "interp_df32": 1300517376}}
+NCU_TRAFFIC = {"sources_sha16": "8145e6bfd9ae742d", "workload": "img2048",
+               "bytes_per_launch": {
+                   "stored": {"spread32": 779469056, "interp32": 726096384,
+                              "spread_df32": 1429140736, "interp_df32": 1317797888},
+                   "image": {"spread32": 835555072, "interp32": 430690048,
+                             "spread_df32": 1062569216, "interp_df32": 889667840}}}
 
 
 def kernel_sources_sha16() -> str:
@@ -318,9 +322,8 @@ def roofline(prof, wl, coords="stored"):
                   + wl.L * wl.n_os ** 3 * float(gbytes))
     traffic, tnote = None, None
     sha = kernel_sources_sha16()
-    if (NCU_TRAFFIC.get("sources_sha16") == sha and NCU_TRAFFIC.get("workload") == wl.name
-            and NCU_TRAFFIC.get("coords", "stored") == coords):
-        traffic = NCU_TRAFFIC["bytes_per_launch"].get(dom)
+    if NCU_TRAFFIC.get("sources_sha16") == sha and NCU_TRAFFIC.get("workload") == wl.name:
+        traffic = NCU_TRAFFIC["bytes_per_launch"].get(coords, {}).get(dom)
         tnote = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, same kernel sources"
     else:
         tnote = ("no ncu capture of the current kernel sources for this workload "
