@@ -58,12 +58,12 @@ FP64_PEAK_TFLOPS = 1.25
 # image), keyed by a hash of the kernel sources at capture time: when the
 # sources change, the figures no longer describe the kernels and the bench
 # reports traffic null.
-NCU_TRAFFIC = {"sources_sha16": "8145e6bfd9ae742d", "workload": "img2048",
+NCU_TRAFFIC = {"sources_sha16": "a7339184cdc16f57", "workload": "img2048",
                "bytes_per_launch": {
-                   "stored": {"spread32": 779469056, "interp32": 726096384,
-                              "spread_df32": 1429140736, "interp_df32": 1317797888},
-                   "image": {"spread32": 835555072, "interp32": 430690048,
-                             "spread_df32": 1062569216, "interp_df32": 889667840}}}
+                   "stored": {"spread32": 779503616, "interp32": 725157632,
+                              "spread_df32": 1429697792, "interp_df32": 1291868160},
+                   "image": {"spread32": 836495872, "interp32": 430536448,
+                             "spread_df32": 1062306816, "interp_df32": 738729728}}}
 
 
 def kernel_sources_sha16() -> str:
