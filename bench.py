@@ -58,12 +58,12 @@ FP64_PEAK_TFLOPS = 1.25
 # image), keyed by a hash of the kernel sources at capture time: when the
 # sources change, the figures no longer describe the kernels and the bench
 # reports traffic null.
-NCU_TRAFFIC = {"sources_sha16": "a7339184cdc16f57", "workload": "img2048",
+NCU_TRAFFIC = {"sources_sha16": "ac4cd03fbe9fd181", "workload": "img2048",
                "bytes_per_launch": {
-                   "stored": {"spread32": 779503616, "interp32": 725157632,
-                              "spread_df32": 1429697792, "interp_df32": 1291868160},
-                   "image": {"spread32": 836495872, "interp32": 430536448,
-                             "spread_df32": 1062306816, "interp_df32": 738729728}}}
+                   "stored": {"spread32": 781678848, "interp32": 725080320,
+                              "spread_df32": 1431764992, "interp_df32": 1292663296},
+                   "image": {"spread32": 839603456, "interp32": 429899520,
+                             "spread_df32": 1061158400, "interp_df32": 735371776}}}
 
 
 def kernel_sources_sha16() -> str:
