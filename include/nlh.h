@@ -90,7 +90,10 @@ typedef struct {
     int max_items_pts;      /* points per work item, 0 = default (64)        */
     double nfft_eps;        /* > 0: choose torus_fill, M and n_os (and m when
                                m = 0) so that the a-priori per-dim alias,
-                               truncation and window errors are <= nfft_eps;
+                               truncation and window errors are <= nfft_eps,
+                               taking among the admissible grid sizes the one
+                               with the least estimated work (a smaller grid
+                               and a larger m for few points per cell);
                                M, n_os, torus_fill are then ignored          */
     int unit_points;        /* points per work unit (one CTA), 0 = 512       */
     int team[3];            /* launch shape of the spreading kernel per NFFT

@@ -827,8 +827,20 @@ static double erfc_inv(double y) {
 // truncation erfc(pi sigma_s (M/2 - 1)) <= eps the bandwidth M, the grid is
 // the next power of two >= 2M (oversampling >= 2, at most 256), and the
 // Kaiser-Bessel window error ~ exp(-4.44 m) at oversampling 2 gives m.
-static void auto_params(double sigma, double R, double eps, int m_in, int &M, int &n_os, int &m,
-                        double &fill) {
+// NFFT parameters for a per-dim error target eps (nlh_plan_desc.nfft_eps):
+// the torus fill and bandwidth M from the alias and truncation bounds, then
+// among the grid sizes n_os (powers of two, oversampling n_os / M >= 1.25)
+// the one with the least estimated work.  The Kaiser-Bessel window with
+// oversampling r = n_os / M has its error decay like
+// exp(-2 pi m sqrt(1 - 1/r)) (Sec. 3; for r = 2 that is exp(-4.44 m)), which
+// fixes the smallest cutoff m for each n_os; the work of a matvec is about
+// N L (2m)^3 stencil updates against L n_os^3 convolved grid cells, whose
+// measured relative cost is ~250 updates per cell (x 1.5 for n_os = 256,
+// whose axis passes run separately).  Small images (few points per grid
+// cell) thus take a smaller grid and a larger cutoff.  Odd cutoffs from 5 up
+// are rounded up to the even ones whose stencil widths have tuned kernels.
+static void auto_params(double sigma, double R, double eps, int m_in, int64_t NL, int L, int &M,
+                        int &n_os, int &m, double &fill) {
     const double a = std::sqrt(std::log(2.0 / eps));
     fill = std::min(0.9, 1.0 / (1.0 + a * sigma / R));
     const double ss = sigma * fill / R;
@@ -836,10 +848,31 @@ static void auto_params(double sigma, double R, double eps, int m_in, int &M, in
     M = 2 * (int)std::ceil(half);
     if (M < 8) M = 8;
     if (M > 128) M = 128;
-    n_os = 32;
-    while (n_os < 2 * M && n_os < 256) n_os *= 2;
-    m = m_in > 0 ? m_in : std::min(8, std::max(2, (int)std::ceil(std::log(1.0 / eps) / 4.44)));
-    if (2 * m >= n_os) m = n_os / 2 - 1;
+    double best = INFINITY;
+    n_os = 0;
+    m = 0;
+    for (int n = 32; n <= 256; n *= 2) {
+        const double r = (double)n / M;
+        if (r < 1.25) continue;
+        int mm = m_in > 0 ? m_in
+                          : (int)std::ceil(std::log(1.0 / eps) / (2.0 * M_PI * std::sqrt(1.0 - 1.0 / r)));
+        mm = std::min(8, std::max(2, mm));
+        if (m_in <= 0 && mm >= 5 && (mm & 1)) ++mm;  // 2m = 12, 16 have the tuned kernel shapes
+        if (2 * mm >= n) continue;
+        const double w = 2.0 * mm;
+        const double cost = (double)NL * w * w * w +
+                            250.0 * (n == 256 ? 1.5 : 1.0) * L * (double)n * n * n;
+        if (cost < best) {
+            best = cost;
+            n_os = n;
+            m = mm;
+        }
+    }
+    if (n_os == 0) {  // M = 128 with no n_os >= 1.25 M below 256: the largest grid
+        n_os = 256;
+        m = m_in > 0 ? m_in : std::min(8, std::max(2, (int)std::ceil(std::log(1.0 / eps) / 4.44)));
+        if (2 * m >= n_os) m = n_os / 2 - 1;
+    }
 }
 
 static double choose_fill(double sigma, double R, int M) {
@@ -955,7 +988,8 @@ static void build_plan(Plan &P, const nlh_plan_desc &desc, const double *feature
     if (!(R > 0.0)) R = 1.0;
     P.R = R;
     if (desc.nfft_eps > 0.0) {
-        auto_params(P.sigma, R, desc.nfft_eps, desc.m, P.M, P.n, P.m, P.fill);
+        auto_params(P.sigma, R, desc.nfft_eps, desc.m, (int64_t)L * N, L, P.M, P.n, P.m,
+                    P.fill);
         P.W2 = 2 * P.m;
     } else {
         P.fill = desc.torus_fill > 0.0 ? desc.torus_fill : choose_fill(P.sigma, R, P.M);
