@@ -33,6 +33,10 @@ def test_auto_parameters_meet_target(sigma):
     P = _auto_plan(img, sigma, precision=7)
     info = P.info()
     assert max(info["est_trunc_err"], info["est_alias_err"]) <= 1e-7 * 1.0001
+    # few points per grid cell: the work-based choice takes the smaller grid
+    # (with at least 1.25x oversampling) and a cutoff that keeps the error
+    assert info["n_os"] >= 1.25 * info["M"] and 2 * info["m"] < info["n_os"]
+    assert info["n_os"] <= 128 or 1.25 * info["M"] > 128, info
     coords = orc.image_coords(img, 1, raster_windows(1))
     v = random_vector(img.size, 31)
     ref = orc.gamma_full_matvec(coords, sigma, v)
