@@ -513,6 +513,9 @@ def run_ours(args):
                                    if sharded else ("replicas" if world > 1 else "single GPU")),
                    "torus_fill": pinfo["torus_fill"], "work_items": pinfo["n_items"],
                    "plan_device_bytes": pinfo["device_bytes"],
+                   "tiling": {"max_items_pts": pinfo["max_items_pts"],
+                              "unit_points": pinfo["unit_points"], "units": pinfo["n_units"],
+                              "team_fp64_fp32_df32": pinfo["team"]},
                    "coordinates": ("recomputed from the image" if args.coords == "image"
                                    else "stored cell offsets per point-window")},
         "solve_seconds": solve_s,
