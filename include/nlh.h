@@ -141,8 +141,10 @@ typedef struct {
  * the affine map onto the torus x~ = s (x - c_l) with c_l the per-window
  * midrange and s = torus_fill / (largest per-dim range), the sort of the
  * points by grid cell with each point's offset inside its cell (the window
- * weights are evaluated from it in every matvec), the Fourier multiplier
- * tables and the degrees d = Gamma_full 1 (one matvec per precision built).
+ * weights are evaluated from it in every matvec; with desc->image the
+ * offsets are recomputed from the image instead of stored), the Fourier
+ * multiplier tables and the degrees d = Gamma_full 1 (one matvec per
+ * precision built).
  *   features  device, N x D FP64 row-major (e.g. from nlh_patch_features).
  * Synchronises `stream`.  Errors: NLH_ERR_ARG, NLH_ERR_OOM, NLH_ERR_CUDA. */
 nlh_status nlh_plan_create(nlh_plan *out, const nlh_plan_desc *desc,
