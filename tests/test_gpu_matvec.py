@@ -163,6 +163,57 @@ def test_image_coordinates_match_stored_offsets(radius, pad, shape):
     assert relmax(y64, ref) < 10 * est * np.abs(host(v)).sum() / np.max(np.abs(ref)) + 1e-6
 
 
+@pytest.mark.parametrize("M,n_os,m,tol", [(16, 32, 3, 1e-4), (64, 128, 5, 1e-6),
+                                          (100, 256, 4, 1e-6)])
+def test_grid_sizes_match_truncated_fourier_sum(M, n_os, m, tol):
+    """Every grid size of the convolution: n_os = 32 and 128 (x and y in one
+    plane kernel, then z) and 256 (three axis passes), against the oracle's
+    truncated-Fourier kernel sum at the plan's torus map (the window error
+    of the NFFT only, bounded by tol for the cutoff and oversampling), the
+    double-float path against FP64 and FP32 within 1e-5."""
+    img = image(20, 24, seed=M)
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    P = make_plan(img, M=M, n_os=n_os, m=m, precision=7)
+    info = P.info()
+    assert (info["n_os"], info["M"], info["m"]) == (n_os, M, m)
+    tc, s = orc.torus_map(coords, info["torus_fill"])
+    v = random_vector(img.size, 40)
+    trig = orc.trig_full_matvec(tc, s * SIGMA, M, v)
+    y64 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP64))
+    ydf = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_DF32))
+    y32 = host(P.matvec(cuda(v), op=0, precision=nlh.NLH_FP32))
+    assert relmax(y64, trig) < tol, relmax(y64, trig)
+    assert relmax(ydf, y64) < 1e-12, relmax(ydf, y64)
+    assert relmax(y32, y64) < 1e-5, relmax(y32, y64)
+    ones = cuda(np.ones(img.size))
+    for prec, t in ((nlh.NLH_FP64, 1e-12), (nlh.NLH_DF32, 1e-11), (nlh.NLH_FP32, 1e-5)):
+        l1 = host(P.matvec(ones, op=1, precision=prec))
+        assert np.abs(l1).max() < t * host(P.degrees()).max(), (prec, np.abs(l1).max())
+
+
+def test_two_pixel_image():
+    """The smallest plan (N = 2, one row of two pixels, reflect padding):
+    every arithmetic against the direct sum at tight parameters, and a
+    solve certified by the direct operator.  The two points are close
+    against sigma, so the torus fill is chosen by the plan (a fixed fill of
+    0.5 would make sigma on the torus ~1 and the periodic copies overlap;
+    the plan's alias estimate reports that)."""
+    img = image(1, 2, seed=9)
+    coords = orc.image_coords(img, 1, raster_windows(1))
+    P = make_plan(img, M=64, n_os=128, m=8, precision=7)
+    info = P.info()
+    assert max(info["est_trunc_err"], info["est_alias_err"]) < 1e-12, info
+    v = random_vector(2, 41)
+    ref = orc.gamma_full_matvec(coords, SIGMA, v)
+    for prec, tol in ((nlh.NLH_FP64, 1e-10), (nlh.NLH_DF32, 1e-10), (nlh.NLH_FP32, 1e-5)):
+        y = host(P.matvec(cuda(v), op=0, precision=prec))
+        assert relmax(y, ref) < tol, (prec, relmax(y, ref))
+    b = 0.5 * img.ravel()
+    res = P.solve(0.5, cuda(b), tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    r = b - orc.A_apply(coords, SIGMA, 0.5, 1.0, host(res.u))
+    assert res.info["status"] == 0 and np.linalg.norm(r) / np.linalg.norm(b) <= 2e-6
+
+
 def test_fp64_ragged_image_tight(img64):
     img = image(37, 53, seed=3)
     coords = orc.image_coords(img, 1, raster_windows(1))
