@@ -1022,18 +1022,7 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                     "nlh_solve_batched: arith=%d", opts->arith);
         NLH_REQUIRE(opts->x0 == nullptr && opts->diag_scale == nullptr,
                     "nlh_solve_batched: x0 and diag_scale are per-solve; use nlh_solve");
-        // one graph for the whole batch, unless a plan's matvecs call a
-        // reduce callback (its collective is enqueued per call, which a
-        // captured graph would not repeat): those run the round-based path
         bool any_reduce = false;
-        for (int i = 0; i < nsolves; ++i) {
-            NLH_REQUIRE(plans[i] && b[i] && u[i], "nlh_solve_batched: NULL in solve %d", i);
-            any_reduce = any_reduce || plans[i]->reduce_fn != nullptr;
-        }
-        if (!any_reduce) return solve_batched_graph(nsolves, plans, alphas, b, u, opts, infos,
-                                                    (cudaStream_t)stream, t0);
-        // group the solves by plan (a plan's workspace serves one solve at a time)
-        std::map<nlh_plan, std::vector<int>> by_plan;
         for (int i = 0; i < nsolves; ++i) {
             NLH_REQUIRE(plans[i] && b[i] && u[i], "nlh_solve_batched: NULL in solve %d", i);
             NLH_REQUIRE(alphas[i] > 0.0 && std::isfinite(alphas[i]),
@@ -1046,8 +1035,16 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
             else
                 NLH_REQUIRE((pr & 2) && (pr & 5),
                             "nlh_solve_batched: plan %d lacks the FP32 or an accurate path", i);
-            by_plan[plans[i]].push_back(i);
+            any_reduce = any_reduce || plans[i]->reduce_fn != nullptr;
         }
+        // one graph for the whole batch, unless a plan's matvecs call a
+        // reduce callback (its collective is enqueued per call, which a
+        // captured graph would not repeat): those run the round-based path
+        if (!any_reduce) return solve_batched_graph(nsolves, plans, alphas, b, u, opts, infos,
+                                                    (cudaStream_t)stream, t0);
+        // group the solves by plan (a plan's workspace serves one solve at a time)
+        std::map<nlh_plan, std::vector<int>> by_plan;
+        for (int i = 0; i < nsolves; ++i) by_plan[plans[i]].push_back(i);
         std::vector<std::vector<int>> groups;
         for (auto &kv : by_plan) groups.push_back(kv.second);
         const int ns = std::min<int>((int)groups.size(), 16);
