@@ -150,31 +150,4 @@ __device__ __forceinline__ void pk_df_axpy(unsigned long long &h, unsigned long 
     h = s;
 }
 
-// The same update for an accumulator that carries a power-of-two offset
-// B >= 4 max |partial sum| in its high words (h starts at B): every partial
-// sum then stays in [3B/4, 5B/4] and exceeds each product in magnitude, so
-// Fast2Sum (Dekker 1971; 3 operations) recovers the addition's rounding
-// error exactly instead of TwoSum's 6.  The caller subtracts B (exactly,
-// Sterbenz) when the sum is complete.
-__device__ __forceinline__ void pk_df_axpy_biased(unsigned long long &h, unsigned long long &l,
-                                                  unsigned long long ah, unsigned long long nah,
-                                                  unsigned long long nal, unsigned long long wh,
-                                                  unsigned long long wl) {
-    unsigned long long p = pk_mul(ah, wh);
-    unsigned long long e = pk_fma(nah, wh, p);
-    e = pk_fma(nah, wl, e);
-    e = pk_fma(nal, wh, e);
-    const unsigned long long s = pk_add(h, p);
-    const unsigned long long t = pk_sub(p, pk_sub(s, h));
-    l = pk_add(l, pk_sub(t, e));
-    h = s;
-}
-
-// The smallest power of two >= x (x > 0, finite, normal).
-__device__ __forceinline__ float pow2_ceil(float x) {
-    unsigned b = __float_as_uint(x);
-    if (b & 0x7fffffu) b = (b + 0x800000u) & 0x7f800000u;
-    return __uint_as_float(b & 0x7f800000u);
-}
-
 }  // namespace nlh

@@ -301,26 +301,6 @@ template <int W2> struct Line<df32, W2> {
 #pragma unroll
         for (int a = 0; a < W2 / 2; ++a) pk_df_axpy(h[a], l[a], sh, nsh, nsl, w.h[a], w.l[a]);
     }
-    // an accumulator offset by the power of two B (see pk_df_axpy_biased)
-    __device__ __forceinline__ void bias(float B) {
-        const unsigned long long bb = pk_dup(B);
-#pragma unroll
-        for (int a = 0; a < W2 / 2; ++a) {
-            h[a] = bb;
-            l[a] = 0ull;
-        }
-    }
-    __device__ __forceinline__ void axpy_biased(df32 s, const Line &w) {  // this += s w
-        const unsigned long long sh = pk_dup(s.hi), nsh = pk_dup(-s.hi), nsl = pk_dup(-s.lo);
-#pragma unroll
-        for (int a = 0; a < W2 / 2; ++a)
-            pk_df_axpy_biased(h[a], l[a], sh, nsh, nsl, w.h[a], w.l[a]);
-    }
-    __device__ __forceinline__ void unbias(float B) {  // exact: the sums lie in [B/2, 2B]
-        const unsigned long long bb = pk_dup(B);
-#pragma unroll
-        for (int a = 0; a < W2 / 2; ++a) h[a] = pk_sub(h[a], bb);
-    }
     __device__ __forceinline__ df32 dot(const Line &x) const {  // sum_a this[a] x[a]
         unsigned long long sh = 0ull, sl = 0ull;
         const unsigned long long zero = 0ull;
@@ -823,7 +803,6 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
     T *s_wy = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_coef) + kWinStageBytes);
     T *s_wz = s_wy + W2 * NTH;
     __shared__ double sh_red[33];
-    __shared__ unsigned s_gmax;  // double-float: max |G| of the staged tile (float bits)
     if (done && *done) return;
     if constexpr (!std::is_same<T, float>::value) win_stage(a.wstage, s_coef);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -832,10 +811,7 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
     double part = 0.0;
     while (true) {
         __syncthreads();  // previous unit done with the tile
-        if (threadIdx.x == 0) {
-            s_ctl[0] = atomicAdd(&a.unit_ctr[1], 1);
-            s_gmax = 0u;
-        }
+        if (threadIdx.x == 0) s_ctl[0] = atomicAdd(&a.unit_ctr[1], 1);
         __syncthreads();
         const int uidx = s_ctl[0];
         if (uidx >= *a.n_units) break;
@@ -848,7 +824,6 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
         const G *g = grid + (int64_t)l * a.n * a.n * a.n;
         {
             constexpr int UNR = 8;
-            float gmax = 0.f;
             for (int base = threadIdx.x; base < E3; base += blockDim.x * UNR) {
                 G vals[UNR];
 #pragma unroll
@@ -861,7 +836,6 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
                                   gz = (tz0 - m + 1 + ez) & msk;
                         vals[u] = __ldg(&g[((int64_t)gz * a.n + gy) * a.n + gx]);
                     }
-                    if constexpr (Num<T>::kParts == 2) gmax = fmaxf(gmax, (float)fabs((double)vals[u]));
                 }
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
@@ -877,10 +851,6 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
                         }
                     }
                 }
-            }
-            if constexpr (Num<T>::kParts == 2) {
-                for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-                if ((threadIdx.x & 31) == 0) atomicMax(&s_gmax, __float_as_uint(gmax));
             }
         }
         __syncthreads();
@@ -924,19 +894,9 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             // the plain tile)
             const int cx = NC == 1 ? 0 : (lx0 & 3);
             const T *scopy = S + cx * COPY;
-            // double-float: the y sums of each z carry the power-of-two offset
-            // Bp >= 4 max |G| sum |wy| (Fast2Sum instead of TwoSum)
-            float Bp = 0.f;
-            if constexpr (Num<T>::kParts == 2) {
-                float sw = 0.f;
-#pragma unroll
-                for (int k = 0; k < W2; ++k) sw += fabsf(wy[k].hi);
-                Bp = pow2_ceil(fmaxf(4.f * __uint_as_float(s_gmax) * sw * 1.0001f, 1e-30f));
-            }
 #pragma unroll 1
             for (int z = 0; z < W2; ++z) {
-                if constexpr (Num<T>::kParts == 2) t.bias(Bp);
-                else t.zero();
+                t.zero();
                 const int so = ((lz0 + z) * E + ly0) * EP + lx0 - cx;
                 if (!idx_ok(so >= 0 && so + (W2 - 1) * EP + W2 - 1 < COPY, 13, so, COPY)) break;
                 const T *srow = scopy + so;
@@ -947,11 +907,9 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
                     } else {
                         h.load_cells_v4(srow + y * EP);
                     }
-                    if constexpr (Num<T>::kParts == 2) t.axpy_biased(s_wy[y * NTH + threadIdx.x], h);
-                    else if constexpr (SW) t.axpy(s_wy[y * NTH + threadIdx.x], h);
+                    if constexpr (SW) t.axpy(s_wy[y * NTH + threadIdx.x], h);
                     else t.axpy(wy[y], h);
                 }
-                if constexpr (Num<T>::kParts == 2) t.unbias(Bp);
                 T wzz;
                 if constexpr (SW) {
                     wzz = s_wz[z * NTH + threadIdx.x];

@@ -204,3 +204,29 @@ def test_retile_and_team_after_a_solve_keep_the_plan_consistent():
             d = host(P.degrees())
             assert np.abs(l1).max() <= (1e-4 if prec == nlh.NLH_FP32 else 1e-9) * d.max()
     P.close()
+
+
+def test_mixed_solve_reaches_tol_when_degrees_dwarf_alpha():
+    """The hardest pair of the (sigma, alpha) sweep: sigma = 1 on an 896 x 896
+    image, alpha = 0.01.  The degrees are of order N (a wide Gaussian), so
+    A = alpha I + diag(eta) - Gamma amplifies the double-float operator's
+    rounding (~2e-14 of ||Gamma||) by a factor of order eta / alpha in the
+    outer residual of the mixed-precision solve (Sec. 4.3.2 with the operator
+    of Eq. discrete_ANOVA).  The measured floor is ~5e-7, so a change
+    that makes the double-float operator 2-3x less accurate stalls this solve
+    at max_outer above the 1e-6 tolerance; both the single and the batched
+    path must reach it in a few refinement steps."""
+    from paper_2407_06834_gb300.inputs import SWEEP_SIZES, synthetic_image
+    n = SWEEP_SIZES[7]
+    img = synthetic_image(n, n, 8)[1]
+    P = _auto_plan(img, 1.0, eps=1e-7, precision=6)
+    alpha = 0.01
+    b = cuda(alpha * img.ravel())
+    single = P.solve(alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    assert single.info["status"] == 0, single.info
+    assert single.info["rel_res_true"] <= 1e-6 and single.info["outer"] <= 4, single.info
+    _, infos = nlh.solve_batched([P], [alpha], [b], tol=1e-6, arith=nlh.SOLVE_MIXED,
+                                 inner_tol=1e-3)
+    assert infos[0]["status"] == 0 and infos[0]["rel_res_true"] <= 1e-6, infos[0]
+    assert infos[0]["outer"] <= 4, infos[0]
+    P.close()
