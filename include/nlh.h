@@ -248,11 +248,18 @@ typedef struct {
     int maxit;              /* CG iterations (per inner solve when mixed)     */
     int method;             /* NLH_CG .. NLH_CG_DEFLATED                      */
     int arith;              /* NLH_SOLVE_FP64 or NLH_SOLVE_MIXED              */
-    double inner_tol;       /* mixed: inner relative tolerance (0 = 1e-4) of a
-                               refinement step; a step that can end the solve
+    double inner_tol;       /* mixed: inner relative tolerance of a refinement
+                               step.  > 0: fixed; a step that can end the solve
                                (tol / (2 rel) >= max(inner_tol / 4, 1e-4), rel
                                the current relative residual) runs to
-                               min(tol / (2 rel), 0.1) instead              */
+                               min(tol / (2 rel), 0.1) instead.  <= 0
+                               (automatic): every step runs to tol / rel
+                               clamped to [1e-7, 0.1], so the first step aims
+                               at tol and one FP64-accurate residual often
+                               ends the solve; an inner solve also ends when,
+                               within 32x of its target, 3 iterations pass
+                               without its best residual falling by 30 % (the
+                               FP32 operator's rounding floor)              */
     int max_outer;          /* mixed: refinement steps (0 = 20)               */
     const double *x0;       /* device N, initial guess, or NULL (zero)        */
     const double *diag_scale; /* device N, positive factors c_i multiplying

@@ -99,6 +99,12 @@ struct SolveState {
     double rz_old;   // copy made by the update kernel
     double rr;       // ||r||^2 of the current iterate
     double alpha;    // shift of A = alpha I + L
+    // stagnation exit (stag > 0): once the relative residual is within 32x
+    // of tol, the solve ends when `stag` iterations pass without the best
+    // residual so far falling by 30 % (the operator's rounding floor)
+    int stag;
+    int k_best;      // iteration of the last such fall
+    double best;     // best relative residual within 32x of tol (0: none yet)
 };
 
 constexpr int kMaxHist = 4096;

@@ -174,6 +174,13 @@ k_direction(const double *__restrict__ t, double *__restrict__ p, int64_t N, int
             st->done = 1;
         } else if (rel <= st->tol || k >= st->maxit) {
             st->done = 1;
+        } else if (st->stag > 0 && rel <= 32.0 * st->tol) {
+            if (!(st->best > 0.0) || rel < 0.7 * st->best) {
+                st->best = rel;
+                st->k_best = k;
+            } else if (k - st->k_best >= st->stag) {
+                st->done = 1;  // stagnated at the operator's rounding floor
+            }
         }
         set_loop(cond, st);
     }
@@ -423,12 +430,24 @@ static cudaGraphExec_t solve_graph(Plan &P, int prec, int method, bool has_x0, b
 // copy of the device state to the pinned mirror.  krylov_collect reads it
 // after the stream has been synchronised.
 // Relative tolerance of the inner FP32 solve of one refinement step, from
-// the current FP64-accurate relative residual rel: a step whose remaining
-// reduction is within reach (tol / (2 rel) >= max(inner / 4, 1e-4), 1e-4
-// being about where the FP32 operator's rounding stops a solve) runs to
-// exactly that reduction, capped at 0.1, so that it is the last step; any
-// other step runs to the caller's inner tolerance.
+// the current FP64-accurate relative residual rel.
+// - inner > 0 (the caller's fixed inner tolerance): a step whose remaining
+//   reduction is within reach (tol / (2 rel) >= max(inner / 4, 1e-4)) runs
+//   to exactly tol / (2 rel), capped at 0.1, so that it is the last step;
+//   any other step runs to inner.
+// - inner <= 0 (automatic): every step runs to tol / rel, clamped to
+//   [kInnerFloor, 0.1], with the stagnation exit of kInnerStag iterations.
+//   The first step from u = 0 therefore aims at the outer tolerance: where
+//   the FP32 operator's rounding floor lies below it, one FP64-accurate
+//   residual certifies the solve and a whole refinement step with its
+//   FP64-accurate matvec is saved; where it does not, the inner CG stops at
+//   the floor (stagnation exit) and a short second step follows.  The floor
+//   depends on the plan (measured 6e-7 to 3e-6 relative at 512^2 and
+//   2048^2), so a fixed target below it would spin to maxit.
+static constexpr double kInnerFloor = 1e-7;
+static constexpr int kInnerStag = 3;
 __host__ __device__ static double inner_tolerance(double inner, double tol, double rel) {
+    if (inner <= 0) return fmin(fmax(tol / rel, kInnerFloor), 0.1);
     const double need = 0.5 * tol / rel;
     if (need >= fmax(0.25 * inner, 1e-4)) return fmin(need, 0.1);
     return inner;
@@ -436,7 +455,8 @@ __host__ __device__ static double inner_tolerance(double inner, double tol, doub
 
 static void krylov_launch(Plan &P, int prec, double alpha, const double *rhs, const double *x0,
                           double *x_out, int accumulate, double tol, int maxit, int method,
-                          const double *scale, int check_every, cudaStream_t s) {
+                          const double *scale, int check_every, cudaStream_t s,
+                          int stag = 0) {
     int deflate, precond;
     method_flags(method, deflate, precond);
     // a plan whose matvecs call a reduce callback (a window range summed over
@@ -448,6 +468,7 @@ static void krylov_launch(Plan &P, int prec, double alpha, const double *rhs, co
     init.maxit = maxit;
     init.rz_old = 1.0;
     init.alpha = alpha;
+    init.stag = stag;
     *P.st_host = init;
     NLH_CUDA(cudaMemcpyAsync(P.st, P.st_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     if (rhs != P.rhs)
@@ -599,7 +620,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 inf.rel_res_true = residual_collect(P);
                 st = kr.status;
             } else {
-                const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+                const double inner = opts->inner_tol;  // <= 0: automatic
                 const int max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
                 double rel;
                 if (x0 && attempt == 0 && screen) {
@@ -627,7 +648,7 @@ extern "C" nlh_status nlh_solve(nlh_plan plan, double alpha, const double *b, do
                 while (rel > opts->tol && outer < max_outer) {
                     krylov_launch(P, NLH_FP32, alpha, P.rhs, nullptr, u, 1,
                                   inner_tolerance(inner, opts->tol, rel), opts->maxit,
-                                  opts->method, scale, ce, s);
+                                  opts->method, scale, ce, s, inner <= 0 ? kInnerStag : 0);
                     residual_launch(P, accurate, alpha, b, u, P.rhs, s);
                     NLH_CUDA(cudaStreamSynchronize(s));
                     KrylovResult kr = krylov_collect(P);
@@ -723,6 +744,7 @@ __global__ void k_batch_state(const BatchParams *bp, const OuterState *os, Solve
     v.maxit = bp->maxit;
     v.rz_old = 1.0;
     v.alpha = bp->alpha;
+    v.stag = bp->mixed && bp->inner <= 0 ? kInnerStag : 0;
     *st = v;
 }
 
@@ -960,7 +982,7 @@ static nlh_status solve_batched_graph(int n, const nlh_plan *plans, const double
         BatchParams &q = G.bp_host[i];
         q.alpha = alphas[i];
         q.tol = opts->tol;
-        q.inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        q.inner = opts->inner_tol;  // <= 0: automatic
         q.maxit = opts->maxit;
         q.max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
         q.mixed = mixed ? 1 : 0;
@@ -1061,7 +1083,7 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
         std::vector<int> outer(nsolves, 0), done(nsolves, 0), status(nsolves, 1);
         std::vector<size_t> pos(groups.size(), 0);  // next solve of each group
         const bool mixed = opts->arith == NLH_SOLVE_MIXED;
-        const double inner = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        const double inner = opts->inner_tol;  // <= 0: automatic
         const int max_outer = opts->max_outer > 0 ? opts->max_outer : 20;
         while (true) {
             // one round: the current solve of every unfinished group advances one step
@@ -1088,7 +1110,7 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
                     }
                     krylov_launch(P, NLH_FP32, alphas[i], P.rhs, nullptr, u[i], 1,
                                   inner_tolerance(inner, opts->tol, rel[i]), opts->maxit,
-                                  opts->method, nullptr, 0, s);
+                                  opts->method, nullptr, 0, s, inner <= 0 ? kInnerStag : 0);
                     residual_launch(P, accurate, alphas[i], b[i], u[i], P.rhs, s);
                 }
                 active.push_back({(int)gi, i});

@@ -62,8 +62,9 @@ def test_batched_equals_single(arith):
         assert rel(host(us[k]), host(single.u)) < 1e-9
 
 
-@pytest.mark.parametrize("arith", [nlh.SOLVE_MIXED, nlh.SOLVE_DF32])
-def test_batched_solutions_certified_by_oracle(arith):
+@pytest.mark.parametrize("arith,inner", [(nlh.SOLVE_MIXED, 1e-3), (nlh.SOLVE_MIXED, 0.0),
+                                         (nlh.SOLVE_DF32, 1e-3)])
+def test_batched_solutions_certified_by_oracle(arith, inner):
     """Batched solves on images of uneven sizes, each with its own plan at
     tight NFFT parameters: every solution's residual under the oracle's
     direct operator A = alpha I + diag(eta) - Gamma (Sec. 2.3,
@@ -78,7 +79,7 @@ def test_batched_solutions_certified_by_oracle(arith):
              for im, s in zip(imgs, sig)]
     bs = [a * im.ravel() for im, a in zip(imgs, alphas)]
     us, infos = nlh.solve_batched(plans, alphas, [cuda(b) for b in bs], tol=1e-6, arith=arith,
-                                  inner_tol=1e-3)
+                                  inner_tol=inner)
     for k, (im, s, a, b) in enumerate(zip(imgs, sig, alphas, bs)):
         assert infos[k]["status"] == 0 and infos[k]["rel_res_true"] <= 1e-6, infos[k]
         coords = orc.image_coords(im, 1, raster_windows(1))
@@ -206,7 +207,8 @@ def test_retile_and_team_after_a_solve_keep_the_plan_consistent():
     P.close()
 
 
-def test_mixed_solve_reaches_tol_when_degrees_dwarf_alpha():
+@pytest.mark.parametrize("inner", [1e-3, 0.0])
+def test_mixed_solve_reaches_tol_when_degrees_dwarf_alpha(inner):
     """The hardest pair of the (sigma, alpha) sweep: sigma = 1 on an 896 x 896
     image, alpha = 0.01.  The degrees are of order N (a wide Gaussian), so
     A = alpha I + diag(eta) - Gamma amplifies the double-float operator's
@@ -215,18 +217,44 @@ def test_mixed_solve_reaches_tol_when_degrees_dwarf_alpha():
     of Eq. discrete_ANOVA).  The measured floor is ~5e-7, so a change
     that makes the double-float operator 2-3x less accurate stalls this solve
     at max_outer above the 1e-6 tolerance; both the single and the batched
-    path must reach it in a few refinement steps."""
+    path must reach it in a few refinement steps, with a fixed inner
+    tolerance and with the automatic one (inner_tol = 0)."""
     from paper_2407_06834_gb300.inputs import SWEEP_SIZES, synthetic_image
     n = SWEEP_SIZES[7]
     img = synthetic_image(n, n, 8)[1]
     P = _auto_plan(img, 1.0, eps=1e-7, precision=6)
     alpha = 0.01
     b = cuda(alpha * img.ravel())
-    single = P.solve(alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    single = P.solve(alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=inner)
     assert single.info["status"] == 0, single.info
     assert single.info["rel_res_true"] <= 1e-6 and single.info["outer"] <= 4, single.info
     _, infos = nlh.solve_batched([P], [alpha], [b], tol=1e-6, arith=nlh.SOLVE_MIXED,
-                                 inner_tol=1e-3)
+                                 inner_tol=inner)
     assert infos[0]["status"] == 0 and infos[0]["rel_res_true"] <= 1e-6, infos[0]
     assert infos[0]["outer"] <= 4, infos[0]
+    P.close()
+
+
+def test_automatic_inner_tolerance_steps():
+    """The automatic inner tolerance (inner_tol = 0) of the mixed solve: the
+    first FP32 inner solve aims at the outer tolerance, so on a well
+    conditioned problem one FP64-accurate residual certifies the result
+    (one refinement step, one FP64-accurate matvec); at a tolerance below
+    what the FP32 operator can reach (1e-9), the inner solves stop at their
+    floor and refinement still converges, on the single and the batched
+    path."""
+    img = image(48, 48, seed=21)
+    P = _auto_plan(img, 0.3, eps=1e-7, precision=6)
+    b = cuda(2.0 * img.ravel())
+    one = P.solve(2.0, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=0.0)
+    assert one.info["status"] == 0 and one.info["rel_res_true"] <= 1e-6, one.info
+    fixed = P.solve(2.0, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    assert fixed.info["status"] == 0 and fixed.info["outer"] >= 2, fixed.info
+    assert one.info["outer"] < fixed.info["outer"], (one.info, fixed.info)
+    tight = P.solve(2.0, b, tol=1e-9, arith=nlh.SOLVE_MIXED, inner_tol=0.0)
+    assert tight.info["status"] == 0 and tight.info["rel_res_true"] <= 1e-9, tight.info
+    assert 2 <= tight.info["outer"] <= 6, tight.info
+    _, infos = nlh.solve_batched([P], [2.0], [b], tol=1e-9, arith=nlh.SOLVE_MIXED, inner_tol=0.0)
+    assert infos[0]["status"] == 0 and infos[0]["rel_res_true"] <= 1e-9, infos[0]
+    assert abs(infos[0]["outer"] - tight.info["outer"]) <= 1, (infos[0], tight.info)
     P.close()

@@ -49,17 +49,42 @@ def test_sampled_rows_and_fp32(big):
     assert err32 < bound + 1e-5, err32
 
 
+@pytest.mark.parametrize("inner", [1e-3, 0.0])
 @pytest.mark.parametrize("sigma", [0.1, 0.2, 0.4])
-def test_mixed_solve_2048(big, sigma):
+def test_mixed_solve_2048(big, sigma, inner):
+    """inner = 0 is the automatic inner tolerance: the first step aims at
+    1e-6, below the FP32 operator's rounding floor on some plans (measured
+    up to ~3e-6 here); its stagnation exit must end such a step within a few
+    iterations instead of running to maxit (200)."""
     img, f = big
     P = nlh.Plan.from_image(f, WL.radius, WL.windows, sigma, M=WL.M, n_os=WL.n_os, m=WL.m,
                             precision=6)
     b = f.reshape(-1) * WL.alpha
-    res = P.solve(WL.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+    res = P.solve(WL.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=inner)
     assert res.info["status"] == 0 and res.info["rel_res_true"] <= 1e-6
+    assert res.info["iters"] <= 40 and res.info["outer"] <= 3, res.info
     # the FP64-accurate residual, recomputed independently of the solve
     q = host(P.matvec(res.u, op=2, alpha=WL.alpha, precision=nlh.NLH_DF32))
     bh = img.ravel() * WL.alpha
     assert np.linalg.norm(bh - q) / np.linalg.norm(bh) <= 1.01e-6
     u = host(res.u)
     assert u.min() >= img.min() - 1e-3 and u.max() <= img.max() + 1e-3
+
+
+def test_automatic_inner_tolerance_512_does_not_spin():
+    """The 512 x 512 workload (3x3 patches, L = 3, M = 32, n_os = 64, m = 4)
+    whose FP32 recurrence residual floors at ~1e-6: with the automatic inner
+    tolerance the mixed solve reaches 1e-6 in about as many CG iterations as
+    with a fixed 1e-3, on the default and the autotuned tiling."""
+    wl = WORKLOADS["img512"]
+    f = cuda(wl.image())
+    b = f.reshape(-1) * wl.alpha
+    for at in (False, True):
+        P = nlh.Plan.from_image(f, wl.radius, wl.windows, wl.sigma, pad=wl.pad, M=wl.M,
+                                n_os=wl.n_os, m=wl.m, precision=6, autotune=at)
+        fixed = P.solve(wl.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=1e-3)
+        auto = P.solve(wl.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=0.0)
+        for r in (fixed, auto):
+            assert r.info["status"] == 0 and r.info["rel_res_true"] <= 1e-6, r.info
+        assert auto.info["iters"] <= fixed.info["iters"] + 6, (auto.info, fixed.info)
+        P.close()
