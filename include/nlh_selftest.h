@@ -1,6 +1,6 @@
 /*
  * nlh_selftest.h -- test hooks for the failure path of the library's bounded
- * device waits.
+ * device waits, and for the solver's stopping rules.
  *
  * Every wait inside the library's kernels (bulk copies, tensor-core
  * commits) is bounded: a wait that gives up records NLH_ERR_TIMEOUT in the
@@ -33,6 +33,18 @@ nlh_status nlh_selftest_plan_timeout(nlh_plan plan, void *stream);
  * synchronising network calls) then return NLH_ERR_TIMEOUT once.
  * Errors: NLH_ERR_ARG (NULL net), NLH_ERR_CUDA. */
 nlh_status nlh_selftest_net_timeout(nlh_net net, void *stream);
+
+/* The mixed solve's inner tolerance for a refinement step (nlh_solve_opts
+ * .inner_tol = inner, outer tolerance tol, current FP64-accurate relative
+ * residual rel), as the solver computes it.  Host only, no GPU needed. */
+double nlh_selftest_inner_tolerance(double inner, double tol, double rel);
+
+/* Replays the Krylov stopping rule on a host array of relative residuals
+ * rel[0..n) (iteration k has rel[k]) with tolerance tol, maxit and the
+ * stagnation window stag (0: off; the automatic inner tolerance uses 3).
+ * Returns the iteration at which the solve stops, -1 if it runs through
+ * all n, -2 for a NULL array or n < 0.  Host only, no GPU needed. */
+int nlh_selftest_convergence(const double *rel, int n, double tol, int maxit, int stag);
 
 #ifdef __cplusplus
 }

@@ -130,6 +130,27 @@ k_init2(double *__restrict__ r, const double *__restrict__ pinv, int64_t N, int 
     }
 }
 
+// The stopping rule after iteration k with relative residual rel: breakdown
+// on a NaN residual; done at rel <= tol or k == maxit; and, with stag > 0,
+// done once rel is within 32x of tol and `stag` iterations have passed
+// since the best residual in that range last fell by 30 % (the operator's
+// rounding floor: the recurrence residual stops falling there).
+__host__ __device__ static void convergence_step(SolveState *st, double rel, int k) {
+    if (!(rel == rel)) {  // NaN residual: breakdown
+        st->status = -4;
+        st->done = 1;
+    } else if (rel <= st->tol || k >= st->maxit) {
+        st->done = 1;
+    } else if (st->stag > 0 && rel <= 32.0 * st->tol) {
+        if (!(st->best > 0.0) || rel < 0.7 * st->best) {
+            st->best = rel;
+            st->k_best = k;
+        } else if (k - st->k_best >= st->stag) {
+            st->done = 1;
+        }
+    }
+}
+
 // Shared tail of the init and direction kernels: from the stats partials
 // (sum t, r.t, r.r, sum r) form z = t - mean(t) (deflated) or t, then
 // p = z + beta p.  Block 0 records the scalars and the convergence flag.
@@ -169,19 +190,7 @@ k_direction(const double *__restrict__ t, double *__restrict__ p, int64_t N, int
         st->rz = rz;
         st->rr = rr;
         if (k < kMaxHist) hist[k] = rel;
-        if (!(rel == rel)) {               // NaN residual: breakdown
-            st->status = -4;
-            st->done = 1;
-        } else if (rel <= st->tol || k >= st->maxit) {
-            st->done = 1;
-        } else if (st->stag > 0 && rel <= 32.0 * st->tol) {
-            if (!(st->best > 0.0) || rel < 0.7 * st->best) {
-                st->best = rel;
-                st->k_best = k;
-            } else if (k - st->k_best >= st->stag) {
-                st->done = 1;  // stagnated at the operator's rounding floor
-            }
-        }
+        convergence_step(st, rel, k);
         set_loop(cond, st);
     }
 }
@@ -1172,4 +1181,24 @@ extern "C" nlh_status nlh_solve_batched(int nsolves, const nlh_plan *plans, cons
     } catch (Failure &f) {
         return f.st;
     }
+}
+
+// Test hooks (include/nlh_selftest.h): the host side of the solver's
+// stopping rules, callable without a GPU.
+extern "C" double nlh_selftest_inner_tolerance(double inner, double tol, double rel) {
+    return nlh::inner_tolerance(inner, tol, rel);
+}
+
+extern "C" int nlh_selftest_convergence(const double *rel, int n, double tol, int maxit,
+                                        int stag) {
+    if (!rel || n < 0) return -2;
+    nlh::SolveState st{};
+    st.tol = tol;
+    st.maxit = maxit;
+    st.stag = stag;
+    for (int k = 0; k < n; ++k) {
+        nlh::convergence_step(&st, rel[k], k);
+        if (st.done) return k;
+    }
+    return -1;
 }

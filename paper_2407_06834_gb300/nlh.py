@@ -134,6 +134,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nlh_selftest_plan_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nlh_selftest_net_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nlh_selftest_inner_tolerance": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+    "nlh_selftest_convergence": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]),
     "nlh_kernel_launches": (C.c_int64, []),
     "nlh_profile_enable": (C.c_int, [C.c_int]),
     "nlh_profile_reset": (C.c_int, []),
