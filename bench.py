@@ -585,11 +585,13 @@ def small_line(args, dev, lib, flush):
                             n_os=wl.n_os, m=wl.m, precision=7)
     b = img.reshape(-1) * wl.alpha
     sv = {}
-    for nm, ar in (("fp64", nlh.SOLVE_FP64), ("df32", nlh.SOLVE_DF32), ("mixed", nlh.SOLVE_MIXED)):
-        P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=INNER_TOL)
-        r = P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=INNER_TOL)
+    for nm, ar, it in (("fp64", nlh.SOLVE_FP64, INNER_TOL), ("df32", nlh.SOLVE_DF32, INNER_TOL),
+                       ("mixed", nlh.SOLVE_MIXED, INNER_TOL),
+                       ("mixed_inner_1e-3", nlh.SOLVE_MIXED, 1e-3)):
+        P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=it)
+        r = P.solve(wl.alpha, b, tol=wl.tol, arith=ar, inner_tol=it)
         sv[nm] = {"seconds": r.info["seconds"], "iters": r.info["iters"],
-                  "rel_res_fp64": r.info["rel_res_true"]}
+                  "outer": r.info["outer"], "rel_res_fp64": r.info["rel_res_true"]}
     P.close()
     out["solve_seconds"] = sv
     return out

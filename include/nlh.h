@@ -256,10 +256,10 @@ typedef struct {
                                (automatic): every step runs to tol / rel
                                clamped to [1e-7, 0.1], so the first step aims
                                at tol and one FP64-accurate residual often
-                               ends the solve; an inner solve also ends when,
-                               within 32x of its target, 3 iterations pass
-                               without its best residual falling by 30 % (the
-                               FP32 operator's rounding floor)              */
+                               ends the solve; an inner solve also ends when
+                               its best residual has not fallen by 30 % for 3
+                               iterations within 8x of its target, or for 9
+                               anywhere (the FP32 operator's rounding floor) */
     int max_outer;          /* mixed: refinement steps (0 = 20)               */
     const double *x0;       /* device N, initial guess, or NULL (zero)        */
     const double *diag_scale; /* device N, positive factors c_i multiplying

@@ -99,12 +99,13 @@ struct SolveState {
     double rz_old;   // copy made by the update kernel
     double rr;       // ||r||^2 of the current iterate
     double alpha;    // shift of A = alpha I + L
-    // stagnation exit (stag > 0): once the relative residual is within 32x
-    // of tol, the solve ends when `stag` iterations pass without the best
-    // residual so far falling by 30 % (the operator's rounding floor)
+    // stagnation exit (stag > 0): the solve ends when the best residual so
+    // far has not fallen by 30 % for `stag` iterations with the residual
+    // within 8x of tol, or for 3 stag iterations anywhere (the operator's
+    // rounding floor)
     int stag;
     int k_best;      // iteration of the last such fall
-    double best;     // best relative residual within 32x of tol (0: none yet)
+    double best;     // best relative residual so far (0: none yet)
 };
 
 constexpr int kMaxHist = 4096;

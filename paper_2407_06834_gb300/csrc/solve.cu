@@ -132,20 +132,22 @@ k_init2(double *__restrict__ r, const double *__restrict__ pinv, int64_t N, int 
 
 // The stopping rule after iteration k with relative residual rel: breakdown
 // on a NaN residual; done at rel <= tol or k == maxit; and, with stag > 0,
-// done once rel is within 32x of tol and `stag` iterations have passed
-// since the best residual in that range last fell by 30 % (the operator's
-// rounding floor: the recurrence residual stops falling there).
+// done once the best residual so far has not fallen by 30 % for `stag`
+// iterations while rel is within 8x of tol, or for 3 stag iterations
+// anywhere (the operator's rounding floor: the recurrence residual stops
+// falling there; the wider limit away from tol keeps a plateau of CG's
+// descent from ending the solve early, yet bounds a floor far above tol).
 __host__ __device__ static void convergence_step(SolveState *st, double rel, int k) {
     if (!(rel == rel)) {  // NaN residual: breakdown
         st->status = -4;
         st->done = 1;
     } else if (rel <= st->tol || k >= st->maxit) {
         st->done = 1;
-    } else if (st->stag > 0 && rel <= 32.0 * st->tol) {
+    } else if (st->stag > 0) {
         if (!(st->best > 0.0) || rel < 0.7 * st->best) {
             st->best = rel;
             st->k_best = k;
-        } else if (k - st->k_best >= st->stag) {
+        } else if (k - st->k_best >= (rel <= 8.0 * st->tol ? st->stag : 3 * st->stag)) {
             st->done = 1;
         }
     }

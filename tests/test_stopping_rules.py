@@ -60,12 +60,17 @@ def test_stagnation_exit(lib):
     tol = 1e-6
     # falls to 2e-6 and stays there (the FP32 operator's floor)
     rels = [1.0, 1e-2, 1e-4, 1e-5, 3e-6, 2e-6, 2.1e-6, 1.9e-6, 2.05e-6, 1.95e-6, 2e-6]
-    # within 32 tol from k = 3: best 1e-5 (k 3), 3e-6 (k 4), 2e-6 (k 5, a 33 % fall), then
-    # three iterations without a 30 % fall: stop at k = 8
+    # best 2e-6 at k = 5 (a 33 % fall from 3e-6), then three iterations within 8 tol
+    # without a 30 % fall: stop at k = 8
     assert _stop(lib, rels, tol, stag=3) == 8
     assert _stop(lib, rels, tol, stag=0) == -1   # without the exit it would run to maxit
-    # a plateau above 32 tol never triggers the exit
-    assert _stop(lib, [1.0, 1e-3] + [5e-5] * 20, tol, stag=3) == -1
+    # a plateau above 8 tol (a pause of CG's descent) ends the solve only after 9
+    # iterations without a fall: best 5e-5 at k = 2, stop at k = 11
+    assert _stop(lib, [1.0, 1e-3] + [5e-5] * 20, tol, stag=3) == 11
+    # a pause of 8 iterations above 8 tol, then descent: the exit does not fire
+    pause = [1.0, 1e-2, 1e-4] + [9e-5] * 8 + [1e-5 * 0.5 ** k for k in range(12)]
+    k = _stop(lib, pause, tol, stag=3)
+    assert pause[k] <= tol
     # slow but steady progress (30 % every other iteration) is not stagnation
     slow = [1e-5 * 0.69 ** (k // 2) for k in range(40)]
     k = _stop(lib, slow, tol, stag=3)
