@@ -64,12 +64,12 @@ DF32_OPS_PER_UPDATE = 12
 # image), keyed by a hash of the kernel sources at capture time: when the
 # sources change, the figures no longer describe the kernels and the bench
 # reports traffic null.
-NCU_TRAFFIC = {"sources_sha16": "0376340f995fc03b", "workload": "img2048",
+NCU_TRAFFIC = {"sources_sha16": "266f200935594f5c", "workload": "img2048",
                "bytes_per_launch": {
-                   "stored": {"spread32": 781722368, "interp32": 725104640,
-                              "spread_df32": 1430231296, "interp_df32": 1294247936},
-                   "image": {"spread32": 839197696, "interp32": 430656256,
-                             "spread_df32": 1066927104, "interp_df32": 740065280}}}
+                   "stored": {"spread32": 781465344, "interp32": 724645120,
+                              "spread_df32": 1433175296, "interp_df32": 1292100864},
+                   "image": {"spread32": 839821568, "interp32": 430189824,
+                             "spread_df32": 1064484096, "interp_df32": 736641024}}}
 
 
 def kernel_sources_sha16() -> str:
