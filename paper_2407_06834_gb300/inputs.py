@@ -106,11 +106,14 @@ class Workload:
         return synthetic_image(self.n1, self.n2, self.seed)[1]
 
 
-# The workloads: 64^2 (oracle-sized), 512^2 (the timed one), 2048^2 with
-# 5x5 patches and 9 windows.
+# The workloads: 64^2 (oracle-sized), 512^2 with 3x3 patches and 3 windows,
+# 2048^2 with 5x5 patches and 9 windows (the timed one), and 1024^2 with the
+# 2048^2 workload's patches and NFFT parameters (the same kernel
+# instantiations on a quarter of the points, for multi-pass profiles).
 WORKLOADS = {
     "img64": Workload("img64", 64, 64),
     "img512": Workload("img512", 512, 512),
+    "img1024": Workload("img1024", 1024, 1024, radius=2, M=64, n_os=128, m=6),
     "img2048": Workload("img2048", 2048, 2048, radius=2, M=64, n_os=128, m=6,
                         sigmas=[0.1, 0.2, 0.4]),
 }
