@@ -771,11 +771,21 @@ struct InterpTile {
     static constexpr int COPY = E * E * EP;                            // cells per copy
     static constexpr size_t bytes = align16(sizeof(T) * NC * COPY);
 };
-// Threads of an interpolation CTA: 512 for the FP32 2m = 12 instance (its
-// 4-copy tile allows one CTA per SM), 256 otherwise.
+// Interpolation CTAs whose lanes take two points of one cell each (the FP32
+// 2m = 12 instance): every tile row read from shared memory serves both
+// points' FMAs, half the row loads per FMA of one point per lane, which at
+// 2m = 12 throttle the kernel's shared-memory instruction issue.  The
+// points of an item are paired in order; an item with an odd count ends in
+// a single point.
+template <typename T, int W2>
+__host__ __device__ constexpr bool interp_pairs() {
+    return std::is_same<T, float>::value && W2 == 12;
+}
+// Threads of an interpolation CTA: 256 (the FP32 2m = 12 instance's 4-copy
+// tile allows one CTA per SM; its paired lanes need ~2x the registers).
 template <typename T, int W2>
 constexpr int interp_threads() {
-    return (std::is_same<T, float>::value && W2 == 12) ? 512 : kInterpThreads;
+    return kInterpThreads;
 }
 // Interpolation CTAs that keep each lane's y and z window weights in shared
 // memory ([k][lane]) instead of registers: the double-float ones (this
@@ -802,6 +812,11 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
     // when interp_smem_weights, out of the registers of the stencil loop
     T *s_wy = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_coef) + kWinStageBytes);
     T *s_wz = s_wy + W2 * NTH;
+    constexpr bool PAIR = interp_pairs<T, W2>();
+    // first pair of each item and the unit's pair count (paired lanes)
+    int *s_pst = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(s_wy) +
+                                         (interp_smem_weights<T, W2>() ? 2 * W2 * sizeof(T) * NTH
+                                                                       : 0));
     __shared__ double sh_red[33];
     if (done && *done) return;
     if constexpr (!std::is_same<T, float>::value) win_stage(a.wstage, s_coef);
@@ -821,6 +836,25 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
         int tx0, ty0, tz0;
         tile_origin(un.y, a.n, tx0, ty0, tz0);
         for (int e = threadIdx.x; e < nit; e += blockDim.x) s_items[e] = a.items[it0 + e];
+        if constexpr (PAIR) {
+            // warp 0: s_pst[e] = pairs of items before e, s_pst[nit] = all
+            if (warp == 0) {
+                int carry = 0;
+                if (lane == 0) s_pst[0] = 0;
+                for (int c = 0; c < nit; c += 32) {
+                    const int e = c + lane;
+                    const int v = e < nit ? (a.items[it0 + e].w + 1) >> 1 : 0;
+                    int inc = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += u;
+                    }
+                    if (e < nit) s_pst[e + 1] = carry + inc;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+            }
+        }
         const G *g = grid + (int64_t)l * a.n * a.n * a.n;
         {
             constexpr int UNR = 8;
@@ -854,77 +888,10 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
             }
         }
         __syncthreads();
-        const int first = s_items[0].z;
-        const int total = s_items[nit - 1].z + s_items[nit - 1].w - first;
-        for (int p = warp * 32 + lane; p - lane < total; p += nwarp * 32) {
-            if (p >= total) continue;
-            const int sp = first + p;
-                        int lo = 0, hi = nit - 1;  // the last item starting at or before sp
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_items[mid].z <= sp) lo = mid; else hi = mid - 1;
-            }
-            int lx0, ly0, lz0;
-            item_local(s_items[lo].x, lx0, ly0, lz0);
-            if (!idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N && lo >= 0 && lo < nit, 12, sp, lo)) continue;
-            const int i = __ldg(a.perm + sp);
-            if (!idx_ok(i >= 0 && i < a.N, 14, i, sp)) continue;
-            T wxa[W2], wy[W2], wz[W2];
-            const PixRC prc = pix_rc(a, i);
-            const T o0 = point_offset<T>(a, sp, 0, l, prc, tx0 + lx0);
-            const T o1 = point_offset<T>(a, sp, 1, l, prc, ty0 + ly0);
-            const T o2 = point_offset<T>(a, sp, 2, l, prc, tz0 + lz0);
-            win_weights<W2>(wp, s_coef, o0, wxa);
-            win_weights<W2>(wp, s_coef, o1, wy);
-            win_weights<W2>(wp, s_coef, o2, wz);
-            Line<T, W2> wx, t, h;
-            wx.from(wxa);
-            T acc = T(0);
-            constexpr bool SW = interp_smem_weights<T, W2>();
-            if constexpr (SW) {
-#pragma unroll
-                for (int k = 0; k < W2; ++k) {
-                    s_wy[k * NTH + threadIdx.x] = wy[k];
-                    s_wz[k * NTH + threadIdx.x] = wz[k];
-                }
-            }
-            // the z loop stays rolled (the unrolled y loop is the work; a
-            // fully unrolled stencil makes the compile very long)
-            // the copy whose rows start 16-byte aligned at x = lx0 (one copy:
-            // the plain tile)
-            const int cx = NC == 1 ? 0 : (lx0 & 3);
-            const T *scopy = S + cx * COPY;
-#pragma unroll 1
-            for (int z = 0; z < W2; ++z) {
-                t.zero();
-                const int so = ((lz0 + z) * E + ly0) * EP + lx0 - cx;
-                if (!idx_ok(so >= 0 && so + (W2 - 1) * EP + W2 - 1 < COPY, 13, so, COPY)) break;
-                const T *srow = scopy + so;
-#pragma unroll
-                for (int y = 0; y < W2; ++y) {
-                    if constexpr (NC == 1) {
-                        h.load_cells(srow + y * EP);
-                    } else {
-                        h.load_cells_v4(srow + y * EP);
-                    }
-                    if constexpr (SW) t.axpy(s_wy[y * NTH + threadIdx.x], h);
-                    else t.axpy(wy[y], h);
-                }
-                T wzz;
-                if constexpr (SW) {
-                    wzz = s_wz[z * NTH + threadIdx.x];
-                } else {
-                    // wz[z] by a select over the unrolled array (no local memory)
-                    wzz = wz[0];
-#pragma unroll
-                    for (int k = 1; k < W2; ++k)
-                        if (z == k) wzz = wz[k];
-                }
-                acc = fma(wzz, wx.dot(t), acc);
-            }
-            // epilogue: one window alone finishes the pixel here; with several
-            // windows the value is added into the pixel's sum, which
-            // k_finish turns into the output after every window is in
+        // epilogue: one window alone finishes the pixel here; with several
+        // windows the value is added into the pixel's sum, which k_finish
+        // turns into the output after every window is in
+        auto finish = [&](int i, T acc) {
             const double val = (double)acc;
             if (ep.L > 1) {
                 atomicAdd(&ep.yacc[i], val);
@@ -938,6 +905,142 @@ k_interp(const NfftArgs a, const typename PolyArg<T>::type wp,
                 }
                 ep.y[i] = out;
                 part = fma(xi, out, part);
+            }
+        };
+        if constexpr (PAIR) {
+            const int npairs = s_pst[nit];
+            for (int q = warp * 32 + lane; q - lane < npairs; q += nwarp * 32) {
+                if (q >= npairs) continue;
+                int lo = 0, hi = nit - 1;  // the last item whose first pair is at or before q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pst[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                const int4 itm = s_items[lo];
+                const int o = 2 * (q - s_pst[lo]);
+                const bool two = o + 1 < itm.w;
+                const int sp1 = itm.z + o, sp2 = two ? sp1 + 1 : sp1;
+                int lx0, ly0, lz0;
+                item_local(itm.x, lx0, ly0, lz0);
+                if (!idx_ok(sp1 >= 0 && sp2 < (int64_t)a.L * a.N && o < itm.w, 12, sp1, lo)) continue;
+                const int i1 = __ldg(a.perm + sp1), i2 = __ldg(a.perm + sp2);
+                if (!idx_ok(i1 >= 0 && i1 < a.N && i2 >= 0 && i2 < a.N, 14, i1, sp1)) continue;
+                T wxa[W2], wy1[W2], wz1[W2], wy2[W2], wz2[W2];
+                Line<T, W2> wx1, wx2, t1, t2, h;
+                {
+                    const PixRC prc = pix_rc(a, i1);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp1, 0, l, prc, tx0 + lx0), wxa);
+                    wx1.from(wxa);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp1, 1, l, prc, ty0 + ly0), wy1);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp1, 2, l, prc, tz0 + lz0), wz1);
+                }
+                {
+                    const PixRC prc = pix_rc(a, i2);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp2, 0, l, prc, tx0 + lx0), wxa);
+                    wx2.from(wxa);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp2, 1, l, prc, ty0 + ly0), wy2);
+                    win_weights<W2>(wp, s_coef, point_offset<T>(a, sp2, 2, l, prc, tz0 + lz0), wz2);
+                }
+                T acc1 = T(0), acc2 = T(0);
+                const int cx = NC == 1 ? 0 : (lx0 & 3);
+                const T *scopy = S + cx * COPY;
+#pragma unroll 1
+                for (int z = 0; z < W2; ++z) {
+                    t1.zero();
+                    t2.zero();
+                    const int so = ((lz0 + z) * E + ly0) * EP + lx0 - cx;
+                    if (!idx_ok(so >= 0 && so + (W2 - 1) * EP + W2 - 1 < COPY, 13, so, COPY)) break;
+                    const T *srow = scopy + so;
+#pragma unroll
+                    for (int y = 0; y < W2; ++y) {
+                        h.load_cells_v4(srow + y * EP);
+                        t1.axpy(wy1[y], h);
+                        t2.axpy(wy2[y], h);
+                    }
+                    // wz[z] by a select over the unrolled arrays (no local memory)
+                    T w1 = wz1[0], w2 = wz2[0];
+#pragma unroll
+                    for (int k = 1; k < W2; ++k)
+                        if (z == k) {
+                            w1 = wz1[k];
+                            w2 = wz2[k];
+                        }
+                    acc1 = fma(w1, wx1.dot(t1), acc1);
+                    acc2 = fma(w2, wx2.dot(t2), acc2);
+                }
+                finish(i1, acc1);
+                if (two) finish(i2, acc2);
+            }
+        } else {
+            const int first = s_items[0].z;
+            const int total = s_items[nit - 1].z + s_items[nit - 1].w - first;
+            for (int p = warp * 32 + lane; p - lane < total; p += nwarp * 32) {
+                if (p >= total) continue;
+                const int sp = first + p;
+                int lo = 0, hi = nit - 1;  // the last item starting at or before sp
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_items[mid].z <= sp) lo = mid; else hi = mid - 1;
+                }
+                int lx0, ly0, lz0;
+                item_local(s_items[lo].x, lx0, ly0, lz0);
+                if (!idx_ok(sp >= 0 && sp < (int64_t)a.L * a.N && lo >= 0 && lo < nit, 12, sp, lo)) continue;
+                const int i = __ldg(a.perm + sp);
+                if (!idx_ok(i >= 0 && i < a.N, 14, i, sp)) continue;
+                T wxa[W2], wy[W2], wz[W2];
+                const PixRC prc = pix_rc(a, i);
+                const T o0 = point_offset<T>(a, sp, 0, l, prc, tx0 + lx0);
+                const T o1 = point_offset<T>(a, sp, 1, l, prc, ty0 + ly0);
+                const T o2 = point_offset<T>(a, sp, 2, l, prc, tz0 + lz0);
+                win_weights<W2>(wp, s_coef, o0, wxa);
+                win_weights<W2>(wp, s_coef, o1, wy);
+                win_weights<W2>(wp, s_coef, o2, wz);
+                Line<T, W2> wx, t, h;
+                wx.from(wxa);
+                T acc = T(0);
+                constexpr bool SW = interp_smem_weights<T, W2>();
+                if constexpr (SW) {
+    #pragma unroll
+                    for (int k = 0; k < W2; ++k) {
+                        s_wy[k * NTH + threadIdx.x] = wy[k];
+                        s_wz[k * NTH + threadIdx.x] = wz[k];
+                    }
+                }
+                // the z loop stays rolled (the unrolled y loop is the work; a
+                // fully unrolled stencil makes the compile very long)
+                // the copy whose rows start 16-byte aligned at x = lx0 (one copy:
+                // the plain tile)
+                const int cx = NC == 1 ? 0 : (lx0 & 3);
+                const T *scopy = S + cx * COPY;
+    #pragma unroll 1
+                for (int z = 0; z < W2; ++z) {
+                    t.zero();
+                    const int so = ((lz0 + z) * E + ly0) * EP + lx0 - cx;
+                    if (!idx_ok(so >= 0 && so + (W2 - 1) * EP + W2 - 1 < COPY, 13, so, COPY)) break;
+                    const T *srow = scopy + so;
+    #pragma unroll
+                    for (int y = 0; y < W2; ++y) {
+                        if constexpr (NC == 1) {
+                            h.load_cells(srow + y * EP);
+                        } else {
+                            h.load_cells_v4(srow + y * EP);
+                        }
+                        if constexpr (SW) t.axpy(s_wy[y * NTH + threadIdx.x], h);
+                        else t.axpy(wy[y], h);
+                    }
+                    T wzz;
+                    if constexpr (SW) {
+                        wzz = s_wz[z * NTH + threadIdx.x];
+                    } else {
+                        // wz[z] by a select over the unrolled array (no local memory)
+                        wzz = wz[0];
+    #pragma unroll
+                        for (int k = 1; k < W2; ++k)
+                            if (z == k) wzz = wz[k];
+                    }
+                    acc = fma(wzz, wx.dot(t), acc);
+                }
+                finish(i, acc);
             }
         }
     }
@@ -1296,7 +1399,8 @@ constexpr int interp_minb() {
 template <typename T, int W2>
 constexpr size_t interp_smem() {
     return InterpTile<T, W2>::bytes + sizeof(int4) * kUnitItems + 16 + kWinStageBytes +
-           (interp_smem_weights<T, W2>() ? 2 * W2 * sizeof(T) * interp_threads<T, W2>() : 0);
+           (interp_smem_weights<T, W2>() ? 2 * W2 * sizeof(T) * interp_threads<T, W2>() : 0) +
+           (interp_pairs<T, W2>() ? sizeof(int) * (kUnitItems + 1) : 0);
 }
 
 template <typename T, int W2>
