@@ -64,12 +64,12 @@ DF32_OPS_PER_UPDATE = 12
 # image), keyed by a hash of the kernel sources at capture time: when the
 # sources change, the figures no longer describe the kernels and the bench
 # reports traffic null.
-NCU_TRAFFIC = {"sources_sha16": "266f200935594f5c", "workload": "img2048",
+NCU_TRAFFIC = {"sources_sha16": "444583fc392f26ea", "workload": "img2048",
                "bytes_per_launch": {
-                   "stored": {"spread32": 781465344, "interp32": 724645120,
-                              "spread_df32": 1433175296, "interp_df32": 1292100864},
-                   "image": {"spread32": 839821568, "interp32": 430189824,
-                             "spread_df32": 1064484096, "interp_df32": 736641024}}}
+                   "stored": {"spread32": 780996352, "interp32": 725467136,
+                              "spread_df32": 1431011584, "interp_df32": 1294031104},
+                   "image": {"spread32": 840602624, "interp32": 430556672,
+                             "spread_df32": 1062125824, "interp_df32": 738703872}}}
 
 
 def kernel_sources_sha16() -> str:
