@@ -73,9 +73,13 @@ def test_mixed_solve_2048(big, sigma, inner):
 
 def test_automatic_inner_tolerance_512_does_not_spin():
     """The 512 x 512 workload (3x3 patches, L = 3, M = 32, n_os = 64, m = 4)
-    whose FP32 recurrence residual floors at ~1e-6: with the automatic inner
-    tolerance the mixed solve reaches 1e-6 in about as many CG iterations as
-    with a fixed 1e-3, on the default and the autotuned tiling."""
+    whose FP32 operator's floor (~3e-6) lies above the 1e-6 tolerance: with
+    the automatic inner tolerance the first inner solve cannot certify and
+    its recurrence residual stalls near 1e-6, where the stagnation exit must
+    end it (without the exit it ran to maxit = 200).  Measured over several
+    runs the automatic policy took 10-17 iterations against 10-15 for a
+    fixed 1e-3, varying with the grid sums' rounding order, so the bound
+    here is on running away, on the default and the autotuned tiling."""
     wl = WORKLOADS["img512"]
     f = cuda(wl.image())
     b = f.reshape(-1) * wl.alpha
@@ -86,5 +90,5 @@ def test_automatic_inner_tolerance_512_does_not_spin():
         auto = P.solve(wl.alpha, b, tol=1e-6, arith=nlh.SOLVE_MIXED, inner_tol=0.0)
         for r in (fixed, auto):
             assert r.info["status"] == 0 and r.info["rel_res_true"] <= 1e-6, r.info
-        assert auto.info["iters"] <= fixed.info["iters"] + 6, (auto.info, fixed.info)
+        assert auto.info["iters"] <= 40 and auto.info["outer"] <= 4, (auto.info, fixed.info)
         P.close()
